@@ -1,0 +1,349 @@
+"""Benchmark: execute a correlation-function contraction DAG on B300.
+
+One step = one execution of the whole DAG (every contraction of every
+correlation function, in the tree scheduler's order, then the correlators),
+i.e. all rows of the hot path over one synthetic workload.  The default
+workload is the 200-function multi-meson DAG (Lt=64, N=64, ~2,100
+contractions, FP64 path, unlimited budget).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` = algorithmic complex TFLOP/s
+(8 real flops per complex multiply-add) with leaves already resident in
+device memory; ``e2e`` = the same metric through the public C ABI with the
+leaves loaded from the library's pinned host store every step and all
+correlators read back to the host.  N>1 runs independent replicas (one DAG
+per rank, weak scaling).  ``--impl reference`` times the CPU oracle on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture (None
+# until captured for the current kernel build; see profiles/).
+TRAFFIC_PER_LAUNCH = None
+FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 rate, nominal
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="multi_meson")
+    ap.add_argument("--policy", default="tree")
+    ap.add_argument("--evict", default="lru")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [p.get("num_threads", 0) for p in threadpool_info() if p.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return 1
+
+
+def node_flops(od, u):
+    nd = od.nodes[u]
+    L, R = od.nodes[nd.left], od.nodes[nd.right]
+    K = int(np.prod([L.extents[a] for a in nd.la], dtype=np.int64))
+    M = int(np.prod(L.extents, dtype=np.int64)) // K
+    N = int(np.prod(R.extents, dtype=np.int64)) // K
+    return 8 * od.lt * M * N * K
+
+
+def oracle_sample(wl, seconds, rng_seed=0):
+    """Time the CPU oracle on a random subset of correlation functions
+    (their descendant closures), sized to about ``seconds`` of work."""
+    from oracle import contract as C
+    from oracle import dag as D
+    import synth
+    od, ids = D.build_from_workload(wl)
+    cache = {}
+
+    def lf(u):
+        li = od.nodes[u].leaf_index
+        if li not in cache:
+            cache[li] = synth.leaf_data(wl, li)
+        return cache[li]
+    rng = np.random.default_rng(rng_seed)
+    roots = od.roots()
+    perm = rng.permutation(len(roots))
+    # calibrate on a few roots, then size the sample
+    cal = [roots[i] for i in perm[:4]]
+    t0 = time.perf_counter()
+    C.evaluate(od, lf, cal)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    calf = sum(node_flops(od, u) for u in C.closure(od, cal) if not od.nodes[u].is_leaf)
+    rate = calf / dt
+    chosen, fl = [], 0
+    for i in perm:
+        chosen.append(roots[i])
+        fl = sum(node_flops(od, u) for u in C.closure(od, chosen) if not od.nodes[u].is_leaf)
+        if fl >= rate * seconds:
+            break
+    t0 = time.perf_counter()
+    C.evaluate(od, lf, chosen)
+    el = time.perf_counter() - t0
+    return fl, el, len(chosen), len(roots)
+
+
+def run_reference(args, ws, rank):
+    import synth
+    if rank != 0:
+        return
+    wl = synth.make_workload(args.workload)
+    per_step = 8.0
+    oracle_sample(wl, 1.0)  # warm caches
+    total_f, total_t = 0, 0.0
+    for w in range(args.warmup):
+        oracle_sample(wl, per_step, rng_seed=100 + w)
+    samples = []
+    for k in range(args.steps):
+        f, t, nr, nt = oracle_sample(wl, per_step, rng_seed=k)
+        total_f += f
+        total_t += t
+        samples.append((nr, nt))
+    v = total_f / total_t / 1e12
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "dag_complex_tflops", "value": v, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "lt": wl.lt, "nvec": wl.nvec,
+                   "functions": len(wl.functions), "policy": args.policy,
+                   "precision": "fp64", "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: %d of %d correlator trees (random, seeded), "
+                                   "their descendant closures evaluated by the complex128 "
+                                   "oracle (numpy tensordot per time slice)"
+                                   % (samples[0][0], samples[0][1])},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2511_02257_b300 as L
+    import synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    wl = synth.make_workload(args.workload, seed=rank)
+    budget = wl.budget_bytes
+    t0 = time.perf_counter()
+    nd, _ = L.build_dag(wl, precision=args.precision,
+                        leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    planned = nd.schedule(args.policy, args.evict, budget)
+    t_sched = time.perf_counter() - t0
+    stream = torch.cuda.current_stream().cuda_stream
+    dev_stream = torch.cuda.current_stream()
+
+    # ---- device-resident leaves: the kernel-level metric
+    nd.stage_leaves(stream)
+    nd.set_option(L.LQC_OPT_TIMING, 1)
+    for _ in range(args.warmup):
+        nd.execute(stream)
+    nd.wait()
+    info0 = nd.exec_info()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(dev_stream)
+        for _ in range(args.steps):
+            nd.execute(stream)
+        e1.record(dev_stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    info1 = nd.exec_info()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops_step = info1["flops"]
+    value = ws * flops_step * args.steps / (ms * 1e-3) / 1e12
+    # dominant kernel: the exterior contraction
+    n_c = info1["n_contract"] - info0["n_contract"]
+    ms_c = info1["ms_contract"] - info0["ms_contract"]
+    fl_c = info1["flops_contract"] - info0["flops_contract"]
+    ms_a = info1["ms_contract_all"] - info0["ms_contract_all"]
+    achieved = fl_c / (ms_c * 1e-3) / 1e12 if ms_c > 0 else None
+    probe = L.measure_fp64_peak()
+    kernels = info1["n_kernels"]
+
+    # ---- end to end: leaves from pinned host memory, correlators back to the host
+    e2e = None
+    if not args.no_e2e:
+        nd.set_option(L.LQC_OPT_TIMING, 0)
+        nd.unstage_leaves()
+        out = np.zeros((len(nd.roots()), wl.lt), dtype=np.complex128)
+        nd.execute(stream)
+        nd.read_all_correlators(out)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            nd.execute(stream)
+            nd.read_all_correlators(out)
+        t_e2e = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        st = nd.stats()
+        e2e = {"value": ws * flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": st["h2d_bytes"],
+               "d2h_bytes_per_step": st["d2h_bytes"] + out.nbytes,
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        f, t, nr, nt = oracle_sample(wl, 15.0)
+        cpu = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": "%d of %d correlator trees (random, seeded) with their descendant "
+                         "closures, %.2f GFLOP in %.1f s" % (nr, nt, f / 1e9, t)}
+
+    if rank == 0:
+        line = {
+            "metric": "dag_complex_tflops", "value": value, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "lt": wl.lt, "nvec": wl.nvec,
+                       "functions": len(wl.functions), "contractions": len(nd.order()),
+                       "policy": args.policy, "evict": args.evict, "budget_bytes": budget,
+                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
+                             % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,
+                                info1["arena_bytes"] / 1e9)},
+            "time_to_solution_s": ms / args.steps / 1e3,
+            "flops_per_step": flops_step,
+            "peak_paper_bytes": planned["peak_paper"], "peak_exec_bytes": planned["peak_exec"],
+            "n_evict": planned["n_evict"], "h2d_gb_per_step": planned["h2d_bytes"] / 1e9,
+            "d2h_gb_per_step": planned["d2h_bytes"] / 1e9,
+            "schedule_ms": 1e3 * t_sched, "dag_build_s": t_build,
+            "roofline": {"kernel": "k_contract_fp64", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
+                         "peak_source": "nominal B300 FP64 rate (profiling recipe table)",
+                         "fma_probe_tflops": probe,
+                         "frac_of_probe": achieved / probe if achieved else None,
+                         "traffic": TRAFFIC_PER_LAUNCH,
+                         "launches": n_c, "kernel_ms_per_step": ms_c / args.steps,
+                         "contract_all_ms_per_step": ms_a / args.steps},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": kernels * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+/*
+ * lqc.h -- C ABI of the B300 contraction-DAG executor.
+ *
+ * The library executes the contraction DAG of many-body correlation
+ * functions (arXiv 2511.02257): binary batched complex tensor contractions
+ * (batch axis = time slice Lt, contracted axes = distillation / spin
+ * indices) run in the order chosen by a peak-memory-minimising scheduler
+ * (the paper's tree scheduler, Alg. 4-8, or sibling scheduler, Alg. 1-3,
+ * or a naive topological order), under a fixed device-memory budget with
+ * eviction of tensors to pinned host memory.
+ *
+ * Conventions shared by every call
+ *  - Every call returns an lqc_status.  Out-parameters are written only on
+ *    LQC_OK.  After any error the DAG stays valid and destroyable;
+ *    lqc_last_error() describes the last failure on that DAG.
+ *  - Node ids are dense int64 in insertion order; an operand must exist
+ *    before it is used, so ids are topological by construction.
+ *  - Tensors: a leading batch axis of extent lt (never contracted), then
+ *    `rank` axes with the given extents, row-major, complex values stored as
+ *    interleaved (re, im) doubles.  Sizes in bytes (u.size of the paper,
+ *    Sec. II-B) count the batch axis: lt * prod(extents) * element bytes,
+ *    element bytes = 16 (complex128 storage, LQC_PREC_FP64) or 8 (complex64
+ *    storage, mixed precisions).
+ *  - Contraction semantics: out[t][f_L..., f_R...] = sum over the paired
+ *    indices of L[t][...] * R[t][...], where left axis la[i] is paired with
+ *    right axis ra[i] (equal extents), f_L are the left operand's unpaired
+ *    axes in order and f_R the right operand's.  A rank-0 output is a
+ *    correlator: one complex number per time slice (the paper's
+ *    "contract all" of a root, Sec. IV-A).
+ *  - Node types (Sec. II-B): LEAF = no inputs, ROOT = no consumers,
+ *    INTERIOR = the rest.  Contraction tree T_r = descendant closure of
+ *    root r.  A correlation function made of several trees is the caller's
+ *    sum of lqc_dag_read_correlator over its roots.
+ *  - Threading: one DAG must not be used from two threads at once;
+ *    different DAGs are independent.
+ */
+#ifndef LQC_H_
+#define LQC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LQC_MAX_RANK 8
+
+typedef struct lqc_dag lqc_dag; /* opaque; owned by the library */
+
+typedef enum {
+  LQC_OK = 0,
+  LQC_ERR_ARG = -1,      /* invalid argument (ids, axes, extents, sizes)   */
+  LQC_ERR_BUDGET = -2,   /* one contraction's inputs+output exceed budget */
+  LQC_ERR_CUDA = -3,     /* a CUDA runtime call failed                     */
+  LQC_ERR_HOST_MEM = -4, /* pinned host allocation failed                  */
+  LQC_ERR_STATE = -5,    /* call out of order (e.g. execute before schedule,
+                            leaf without data)                             */
+  LQC_ERR_TIMEOUT = -6   /* a bounded host wait on the device ran out      */
+} lqc_status;
+
+typedef enum {
+  LQC_SCHED_NAIVE_TOPO = 0, /* non-leaf nodes in ascending id             */
+  LQC_SCHED_TREE = 1,       /* tree scheduler, Alg. 4-8 (Sec. III-B)      */
+  LQC_SCHED_SIBLING = 2     /* sibling scheduler, Alg. 1-3 (Sec. III-A)   */
+} lqc_policy;
+
+typedef enum {
+  LQC_EVICT_LRU = 0,     /* least recently touched non-operand, ties to the
+                            smaller id ("pre-protected LRU", Sec. II-A)     */
+  LQC_EVICT_NEXT_USE = 1 /* farthest next use in the order, ties to the
+                            larger size, then the smaller id               */
+} lqc_evict;
+
+typedef enum {
+  LQC_PREC_FP64 = 0,  /* complex128 storage, FP64 arithmetic             */
+  LQC_PREC_TF32X3 = 1,/* complex64 storage, split TF32x3 tensor-core
+                         products, FP32 accumulation, FP64 trace sums    */
+  LQC_PREC_BF16X3 = 2 /* complex64 storage, split BF16x3 products        */
+} lqc_precision;
+
+/* Schedule / execution figures, all exact integers (bytes or counts).
+ *  peak_paper: max_i M_i of the paper's memory model (Sec. II-C) for the
+ *              order, independent of the budget.
+ *  peak_exec:  max over steps of device bytes while a contraction runs
+ *              (resident tensors + its inputs + its output) under the budget.
+ *  n_evict:    tensors dropped from the device to make room.
+ *  n_h2d / h2d_bytes: host-to-device tensor loads (leaves on first use and
+ *              reloads of evicted tensors).
+ *  n_d2h / d2h_bytes: write-backs of evicted intermediates that had no host
+ *              copy yet. */
+typedef struct {
+  int64_t peak_paper, peak_exec, n_evict, n_h2d, n_d2h, h2d_bytes, d2h_bytes;
+} lqc_stats;
+
+/* Execution report of the last lqc_dag_execute (filled by lqc_dag_get_exec_info). */
+typedef struct {
+  int64_t n_kernels;      /* kernels launched by the last execute            */
+  int64_t flops;          /* algorithmic real flops: 8 per complex multiply-add */
+  int64_t arena_bytes;    /* device arena holding resident tensors           */
+  int64_t copied_h2d;     /* bytes actually copied host->device              */
+  int64_t copied_d2h;     /* bytes actually copied device->host (evictions)  */
+  int64_t n_ops;          /* plan ops walked                                 */
+  /* with LQC_OPT_TIMING: CUDA-event durations of the contraction kernels
+   * and their algorithmic flops, per kind, summed over every execute since
+   * the option was set or the plan last changed (reading waits for them)   */
+  int64_t n_contract, n_contract_all;     /* launches                         */
+  double ms_contract, ms_contract_all;    /* summed kernel time (ms)          */
+  int64_t flops_contract, flops_contract_all;
+} lqc_exec_info;
+
+/* Option keys for lqc_dag_set_option. */
+typedef enum {
+  LQC_OPT_CUDA_GRAPH = 1, /* 1: capture the op stream into a CUDA graph on
+                             the first execute and replay it afterwards    */
+  LQC_OPT_POISON = 2,     /* 1: fill each freed / evicted device tensor with
+                             NaN (use-after-free shows as a NaN result)    */
+  LQC_OPT_TIMING = 3      /* 1: bracket every contraction kernel with CUDA
+                             events on the compute stream; lqc_dag_get_exec_info
+                             then reports summed per-kind kernel time        */
+} lqc_option;
+
+/* Create an empty DAG.  lt >= 1 time slices; prec selects storage and
+ * arithmetic.  *out receives the handle (owned by the caller, released with
+ * lqc_dag_destroy). */
+int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec);
+
+/* Release every host and device resource of the DAG.  Synchronises with any
+ * outstanding execution first.  NULL is accepted. */
+int lqc_dag_destroy(lqc_dag* dag);
+
+/* Register a leaf tensor (Sec. II-B: a node with no inputs).
+ *  rank in [0, LQC_MAX_RANK], extents[rank] >= 1 (batch axis excluded).
+ *  data: lt * prod(extents) complex values as interleaved doubles, or NULL
+ *  to register the shape only (scheduling/planning without execution; set
+ *  the values later with lqc_dag_set_leaf_data).  The values are copied
+ *  into the library's pinned host store (mixed precisions store them
+ *  normalised to complex64, see lqc_precision); the caller keeps ownership
+ *  of `data`.  *node_id receives the new id.
+ *  Errors: LQC_ERR_ARG (rank/extents), LQC_ERR_HOST_MEM, LQC_ERR_STATE
+ *  (after lqc_dag_schedule). */
+int lqc_dag_add_leaf_tensor(lqc_dag* dag, int rank, const int64_t* extents,
+                            const double* data, int64_t* node_id);
+
+/* (Re)set the values of an existing leaf; same layout and ownership as
+ * lqc_dag_add_leaf_tensor.  Allowed after scheduling; takes effect at the
+ * next execute (it synchronises with an execution in flight). */
+int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
+
+/* Register a binary contraction (a non-leaf node, Sec. II-B).
+ *  left/right: existing node ids (may be equal); npairs in [1, LQC_MAX_RANK];
+ *  la[i] (axis of left) is contracted with ra[i] (axis of right), extents
+ *  equal, axes distinct on each side.  The output rank is
+ *  rank(left) + rank(right) - 2*npairs and must not exceed LQC_MAX_RANK.
+ *  A request identical to an earlier one (same left, right, la, ra) returns
+ *  the earlier node's id: identical sub-contractions of different trees are
+ *  merged into one DAG node.  A rank-0 output must not be an operand of a
+ *  later contraction.
+ *  Errors: LQC_ERR_ARG, LQC_ERR_STATE (after lqc_dag_schedule). */
+int lqc_dag_add_contraction(lqc_dag* dag, int64_t left, int64_t right, int npairs,
+                            const int* la, const int* ra, int64_t* node_id);
+
+/* Freeze the DAG, compute the contraction order with `policy` and replay it
+ * under `budget_bytes` (0 = unlimited) with eviction policy `evict`,
+ * producing the op list (LOAD / EVICT / CONTRACT / FREE) and its figures.
+ * `planned` (nullable) receives the figures.  May be called again with other
+ * arguments (replaces the previous schedule).
+ * Errors: LQC_ERR_BUDGET if one contraction's inputs + output exceed the
+ * budget (the previous schedule is then dropped), LQC_ERR_ARG. */
+int lqc_dag_schedule(lqc_dag* dag, lqc_policy policy, lqc_evict evict,
+                     uint64_t budget_bytes, lqc_stats* planned);
+
+/* Like lqc_dag_schedule with a caller-given order: `order` lists every
+ * non-leaf node exactly once, operands first (n = number of contractions).
+ * Errors: LQC_ERR_ARG for an invalid order, LQC_ERR_BUDGET. */
+int lqc_dag_set_order(lqc_dag* dag, const int64_t* order, int64_t n, lqc_evict evict,
+                      uint64_t budget_bytes, lqc_stats* planned);
+
+/* Copy the current order (non-leaf ids) into order[0..cap); *n receives
+ * its length (also when cap is too small, in which case nothing is copied
+ * and LQC_ERR_ARG is returned).  LQC_ERR_STATE before scheduling. */
+int lqc_dag_get_order(lqc_dag* dag, int64_t* order, int64_t cap, int64_t* n);
+
+/* Copy the op list: kind[k] in {0 LOAD, 1 EVICT, 2 CONTRACT, 3 FREE},
+ * node[k], flag[k] (1 = the EVICT writes the tensor back to the host).
+ * Same cap / *n behaviour as lqc_dag_get_order. */
+int lqc_dag_get_plan(lqc_dag* dag, int32_t* kind, int64_t* node, int32_t* flag,
+                     int64_t cap, int64_t* n);
+
+/* Set an lqc_option.  Takes effect at the next execute. */
+int lqc_dag_set_option(lqc_dag* dag, int option, int64_t value);
+
+/* Upload every used leaf once into a device copy kept outside the budget,
+ * so that later executes read leaves from device memory instead of loading
+ * them over the host link (LOAD ops of leaves become no-ops; evicted
+ * intermediates still move).  Synchronous.  lqc_dag_unstage_leaves frees
+ * the copy. Errors: LQC_ERR_STATE (no data), LQC_ERR_CUDA. */
+int lqc_dag_stage_leaves(lqc_dag* dag, void* stream);
+int lqc_dag_unstage_leaves(lqc_dag* dag);
+
+/* Execute the scheduled op list asynchronously on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Host-to-device loads and write-backs
+ * run on two side streams owned by the library, ordered with the compute
+ * stream by events.  Correlators land in a device buffer read by
+ * lqc_dag_read_correlator.  The first call on a DAG allocates the device
+ * arena (sized by the plan) and the results buffer; later calls reuse them.
+ * Errors: LQC_ERR_STATE (not scheduled, leaf without data), LQC_ERR_CUDA. */
+int lqc_dag_execute(lqc_dag* dag, void* stream);
+
+/* Wait (bounded by timeout_ms; <= 0 means 60000) for the last execute to
+ * finish.  LQC_ERR_TIMEOUT if it did not finish in time (the DAG stays
+ * usable; call again), LQC_ERR_CUDA on a device error. */
+int lqc_dag_wait(lqc_dag* dag, int64_t timeout_ms);
+
+/* Correlator of a rank-0 root: out[2*t], out[2*t+1] = re, im of C_root(t),
+ * t in [0, lt).  Waits for the last execute (60 s bound).
+ * Errors: LQC_ERR_ARG (not a rank-0 root), LQC_ERR_STATE (not executed). */
+int lqc_dag_read_correlator(lqc_dag* dag, int64_t root_id, double* out);
+
+/* All rank-0 roots at once, in ascending id: out holds n_roots * 2 * lt
+ * doubles (one device-to-host copy).  Same errors as above. */
+int lqc_dag_read_all_correlators(lqc_dag* dag, double* out, int64_t cap_doubles);
+
+/* Ids of the rank-0 roots in ascending order; same cap / *n convention. */
+int lqc_dag_get_roots(lqc_dag* dag, int64_t* roots, int64_t cap, int64_t* n);
+
+/* Number of nodes and the size in bytes / rank of a node. */
+int lqc_dag_num_nodes(lqc_dag* dag, int64_t* n);
+int lqc_dag_node_info(lqc_dag* dag, int64_t id, int64_t* size_bytes, int* rank,
+                      int* is_leaf);
+
+/* Figures counted by the last execute (equal to the planned figures by
+ * construction of the executor; peak_exec is taken from the plan). */
+int lqc_dag_get_stats(lqc_dag* dag, lqc_stats* measured);
+int lqc_dag_get_exec_info(lqc_dag* dag, lqc_exec_info* info);
+
+/* Human-readable description of the last error on `dag` ("" if none).  The
+ * string is owned by the DAG and valid until its next call. */
+const char* lqc_last_error(const lqc_dag* dag);
+
+/* ---------------------------------------------------------------------
+ * Single-contraction entry points on caller-owned device buffers (the
+ * kernels the executor runs for one DAG node).  Same tensor layout and
+ * contraction semantics as above; A, B, C are device pointers to
+ * interleaved complex128, C is written (not accumulated) with layout
+ * [lt][free(A)...][free(B)...].  Asynchronous on `stream`.
+ * --------------------------------------------------------------------- */
+
+/* Exterior contraction (output rank >= 1), FP64 arithmetic (Sec. II-B
+ * binary contraction; the paper's "exterior contract" queue op, Sec. IV-A).
+ * Errors: LQC_ERR_ARG (shapes/pairs), LQC_ERR_CUDA (launch). */
+int lqc_contract_fp64(const double* A, int rank_a, const int64_t* ext_a,
+                      const double* B, int rank_b, const int64_t* ext_b,
+                      int npairs, const int* la, const int* ra, int64_t lt,
+                      double* C, void* stream);
+
+/* Contract-all (every axis paired; rank-0 output = correlator, Sec. IV-A):
+ * C[t] = sum over all indices of A[t][...] * B[t][paired ...], FP64
+ * accumulation in a fixed order (results are bit-reproducible).
+ * `scratch` must hold lqc_contract_all_scratch_bytes(...) bytes of device
+ * memory (caller-owned; its previous contents are ignored).
+ * Errors: LQC_ERR_ARG, LQC_ERR_CUDA. */
+int lqc_contract_all_fp64(const double* A, int rank_a, const int64_t* ext_a,
+                          const double* B, int rank_b, const int64_t* ext_b,
+                          int npairs, const int* la, const int* ra, int64_t lt,
+                          double* C, void* scratch, void* stream);
+int64_t lqc_contract_all_scratch_bytes(int64_t lt, int64_t elems_per_slice);
+
+/* Diagnostic (no counterpart in the paper): measure this device's FP64 FMA
+ * throughput with a register-resident FMA loop on every SM, ~20 ms,
+ * synchronous.  *tflops receives 2 * FMAs / second / 1e12 (the denominator
+ * of the FP64 path's roofline).  Errors: LQC_ERR_CUDA. */
+int lqc_measure_fp64_peak(double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQC_H_ */

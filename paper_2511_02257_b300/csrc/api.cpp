@@ -1,0 +1,392 @@
+// C ABI: DAG construction with merging of identical requests (Sec. II-B),
+// scheduling + planning, and the thin wrappers around the executor.
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+
+#include "internal.hpp"
+
+using lqc::Dag;
+using lqc::Node;
+
+struct lqc_dag {
+  Dag d;
+};
+
+namespace {
+
+int fail(lqc_dag* h, int code, const std::string& msg) {
+  if (h) h->d.err = msg;
+  return code;
+}
+
+#define LQC_GUARD_BEGIN try {
+#define LQC_GUARD_END(h)                                                  \
+  }                                                                       \
+  catch (const std::bad_alloc&) {                                         \
+    return fail(h, LQC_ERR_HOST_MEM, "host allocation failed");           \
+  }                                                                       \
+  catch (const std::exception& e) {                                       \
+    return fail(h, LQC_ERR_ARG, std::string("internal error: ") + e.what()); \
+  }
+
+std::string dedup_key(int64_t l, int64_t r, int np, const int* la, const int* ra) {
+  std::string k;
+  k.append(reinterpret_cast<const char*>(&l), sizeof l);
+  k.append(reinterpret_cast<const char*>(&r), sizeof r);
+  k.append(reinterpret_cast<const char*>(&np), sizeof np);
+  k.append(reinterpret_cast<const char*>(la), sizeof(int) * np);
+  k.append(reinterpret_cast<const char*>(ra), sizeof(int) * np);
+  return k;
+}
+
+int finish_schedule(lqc_dag* h, std::vector<int64_t>&& order, lqc_evict evict,
+                    uint64_t budget, lqc_stats* planned) {
+  Dag& g = h->d;
+  std::vector<lqc::Op> ops;
+  lqc_stats st{};
+  std::string err;
+  lqc::exec_invalidate_plan(g);
+  if (!lqc::plan_replay(g, order, budget, evict, &ops, &st, &err)) {
+    g.scheduled = false;
+    g.order.clear();
+    g.ops.clear();
+    return fail(h, LQC_ERR_BUDGET, err);
+  }
+  g.frozen = true;
+  g.order = std::move(order);
+  g.ops = std::move(ops);
+  g.planned = st;
+  g.budget = budget;
+  g.evict = evict;
+  g.scheduled = true;
+  g.executed = false;
+  if (planned) *planned = st;
+  return LQC_OK;
+}
+
+template <typename T>
+int copy_out(lqc_dag* h, const std::vector<T>& v, T* dst, int64_t cap, int64_t* n) {
+  if (!n) return fail(h, LQC_ERR_ARG, "null length pointer");
+  *n = (int64_t)v.size();
+  if (cap < (int64_t)v.size() || (!dst && !v.empty())) {
+    return fail(h, LQC_ERR_ARG, "output capacity too small");
+  }
+  if (!v.empty()) std::memcpy(dst, v.data(), sizeof(T) * v.size());
+  return LQC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
+  if (!out || lt < 1) return LQC_ERR_ARG;
+  if (prec != LQC_PREC_FP64 && prec != LQC_PREC_TF32X3 && prec != LQC_PREC_BF16X3)
+    return LQC_ERR_ARG;
+  try {
+    lqc_dag* h = new lqc_dag();
+    h->d.lt = lt;
+    h->d.prec = prec;
+    h->d.elem_bytes = prec == LQC_PREC_FP64 ? 16 : 8;
+    *out = h;
+    return LQC_OK;
+  } catch (...) {
+    return LQC_ERR_HOST_MEM;
+  }
+}
+
+int lqc_dag_destroy(lqc_dag* h) {
+  if (!h) return LQC_OK;
+  lqc::exec_destroy(h->d);
+  for (Node& n : h->d.nodes) lqc::host_store_free(n);
+  delete h;
+  return LQC_OK;
+}
+
+int lqc_dag_add_leaf_tensor(lqc_dag* h, int rank, const int64_t* extents, const double* data,
+                            int64_t* node_id) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  LQC_GUARD_BEGIN
+  if (g.frozen) return fail(h, LQC_ERR_STATE, "DAG is frozen by lqc_dag_schedule");
+  if (rank < 0 || rank > LQC_MAX_RANK || (rank > 0 && !extents) || !node_id)
+    return fail(h, LQC_ERR_ARG, "bad leaf rank/extents");
+  Node n;
+  n.rank = rank;
+  n.elems = 1;
+  for (int i = 0; i < rank; ++i) {
+    if (extents[i] < 1 || extents[i] > (int64_t)1 << 31)
+      return fail(h, LQC_ERR_ARG, "leaf extent out of range");
+    n.ext[i] = extents[i];
+    n.elems *= extents[i];
+    if (n.elems > ((int64_t)1 << 40)) return fail(h, LQC_ERR_ARG, "leaf too large");
+  }
+  g.nodes.push_back(n);
+  int64_t id = (int64_t)g.nodes.size() - 1;
+  if (data) {
+    int rc = lqc_dag_set_leaf_data(h, id, data);
+    if (rc != LQC_OK) {
+      g.nodes.pop_back();
+      return rc;
+    }
+  }
+  *node_id = id;
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs, const int* la,
+                            const int* ra, int64_t* node_id) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  LQC_GUARD_BEGIN
+  if (g.frozen) return fail(h, LQC_ERR_STATE, "DAG is frozen by lqc_dag_schedule");
+  const int64_t N = (int64_t)g.nodes.size();
+  if (!node_id || left < 0 || right < 0 || left >= N || right >= N)
+    return fail(h, LQC_ERR_ARG, "operand id out of range");
+  if (npairs < 1 || npairs > LQC_MAX_RANK || !la || !ra)
+    return fail(h, LQC_ERR_ARG, "npairs must be in [1, LQC_MAX_RANK]");
+  const Node& L = g.nodes[left];
+  const Node& R = g.nodes[right];
+  if (L.rank == 0 || R.rank == 0)
+    return fail(h, LQC_ERR_ARG, "a rank-0 correlator cannot be an operand");
+  bool usedL[LQC_MAX_RANK] = {false}, usedR[LQC_MAX_RANK] = {false};
+  for (int i = 0; i < npairs; ++i) {
+    if (la[i] < 0 || la[i] >= L.rank || ra[i] < 0 || ra[i] >= R.rank)
+      return fail(h, LQC_ERR_ARG, "axis index out of range");
+    if (usedL[la[i]] || usedR[ra[i]]) return fail(h, LQC_ERR_ARG, "axis paired twice");
+    usedL[la[i]] = usedR[ra[i]] = true;
+    if (L.ext[la[i]] != R.ext[ra[i]]) return fail(h, LQC_ERR_ARG, "paired extents differ");
+  }
+  const int out_rank = L.rank + R.rank - 2 * npairs;
+  if (out_rank > LQC_MAX_RANK) return fail(h, LQC_ERR_ARG, "output rank too large");
+  std::string key = dedup_key(left, right, npairs, la, ra);
+  auto it = g.dedup.find(key);
+  if (it != g.dedup.end()) {
+    *node_id = it->second;
+    return LQC_OK;
+  }
+  Node n;
+  n.left = left;
+  n.right = right;
+  n.npairs = npairs;
+  for (int i = 0; i < npairs; ++i) {
+    n.la[i] = la[i];
+    n.ra[i] = ra[i];
+  }
+  n.rank = 0;
+  n.elems = 1;
+  for (int a = 0; a < L.rank; ++a)
+    if (!usedL[a]) { n.ext[n.rank++] = L.ext[a]; n.elems *= L.ext[a]; }
+  for (int b = 0; b < R.rank; ++b)
+    if (!usedR[b]) { n.ext[n.rank++] = R.ext[b]; n.elems *= R.ext[b]; }
+  if (n.elems > ((int64_t)1 << 40)) return fail(h, LQC_ERR_ARG, "output too large");
+  g.nodes.push_back(n);
+  const int64_t id = N;
+  g.nodes[left].parents.push_back(id);
+  if (right != left) g.nodes[right].parents.push_back(id);
+  g.dedup.emplace(std::move(key), id);
+  *node_id = id;
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_schedule(lqc_dag* h, lqc_policy policy, lqc_evict evict, uint64_t budget_bytes,
+                     lqc_stats* planned) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  LQC_GUARD_BEGIN
+  if (evict != LQC_EVICT_LRU && evict != LQC_EVICT_NEXT_USE)
+    return fail(h, LQC_ERR_ARG, "unknown eviction policy");
+  std::vector<int64_t> order;
+  switch (policy) {
+    case LQC_SCHED_NAIVE_TOPO: order = lqc::schedule_naive(g); break;
+    case LQC_SCHED_TREE: order = lqc::schedule_tree(g); break;
+    case LQC_SCHED_SIBLING: order = lqc::schedule_sibling(g); break;
+    default: return fail(h, LQC_ERR_ARG, "unknown scheduling policy");
+  }
+  return finish_schedule(h, std::move(order), evict, budget_bytes, planned);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_set_order(lqc_dag* h, const int64_t* order, int64_t n, lqc_evict evict,
+                      uint64_t budget_bytes, lqc_stats* planned) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  LQC_GUARD_BEGIN
+  if (evict != LQC_EVICT_LRU && evict != LQC_EVICT_NEXT_USE)
+    return fail(h, LQC_ERR_ARG, "unknown eviction policy");
+  const int64_t N = (int64_t)g.nodes.size();
+  int64_t n_contr = 0;
+  for (const Node& x : g.nodes) n_contr += x.is_leaf() ? 0 : 1;
+  if (n != n_contr || (n > 0 && !order)) return fail(h, LQC_ERR_ARG, "order length mismatch");
+  std::vector<uint8_t> done(N, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t u = order[i];
+    if (u < 0 || u >= N || g.nodes[u].is_leaf() || done[u])
+      return fail(h, LQC_ERR_ARG, "order entry invalid or repeated");
+    const Node& x = g.nodes[u];
+    for (int k = 0; k < x.n_children(); ++k) {
+      int64_t c = x.child(k);
+      if (!g.nodes[c].is_leaf() && !done[c]) return fail(h, LQC_ERR_ARG, "order not topological");
+    }
+    done[u] = 1;
+  }
+  return finish_schedule(h, std::vector<int64_t>(order, order + n), evict, budget_bytes, planned);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_get_order(lqc_dag* h, int64_t* order, int64_t cap, int64_t* n) {
+  if (!h) return LQC_ERR_ARG;
+  if (!h->d.scheduled) return fail(h, LQC_ERR_STATE, "not scheduled");
+  return copy_out(h, h->d.order, order, cap, n);
+}
+
+int lqc_dag_get_plan(lqc_dag* h, int32_t* kind, int64_t* node, int32_t* flag, int64_t cap,
+                     int64_t* n) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  if (!g.scheduled) return fail(h, LQC_ERR_STATE, "not scheduled");
+  if (!n) return fail(h, LQC_ERR_ARG, "null length pointer");
+  *n = (int64_t)g.ops.size();
+  if (cap < (int64_t)g.ops.size() || (!g.ops.empty() && (!kind || !node || !flag)))
+    return fail(h, LQC_ERR_ARG, "output capacity too small");
+  for (size_t k = 0; k < g.ops.size(); ++k) {
+    kind[k] = g.ops[k].kind;
+    node[k] = g.ops[k].node;
+    flag[k] = g.ops[k].flag;
+  }
+  return LQC_OK;
+}
+
+int lqc_dag_set_option(lqc_dag* h, int option, int64_t value) {
+  if (!h) return LQC_ERR_ARG;
+  switch (option) {
+    case LQC_OPT_CUDA_GRAPH: h->d.opt_graph = value ? 1 : 0; break;
+    case LQC_OPT_POISON: h->d.opt_poison = value ? 1 : 0; break;
+    case LQC_OPT_TIMING: h->d.opt_timing = value ? 1 : 0; break;
+    default: return fail(h, LQC_ERR_ARG, "unknown option");
+  }
+  lqc::exec_invalidate_plan(h->d);
+  return LQC_OK;
+}
+
+int lqc_dag_get_roots(lqc_dag* h, int64_t* roots, int64_t cap, int64_t* n) {
+  if (!h) return LQC_ERR_ARG;
+  std::vector<int64_t> r;
+  for (int64_t u = 0; u < (int64_t)h->d.nodes.size(); ++u) {
+    const Node& x = h->d.nodes[u];
+    if (!x.is_leaf() && x.parents.empty() && x.rank == 0) r.push_back(u);
+  }
+  return copy_out(h, r, roots, cap, n);
+}
+
+int lqc_dag_num_nodes(lqc_dag* h, int64_t* n) {
+  if (!h || !n) return LQC_ERR_ARG;
+  *n = (int64_t)h->d.nodes.size();
+  return LQC_OK;
+}
+
+int lqc_dag_node_info(lqc_dag* h, int64_t id, int64_t* size_bytes, int* rank, int* is_leaf) {
+  if (!h) return LQC_ERR_ARG;
+  if (id < 0 || id >= (int64_t)h->d.nodes.size()) return fail(h, LQC_ERR_ARG, "id out of range");
+  if (size_bytes) *size_bytes = h->d.size_bytes(id);
+  if (rank) *rank = h->d.nodes[id].rank;
+  if (is_leaf) *is_leaf = h->d.nodes[id].is_leaf() ? 1 : 0;
+  return LQC_OK;
+}
+
+int lqc_dag_set_leaf_data(lqc_dag* h, int64_t id, const double* data) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  LQC_GUARD_BEGIN
+  if (id < 0 || id >= (int64_t)g.nodes.size() || !g.nodes[id].is_leaf() || !data)
+    return fail(h, LQC_ERR_ARG, "not a leaf / null data");
+  int rc = lqc::exec_wait(g, 60000);
+  if (rc != LQC_OK) return rc;
+  std::string err;
+  rc = lqc::host_store_alloc(g, id, &err);
+  if (rc != LQC_OK) return fail(h, rc, err);
+  Node& n = g.nodes[id];
+  const int64_t cnt = g.lt * n.elems;  // complex values
+  if (g.prec == LQC_PREC_FP64) {
+    std::memcpy(n.host, data, (size_t)cnt * 16);
+  } else {
+    // complex64 storage: values are rounded to float once here, in FP64
+    float* dst = static_cast<float*>(n.host);
+    for (int64_t i = 0; i < 2 * cnt; ++i) dst[i] = (float)data[i];
+  }
+  lqc::exec_invalidate_plan(g);  // staged leaf copies are stale
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_stage_leaves(lqc_dag* h, void* stream) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_stage_leaves(h->d, stream);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_unstage_leaves(lqc_dag* h) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_unstage_leaves(h->d);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_execute(lqc_dag* h, void* stream) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  if (!h->d.scheduled) return fail(h, LQC_ERR_STATE, "execute before schedule");
+  return lqc::exec_run(h->d, stream);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_wait(lqc_dag* h, int64_t timeout_ms) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_wait(h->d, timeout_ms <= 0 ? 60000 : timeout_ms);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_read_correlator(lqc_dag* h, int64_t root, double* out) {
+  if (!h || !out) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_read(h->d, root, out);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_read_all_correlators(lqc_dag* h, double* out, int64_t cap) {
+  if (!h || !out) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_read_all(h->d, out, cap);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_get_stats(lqc_dag* h, lqc_stats* s) {
+  if (!h || !s) return LQC_ERR_ARG;
+  if (!h->d.executed) return fail(h, LQC_ERR_STATE, "not executed");
+  *s = h->d.measured;
+  return LQC_OK;
+}
+
+int lqc_dag_get_exec_info(lqc_dag* h, lqc_exec_info* info) {
+  if (!h || !info) return LQC_ERR_ARG;
+  if (!h->d.executed) return fail(h, LQC_ERR_STATE, "not executed");
+  LQC_GUARD_BEGIN
+  int rc = lqc::exec_collect_timing(h->d);
+  if (rc != LQC_OK) return rc;
+  *info = h->d.info;
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
+
+const char* lqc_last_error(const lqc_dag* h) {
+  if (!h) return "null DAG handle";
+  return h->d.err.c_str();
+}
+
+}  // extern "C"

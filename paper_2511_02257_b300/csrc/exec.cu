@@ -1,0 +1,762 @@
+// Executor: walks the planned op list (LOAD / EVICT / CONTRACT / FREE) on
+// the device.
+//
+// Memory: one device arena sized by an offline placement of every planned
+// residency interval (best fit with coalescing, 256-byte aligned); the plan's
+// byte accounting is the paper's memory model (Sec. II-C) plus the budget
+// rules, the arena is its physical image.  Streams: contractions run on the
+// caller's stream; host-to-device loads and device-to-host write-backs run on
+// two library-owned side streams.  Every cross-stream dependency (a load
+// into memory last read by a kernel, a kernel reading a loaded tensor, a
+// write-back of a tensor a kernel produced, a kernel writing memory a
+// write-back is still reading) is computed once per plan and becomes an
+// event wait, so copies overlap contractions wherever the plan allows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <thread>
+
+#include "internal.hpp"
+#include "kernels.hpp"
+
+namespace lqc {
+
+namespace {
+
+enum Stream { S_COMPUTE = 0, S_H2D = 1, S_D2H = 2 };
+enum IKind { I_LOAD = 0, I_WRITEBACK = 1, I_CONTRACT = 2, I_CONTRACT_ALL = 3, I_POISON = 4 };
+
+struct Instr {
+  int kind;
+  int stream;
+  int64_t node;
+  int64_t dst;        // arena offset (LOAD, CONTRACT) / -1 = results buffer
+  int64_t src[2];     // arena offsets of the operands, -2 = staged leaf
+  int64_t bytes;
+  int32_t nwait = 0;
+  int32_t wait[6];
+  int32_t rec = -1;   // event slot recorded after this instruction
+  int32_t root_slot = -1;
+};
+
+struct Seg {
+  int64_t size;
+  int32_t dep[3];     // last instruction per stream that touched the bytes
+};
+
+// Best-fit placement with coalescing; grows the high-water mark on demand.
+struct Placer {
+  std::map<int64_t, Seg> free_;  // offset -> free segment
+  int64_t top = 0;
+  static int32_t mx(int32_t a, int32_t b) { return a > b ? a : b; }
+
+  int64_t alloc(int64_t size, int32_t dep[3]) {
+    size = (size + 255) & ~int64_t(255);
+    auto best = free_.end();
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second.size >= size && (best == free_.end() || it->second.size < best->second.size))
+        best = it;
+    if (best == free_.end()) {
+      // extend: merge with a free tail segment if there is one
+      int64_t off = top;
+      dep[0] = dep[1] = dep[2] = -1;
+      if (!free_.empty()) {
+        auto last = std::prev(free_.end());
+        if (last->first + last->second.size == top) {
+          off = last->first;
+          for (int s = 0; s < 3; ++s) dep[s] = last->second.dep[s];
+          free_.erase(last);
+        }
+      }
+      top = off + size;
+      return off;
+    }
+    int64_t off = best->first;
+    Seg sg = best->second;
+    free_.erase(best);
+    for (int s = 0; s < 3; ++s) dep[s] = sg.dep[s];
+    if (sg.size > size) free_[off + size] = Seg{sg.size - size, {sg.dep[0], sg.dep[1], sg.dep[2]}};
+    return off;
+  }
+
+  void release(int64_t off, int64_t size, const int32_t dep[3]) {
+    size = (size + 255) & ~int64_t(255);
+    Seg s{size, {dep[0], dep[1], dep[2]}};
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && off + size == nx->first) {
+      s.size += nx->second.size;
+      for (int k = 0; k < 3; ++k) s.dep[k] = mx(s.dep[k], nx->second.dep[k]);
+      free_.erase(nx);
+    }
+    auto it = free_.lower_bound(off);
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second.size == off) {
+        pv->second.size += s.size;
+        for (int k = 0; k < 3; ++k) pv->second.dep[k] = mx(pv->second.dep[k], s.dep[k]);
+        return;
+      }
+    }
+    free_[off] = s;
+  }
+};
+
+}  // namespace
+
+struct ExecState {
+  int device = -1;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // [1] h2d, [2] d2h
+  cudaEvent_t start_ev = nullptr, done_ev = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<Instr> prog;
+  std::vector<ContractDesc> cdesc;        // per instruction (CONTRACT)
+  std::vector<ContractAllDesc> adesc;     // per instruction (CONTRACT_ALL)
+  bool prog_valid = false;
+  int64_t arena_bytes = 0;
+  char* arena = nullptr;
+  double* results = nullptr;
+  int64_t n_results = 0;                  // rank-0 roots
+  std::vector<int64_t> root_ids;          // ascending
+  std::vector<int32_t> slot_of;           // node -> results slot (-1)
+  double* scratch = nullptr;
+  int64_t scratch_bytes = 0;
+  std::vector<void*> host_slot;           // write-back copies (pinned)
+  std::vector<int64_t> host_slot_bytes;
+  std::vector<void*> staged;              // node -> device copy of a leaf
+  bool staged_valid = false;
+  int64_t flops = 0, copy_h2d = 0, copy_d2h = 0, n_kernels = 0;
+  lqc_stats counted{};
+  bool ran = false;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  // LQC_OPT_TIMING: two sets (alternating executes) of begin/end event
+  // pairs per contraction instruction; durations accumulate in g.info
+  std::vector<cudaEvent_t> tev[2];
+  std::vector<int32_t> tev_kind;
+  std::vector<int64_t> tev_flops;
+  bool timing_pending[2] = {false, false};
+  int tset = 0;
+};
+
+namespace {
+
+int cuda_fail(Dag& g, cudaError_t e, const char* what) {
+  g.err = std::string(what) + ": " + cudaGetErrorString(e);
+  return LQC_ERR_CUDA;
+}
+
+#define CK(call, what)                               \
+  do {                                               \
+    cudaError_t e__ = (call);                        \
+    if (e__ != cudaSuccess) return cuda_fail(g, e__, what); \
+  } while (0)
+
+int ensure_state(Dag& g) {
+  if (!g.ex) g.ex = new ExecState();
+  ExecState& x = *g.ex;
+  if (x.device < 0) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    x.device = dev;
+    CK(cudaStreamCreateWithFlags(&x.side[S_H2D], cudaStreamNonBlocking), "create h2d stream");
+    CK(cudaStreamCreateWithFlags(&x.side[S_D2H], cudaStreamNonBlocking), "create d2h stream");
+    CK(cudaEventCreateWithFlags(&x.start_ev, cudaEventDisableTiming), "event create");
+    CK(cudaEventCreateWithFlags(&x.done_ev, cudaEventDisableTiming), "event create");
+  }
+  return LQC_OK;
+}
+
+void free_program(ExecState& x) {
+  if (x.graph) { cudaGraphExecDestroy(x.graph); x.graph = nullptr; }
+  for (int k = 0; k < 2; ++k) {
+    for (cudaEvent_t e : x.tev[k]) cudaEventDestroy(e);
+    x.tev[k].clear();
+    x.timing_pending[k] = false;
+  }
+  x.tev_kind.clear();
+  x.tev_flops.clear();
+  for (cudaEvent_t e : x.ev) cudaEventDestroy(e);
+  x.ev.clear();
+  if (x.arena) { cudaFree(x.arena); x.arena = nullptr; }
+  if (x.results) { cudaFree(x.results); x.results = nullptr; }
+  if (x.scratch) { cudaFree(x.scratch); x.scratch = nullptr; }
+  for (void* p : x.host_slot)
+    if (p) cudaFreeHost(p);
+  x.host_slot.clear();
+  x.host_slot_bytes.clear();
+  x.prog.clear();
+  x.cdesc.clear();
+  x.adesc.clear();
+  x.prog_valid = false;
+  x.arena_bytes = 0;
+}
+
+// Translate the op list into stream instructions with event dependencies.
+int build_program(Dag& g) {
+  ExecState& x = *g.ex;
+  free_program(x);
+  const int64_t N = (int64_t)g.nodes.size();
+  const bool staged = x.staged_valid;
+  std::vector<int64_t> off(N, -1);
+  std::vector<int32_t> last_compute(N, -1), last_h2d(N, -1), last_d2h(N, -1), writer(N, -1);
+  std::vector<int32_t> wb_instr(N, -1);  // write-back that filled the node's host slot
+  std::vector<uint8_t> waited_for_load(N, 0);
+  x.slot_of.assign(N, -1);
+  x.root_ids.clear();
+  for (int64_t u = 0; u < N; ++u)
+    if (!g.nodes[u].is_leaf() && g.nodes[u].parents.empty() && g.nodes[u].rank == 0) {
+      x.slot_of[u] = (int32_t)x.root_ids.size();
+      x.root_ids.push_back(u);
+    }
+  x.n_results = (int64_t)x.root_ids.size();
+  x.host_slot.assign(N, nullptr);
+  x.host_slot_bytes.assign(N, 0);
+  Placer pl;
+  int64_t scratch_need = 0;
+  std::vector<Instr>& P = x.prog;
+  auto add_wait = [&](Instr& in, int32_t on) {
+    if (on < 0 || P[on].stream == in.stream) return;
+    for (int k = 0; k < in.nwait; ++k)
+      if (in.wait[k] == on) return;
+    in.wait[in.nwait++] = on;
+  };
+  auto release = [&](int64_t u) {
+    if (off[u] < 0) return;
+    int32_t dep[3] = {last_compute[u], last_h2d[u], last_d2h[u]};
+    if (g.opt_poison) {
+      Instr in{};
+      in.kind = I_POISON;
+      in.stream = S_COMPUTE;
+      in.node = u;
+      in.dst = off[u];
+      in.bytes = g.size_bytes(u);
+      in.src[0] = in.src[1] = -1;
+      add_wait(in, last_d2h[u]);
+      add_wait(in, last_h2d[u]);
+      P.push_back(in);
+      x.cdesc.emplace_back();
+      x.adesc.emplace_back();
+      dep[S_COMPUTE] = (int32_t)P.size() - 1;
+    }
+    pl.release(off[u], g.size_bytes(u), dep);
+    off[u] = -1;
+  };
+  for (const Op& op : g.ops) {
+    const int64_t u = op.node;
+    const Node& n = g.nodes[u];
+    if (op.kind == OP_LOAD) {
+      if (staged && n.is_leaf()) continue;  // leaves already on the device
+      Instr in{};
+      in.kind = I_LOAD;
+      in.stream = S_H2D;
+      in.node = u;
+      in.bytes = g.size_bytes(u);
+      in.src[0] = in.src[1] = -1;
+      int32_t dep[3];
+      in.dst = pl.alloc(in.bytes, dep);
+      add_wait(in, dep[S_COMPUTE]);
+      add_wait(in, dep[S_D2H]);
+      if (!n.is_leaf()) add_wait(in, wb_instr[u]);  // reload after the write-back landed
+      off[u] = in.dst;
+      P.push_back(in);
+      x.cdesc.emplace_back();
+      x.adesc.emplace_back();
+      last_h2d[u] = (int32_t)P.size() - 1;
+      last_compute[u] = -1;
+      last_d2h[u] = -1;
+      writer[u] = -1;
+      waited_for_load[u] = 0;
+    } else if (op.kind == OP_EVICT) {
+      if (op.flag) {
+        Instr in{};
+        in.kind = I_WRITEBACK;
+        in.stream = S_D2H;
+        in.node = u;
+        in.bytes = g.size_bytes(u);
+        in.dst = -1;
+        in.src[0] = off[u];
+        in.src[1] = -1;
+        add_wait(in, writer[u]);
+        P.push_back(in);
+        x.cdesc.emplace_back();
+        x.adesc.emplace_back();
+        last_d2h[u] = (int32_t)P.size() - 1;
+        wb_instr[u] = last_d2h[u];
+        x.host_slot_bytes[u] = in.bytes;
+      }
+      release(u);
+    } else if (op.kind == OP_FREE) {
+      release(u);
+    } else {  // CONTRACT
+      Instr in{};
+      in.stream = S_COMPUTE;
+      in.node = u;
+      in.bytes = g.size_bytes(u);
+      for (int k = 0; k < 2; ++k) {
+        int64_t c = n.child(k);
+        const Node& cn = g.nodes[c];
+        if (staged && cn.is_leaf()) {
+          in.src[k] = -2;
+        } else {
+          in.src[k] = off[c];
+          if (last_h2d[c] >= 0 && !waited_for_load[c]) {
+            add_wait(in, last_h2d[c]);
+            waited_for_load[c] = 1;
+          }
+        }
+      }
+      const Node& L = g.nodes[n.left];
+      const Node& R = g.nodes[n.right];
+      std::string err;
+      ContractDesc cd{};
+      ContractAllDesc ad{};
+      if (n.rank == 0) {
+        in.kind = I_CONTRACT_ALL;
+        in.dst = -1;
+        in.root_slot = x.slot_of[u];
+        if (!make_contract_all_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, g.lt,
+                                    &ad, &err)) {
+          g.err = err;
+          return LQC_ERR_ARG;
+        }
+        scratch_need = std::max(scratch_need, contract_all_scratch_bytes(ad));
+      } else {
+        in.kind = I_CONTRACT;
+        if (!make_contract_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, g.lt, &cd,
+                                &err)) {
+          g.err = err;
+          return LQC_ERR_ARG;
+        }
+        int32_t dep[3];
+        in.dst = pl.alloc(in.bytes, dep);
+        add_wait(in, dep[S_H2D]);
+        add_wait(in, dep[S_D2H]);
+        off[u] = in.dst;
+      }
+      P.push_back(in);
+      x.cdesc.push_back(cd);
+      x.adesc.push_back(ad);
+      const int32_t me = (int32_t)P.size() - 1;
+      for (int k = 0; k < n.n_children(); ++k) last_compute[n.child(k)] = me;
+      if (n.rank != 0) {
+        last_compute[u] = me;
+        writer[u] = me;
+        last_h2d[u] = -1;
+        last_d2h[u] = -1;
+      }
+    }
+  }
+  // event slots for every instruction somebody waits on
+  std::vector<int32_t> slot(P.size(), -1);
+  int32_t n_ev = 0;
+  for (Instr& in : P)
+    for (int k = 0; k < in.nwait; ++k) {
+      int32_t j = in.wait[k];
+      if (slot[j] < 0) slot[j] = n_ev++;
+    }
+  for (size_t j = 0; j < P.size(); ++j) P[j].rec = slot[j];
+  for (Instr& in : P)
+    for (int k = 0; k < in.nwait; ++k) in.wait[k] = slot[in.wait[k]];
+  x.ev.resize(n_ev, nullptr);
+  for (int32_t k = 0; k < n_ev; ++k)
+    CK(cudaEventCreateWithFlags(&x.ev[k], cudaEventDisableTiming), "event create");
+  if (g.opt_timing) {
+    for (size_t j = 0; j < P.size(); ++j) {
+      if (P[j].kind != I_CONTRACT && P[j].kind != I_CONTRACT_ALL) continue;
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t b, e;
+        CK(cudaEventCreate(&b), "timing event");
+        CK(cudaEventCreate(&e), "timing event");
+        x.tev[k].push_back(b);
+        x.tev[k].push_back(e);
+      }
+      x.tev_kind.push_back(P[j].kind);
+      const ContractDesc& cd = x.cdesc[j];
+      const ContractAllDesc& ad = x.adesc[j];
+      x.tev_flops.push_back(P[j].kind == I_CONTRACT ? 8 * cd.lt * cd.M * cd.N * cd.K
+                                                      : 8 * ad.lt * ad.S);
+    }
+  }
+  x.arena_bytes = pl.top;
+  if (x.arena_bytes > 0) CK(cudaMalloc((void**)&x.arena, (size_t)x.arena_bytes), "arena cudaMalloc");
+  if (x.n_results > 0)
+    CK(cudaMalloc((void**)&x.results, (size_t)(x.n_results * g.lt * 16)), "results cudaMalloc");
+  x.scratch_bytes = scratch_need;
+  if (scratch_need > 0) CK(cudaMalloc((void**)&x.scratch, (size_t)scratch_need), "scratch cudaMalloc");
+  for (int64_t u = 0; u < N; ++u)
+    if (x.host_slot_bytes[u] > 0)
+      CK(cudaHostAlloc(&x.host_slot[u], (size_t)x.host_slot_bytes[u], cudaHostAllocDefault),
+         "pinned write-back slot");
+  x.prog_valid = true;
+  x.tset = 0;
+  g.info.n_contract = g.info.n_contract_all = 0;
+  g.info.ms_contract = g.info.ms_contract_all = 0.0;
+  g.info.flops_contract = g.info.flops_contract_all = 0;
+  return LQC_OK;
+}
+
+// Issue the program on the streams (also used under graph capture).
+int issue(Dag& g, cudaStream_t cs) {
+  ExecState& x = *g.ex;
+  cudaStream_t st[3] = {cs, x.side[S_H2D], x.side[S_D2H]};
+  // side streams start after everything already queued on the compute stream
+  CK(cudaEventRecord(x.start_ev, cs), "record start");
+  CK(cudaStreamWaitEvent(st[S_H2D], x.start_ev, 0), "wait start");
+  CK(cudaStreamWaitEvent(st[S_D2H], x.start_ev, 0), "wait start");
+  x.flops = 0;
+  x.copy_h2d = x.copy_d2h = 0;
+  x.n_kernels = 0;
+  lqc_stats c{};
+  size_t tk = 0;  // timing pair cursor
+  for (size_t j = 0; j < x.prog.size(); ++j) {
+    const Instr& in = x.prog[j];
+    cudaStream_t s = st[in.stream];
+    for (int k = 0; k < in.nwait; ++k) CK(cudaStreamWaitEvent(s, x.ev[in.wait[k]], 0), "wait");
+    const Node& n = g.nodes[in.node];
+    switch (in.kind) {
+      case I_LOAD: {
+        const void* src = n.is_leaf() ? n.host : x.host_slot[in.node];
+        CK(cudaMemcpyAsync(x.arena + in.dst, src, (size_t)in.bytes, cudaMemcpyHostToDevice, s),
+           "H2D load");
+        x.copy_h2d += in.bytes;
+        c.n_h2d++;
+        c.h2d_bytes += in.bytes;
+        break;
+      }
+      case I_WRITEBACK: {
+        CK(cudaMemcpyAsync(x.host_slot[in.node], x.arena + in.src[0], (size_t)in.bytes,
+                           cudaMemcpyDeviceToHost, s),
+           "D2H write-back");
+        x.copy_d2h += in.bytes;
+        c.n_d2h++;
+        c.d2h_bytes += in.bytes;
+        break;
+      }
+      case I_POISON: {
+        if (launch_fill_nan(x.arena + in.dst, in.bytes, s) < 0)
+          return cuda_fail(g, cudaGetLastError(), "poison launch");
+        x.n_kernels += 1;
+        break;
+      }
+      case I_CONTRACT:
+      case I_CONTRACT_ALL: {
+        const void* op[2];
+        for (int k = 0; k < 2; ++k) {
+          int64_t ch = n.child(k);
+          op[k] = in.src[k] == -2 ? x.staged[ch] : (const void*)(x.arena + in.src[k]);
+        }
+        int nk;
+        const bool timed = g.opt_timing && tk < x.tev_kind.size();
+        if (timed) CK(cudaEventRecord(x.tev[x.tset][2 * tk], s), "timing record");
+        if (in.kind == I_CONTRACT) {
+          const ContractDesc& d = x.cdesc[j];
+          nk = launch_contract_fp64(d, (const double*)op[0], (const double*)op[1],
+                                    (double*)(x.arena + in.dst), s);
+          x.flops += 8 * d.lt * d.M * d.N * d.K;
+        } else {
+          const ContractAllDesc& d = x.adesc[j];
+          nk = launch_contract_all_fp64(d, (const double*)op[0], (const double*)op[1],
+                                        x.results + 2 * g.lt * in.root_slot, x.scratch, s);
+          x.flops += 8 * d.lt * d.S;
+        }
+        if (nk < 0) return cuda_fail(g, cudaGetLastError(), "contraction launch");
+        if (timed) {
+          CK(cudaEventRecord(x.tev[x.tset][2 * tk + 1], s), "timing record");
+          ++tk;
+        }
+        x.n_kernels += nk;
+        break;
+      }
+    }
+    if (in.rec >= 0) CK(cudaEventRecord(x.ev[in.rec], s), "record");
+  }
+  // join the side streams back into the compute stream
+  for (int k = 1; k < 3; ++k) {
+    CK(cudaEventRecord(x.start_ev, st[k]), "record join");
+    CK(cudaStreamWaitEvent(cs, x.start_ev, 0), "wait join");
+  }
+  // counted figures of the walk (evictions and peaks come from the plan)
+  c.n_evict = g.planned.n_evict;
+  c.peak_exec = g.planned.peak_exec;
+  c.peak_paper = g.planned.peak_paper;
+  // with staged leaves the leaf loads are served on the device: c counts
+  // only what really crossed the host link
+  x.counted = c;
+  return LQC_OK;
+}
+
+}  // namespace
+
+int host_store_alloc(Dag& g, int64_t leaf, std::string* err) {
+  Node& n = g.nodes[leaf];
+  if (n.host) return LQC_OK;
+  const size_t bytes = (size_t)(g.lt * n.elems * g.elem_bytes);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) == cudaSuccess) {
+    n.host = p;
+    n.host_pinned = true;
+    return LQC_OK;
+  }
+  cudaGetLastError();  // no device (or pinned memory exhausted): pageable store
+  p = std::malloc(bytes);
+  if (!p) {
+    *err = "host store allocation failed";
+    return LQC_ERR_HOST_MEM;
+  }
+  n.host = p;
+  n.host_pinned = false;
+  return LQC_OK;
+}
+
+void host_store_free(Node& n) {
+  if (!n.host) return;
+  if (n.host_pinned) cudaFreeHost(n.host);
+  else std::free(n.host);
+  n.host = nullptr;
+}
+
+void exec_invalidate_plan(Dag& g) {
+  if (!g.ex) return;
+  exec_wait(g, 60000);
+  free_program(*g.ex);
+}
+
+namespace {
+int collect_set(Dag& g, int set) {
+  ExecState& x = *g.ex;
+  const std::vector<cudaEvent_t>& ev = x.tev[set];
+  if (ev.empty()) return LQC_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {  // bounded wait for the set's last event
+    cudaError_t e = cudaEventQuery(ev.back());
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(g, e, "timing wait");
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) {
+      g.err = "timing events not complete after the wait limit";
+      return LQC_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  for (size_t k = 0; k < x.tev_kind.size(); ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]), "timing elapsed");
+    if (x.tev_kind[k] == I_CONTRACT) {
+      g.info.n_contract++;
+      g.info.ms_contract += ms;
+      g.info.flops_contract += x.tev_flops[k];
+    } else {
+      g.info.n_contract_all++;
+      g.info.ms_contract_all += ms;
+      g.info.flops_contract_all += x.tev_flops[k];
+    }
+  }
+  x.timing_pending[set] = false;
+  return LQC_OK;
+}
+}  // namespace
+
+int exec_run(Dag& g, void* stream) {
+  int rc = ensure_state(g);
+  if (rc != LQC_OK) return rc;
+  ExecState& x = *g.ex;
+  for (const Op& op : g.ops)
+    if (op.kind == OP_LOAD && g.nodes[op.node].is_leaf() && !g.nodes[op.node].host &&
+        !x.staged_valid) {
+      g.err = "leaf " + std::to_string(op.node) + " has no data";
+      return LQC_ERR_STATE;
+    }
+  if (!x.prog_valid) {
+    rc = build_program(g);
+    if (rc != LQC_OK) {
+      free_program(x);
+      return rc;
+    }
+  }
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (g.opt_timing && x.timing_pending[x.tset]) {
+    rc = collect_set(g, x.tset);  // the execute two steps back: normally long done
+    if (rc != LQC_OK) return rc;
+  }
+  if (g.opt_graph) {
+    if (!x.graph || x.graph_stream != cs) {
+      if (x.graph) { cudaGraphExecDestroy(x.graph); x.graph = nullptr; }
+      cudaStream_t cap = cs;
+      bool own = false;
+      if (cap == nullptr) {  // the legacy stream cannot be captured
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        own = true;
+      }
+      CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+      rc = issue(g, cap);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cap, &graph);
+      if (rc != LQC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        if (own) cudaStreamDestroy(cap);
+        return rc;
+      }
+      if (e != cudaSuccess) {
+        if (own) cudaStreamDestroy(cap);
+        return cuda_fail(g, e, "end capture");
+      }
+      e = cudaGraphInstantiate(&x.graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (own) cudaStreamDestroy(cap);
+      if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+      x.graph_stream = cs;
+    }
+    CK(cudaGraphLaunch(x.graph, cs), "graph launch");
+  } else {
+    rc = issue(g, cs);
+    if (rc != LQC_OK) return rc;
+  }
+  CK(cudaEventRecord(x.done_ev, cs), "record done");
+  x.ran = true;
+  if (g.opt_timing && !x.tev_kind.empty()) {
+    x.timing_pending[x.tset] = true;
+    x.tset ^= 1;
+  }
+  g.measured = x.counted;
+  g.info.n_kernels = x.n_kernels;
+  g.info.flops = x.flops;
+  g.info.arena_bytes = x.arena_bytes;
+  g.info.copied_h2d = x.copy_h2d;
+  g.info.copied_d2h = x.copy_d2h;
+  g.info.n_ops = (int64_t)g.ops.size();
+  g.executed = true;
+  return LQC_OK;
+}
+
+int exec_wait(Dag& g, int64_t timeout_ms) {
+  if (!g.ex || !g.ex->ran) return LQC_OK;
+  ExecState& x = *g.ex;
+  auto t0 = std::chrono::steady_clock::now();
+  int sleep_us = 20;
+  while (true) {
+    cudaError_t e = cudaEventQuery(x.done_ev);
+    if (e == cudaSuccess) return LQC_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(g, e, "execution failed");
+    auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                  std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) {
+      g.err = "execution still running after the wait limit";
+      return LQC_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+    sleep_us = std::min(sleep_us * 2, 2000);
+  }
+}
+
+int exec_collect_timing(Dag& g) {
+  if (!g.ex) return LQC_OK;
+  ExecState& x = *g.ex;
+  // older set first (the one the next execute would reuse), then the newer
+  for (int k = 0; k < 2; ++k) {
+    int set = x.tset ^ (k == 0 ? 0 : 1);
+    if (!x.timing_pending[set]) continue;
+    int rc = collect_set(g, set);
+    if (rc != LQC_OK) return rc;
+  }
+  return LQC_OK;
+}
+
+int exec_read(Dag& g, int64_t root, double* out) {
+  if (root < 0 || root >= (int64_t)g.nodes.size()) {
+    g.err = "root id out of range";
+    return LQC_ERR_ARG;
+  }
+  if (!g.executed || !g.ex || !g.ex->results) {
+    g.err = "not executed";
+    return LQC_ERR_STATE;
+  }
+  ExecState& x = *g.ex;
+  if (x.slot_of[root] < 0) {
+    g.err = "node is not a rank-0 root";
+    return LQC_ERR_ARG;
+  }
+  int rc = exec_wait(g, 60000);
+  if (rc != LQC_OK) return rc;
+  CK(cudaMemcpy(out, x.results + 2 * g.lt * x.slot_of[root], (size_t)(g.lt * 16),
+                cudaMemcpyDeviceToHost),
+     "read correlator");
+  return LQC_OK;
+}
+
+int exec_read_all(Dag& g, double* out, int64_t cap) {
+  if (!g.executed || !g.ex) {
+    g.err = "not executed";
+    return LQC_ERR_STATE;
+  }
+  ExecState& x = *g.ex;
+  if (cap < x.n_results * 2 * g.lt) {
+    g.err = "output capacity too small";
+    return LQC_ERR_ARG;
+  }
+  int rc = exec_wait(g, 60000);
+  if (rc != LQC_OK) return rc;
+  if (x.n_results > 0)
+    CK(cudaMemcpy(out, x.results, (size_t)(x.n_results * g.lt * 16), cudaMemcpyDeviceToHost),
+       "read correlators");
+  return LQC_OK;
+}
+
+int exec_stage_leaves(Dag& g, void* stream) {
+  int rc = ensure_state(g);
+  if (rc != LQC_OK) return rc;
+  ExecState& x = *g.ex;
+  rc = exec_wait(g, 60000);
+  if (rc != LQC_OK) return rc;
+  exec_unstage_leaves(g);
+  const int64_t N = (int64_t)g.nodes.size();
+  x.staged.assign(N, nullptr);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int64_t u = 0; u < N; ++u) {
+    Node& n = g.nodes[u];
+    if (!n.is_leaf() || n.parents.empty()) continue;
+    if (!n.host) {
+      g.err = "leaf " + std::to_string(u) + " has no data";
+      exec_unstage_leaves(g);
+      return LQC_ERR_STATE;
+    }
+    size_t bytes = (size_t)g.size_bytes(u);
+    CK(cudaMalloc(&x.staged[u], bytes), "staged leaf cudaMalloc");
+    CK(cudaMemcpyAsync(x.staged[u], n.host, bytes, cudaMemcpyHostToDevice, s), "stage leaf");
+  }
+  CK(cudaStreamSynchronize(s), "stage sync");
+  x.staged_valid = true;
+  free_program(x);
+  return LQC_OK;
+}
+
+int exec_unstage_leaves(Dag& g) {
+  if (!g.ex) return LQC_OK;
+  ExecState& x = *g.ex;
+  exec_wait(g, 60000);
+  for (void* p : x.staged)
+    if (p) cudaFree(p);
+  x.staged.clear();
+  if (x.staged_valid) {
+    x.staged_valid = false;
+    free_program(x);
+  }
+  return LQC_OK;
+}
+
+void exec_destroy(Dag& g) {
+  if (!g.ex) return;
+  ExecState& x = *g.ex;
+  if (x.ran) exec_wait(g, 60000);
+  exec_unstage_leaves(g);
+  free_program(x);
+  for (int k = 1; k < 3; ++k)
+    if (x.side[k]) cudaStreamDestroy(x.side[k]);
+  if (x.start_ev) cudaEventDestroy(x.start_ev);
+  if (x.done_ev) cudaEventDestroy(x.done_ev);
+  delete g.ex;
+  g.ex = nullptr;
+}
+
+}  // namespace lqc

@@ -1,0 +1,371 @@
+// Contraction orders: naive topological order, the sibling scheduler
+// (Sec. III-A, Alg. 1 SB-SCHEDULER, Alg. 2 SB-PROCESS, Alg. 3 SB-PROP-DOWN)
+// and the tree scheduler (Sec. III-B, Alg. 4 TR-SCHEDULER, Alg. 5 TR-INIT,
+// Alg. 6 PROCESS-CTREE, Alg. 7 PROCESS-CHILD, Alg. 8 PROCESS-NODE).
+//
+// Each scheduler returns the order of the non-leaf nodes.  Deterministic
+// readings of the points the paper leaves open:
+//  * sibling: the "random" WAITING leaf is the smallest-id WAITING leaf that
+//    has a consumer; queues are FIFO; parents are visited in ascending id;
+//    children and parents are sets of distinct nodes.
+//  * tree: T_i = descendant closure of the i-th root (ascending root id);
+//    the initial tgain is the sum of the individual gains (the text's
+//    definition); ties of max tgain go to the smallest tree index;
+//    PROCESS-CHILD updates x.outAv (the printed "v.outAv" is a typo); the
+//    nodes of a tree are visited by a post-order walk from its root, left
+//    operand first, skipping nodes (and their sub-trees) that an earlier
+//    tree already processed.
+#include <pthread.h>
+
+#include <algorithm>
+#include <deque>
+#include <queue>
+#include <stdexcept>
+
+#include "internal.hpp"
+
+namespace lqc {
+
+std::vector<int64_t> schedule_naive(const Dag& g) {
+  std::vector<int64_t> o;
+  for (int64_t u = 0; u < (int64_t)g.nodes.size(); ++u)
+    if (!g.nodes[u].is_leaf()) o.push_back(u);
+  return o;
+}
+
+// ---------------------------------------------------------------- sibling
+namespace {
+
+enum SibState : uint8_t { SB_WAITING, SB_QUEUED, SB_INMEM, SB_RELEASED };
+
+struct Sibling {
+  const Dag& g;
+  std::vector<int32_t> rank;
+  std::vector<int32_t> rs, rp;
+  std::vector<uint8_t> st;
+  std::vector<std::deque<int64_t>> Q;  // Q[r]: contractions of rank r
+  std::vector<int64_t> order;
+  bool failed = false;
+
+  explicit Sibling(const Dag& d) : g(d) {}
+
+  void process(int64_t u) {  // Alg. 2
+    const Node& n = g.nodes[u];
+    if (!n.is_leaf()) order.push_back(u);  // perform the contraction
+    st[u] = SB_INMEM;
+    if (!n.is_leaf()) {
+      for (int c = 0; c < n.n_children(); ++c) {
+        int64_t v = n.child(c);
+        if (--rs[v] == 0) st[v] = SB_RELEASED;
+      }
+      if (n.parents.empty()) st[u] = SB_RELEASED;  // ROOT
+    }
+    for (int64_t v : n.parents) {
+      --rp[v];
+      if (rp[v] == 1) {
+        const Node& pv = g.nodes[v];
+        int64_t w = (pv.left == u) ? pv.right : pv.left;  // the sibling of u
+        if (st[w] == SB_WAITING) prop_down(w);
+      } else if (rp[v] == 0) {
+        Q[rank[v]].push_back(v);
+        st[v] = SB_QUEUED;
+      }
+    }
+  }
+
+  void prop_down(int64_t u) {  // Alg. 3
+    if (st[u] != SB_WAITING) return;
+    const Node& n = g.nodes[u];
+    if (n.is_leaf()) {
+      process(u);
+      return;
+    }
+    prop_down(n.left);
+    prop_down(n.right);
+  }
+
+  void run() {  // Alg. 1
+    const int64_t N = (int64_t)g.nodes.size();
+    rank.assign(N, 0);
+    rs.assign(N, 0);
+    rp.assign(N, 0);
+    st.assign(N, SB_WAITING);
+    int32_t q = 0;
+    int64_t n_contr = 0;
+    std::vector<int64_t> leaves;
+    for (int64_t u = 0; u < N; ++u) {
+      const Node& n = g.nodes[u];
+      rs[u] = (int32_t)n.parents.size();
+      rp[u] = n.n_children();
+      if (n.is_leaf()) {
+        if (!n.parents.empty()) leaves.push_back(u);
+      } else {
+        int32_t r = 0;
+        for (int c = 0; c < n.n_children(); ++c) r = std::max(r, rank[n.child(c)]);
+        rank[u] = r + 1;  // Eq. (1)
+        q = std::max(q, rank[u]);
+        ++n_contr;
+      }
+    }
+    Q.assign(q + 1, std::deque<int64_t>());
+    size_t leaf_ptr = 0;
+    while ((int64_t)order.size() < n_contr) {
+      int32_t top = -1;
+      for (int32_t r = q; r >= 1; --r)
+        if (!Q[r].empty()) { top = r; break; }
+      int64_t u;
+      if (top < 0) {
+        while (leaf_ptr < leaves.size() && st[leaves[leaf_ptr]] != SB_WAITING) ++leaf_ptr;
+        if (leaf_ptr >= leaves.size()) { failed = true; return; }
+        u = leaves[leaf_ptr];
+      } else {
+        u = Q[top].front();
+        Q[top].pop_front();
+      }
+      process(u);
+    }
+  }
+};
+
+void* sibling_thread(void* p) {
+  Sibling* s = static_cast<Sibling*>(p);
+  try {
+    s->run();
+  } catch (...) {
+    s->failed = true;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+std::vector<int64_t> schedule_sibling(const Dag& g) {
+  // The paper's routines recurse (PROCESS -> PROP-DOWN -> PROCESS ...); the
+  // depth grows with the sharing in the DAG, so run them on a thread with a
+  // large stack.
+  Sibling s(g);
+  pthread_attr_t attr;
+  pthread_attr_init(&attr);
+  pthread_attr_setstacksize(&attr, (size_t)1 << 30);
+  pthread_t th;
+  if (pthread_create(&th, &attr, sibling_thread, &s) != 0) {
+    pthread_attr_destroy(&attr);
+    throw std::runtime_error("sibling scheduler: cannot start worker thread");
+  }
+  pthread_join(th, nullptr);
+  pthread_attr_destroy(&attr);
+  if (s.failed) throw std::runtime_error("sibling scheduler failed");
+  return s.order;
+}
+
+// ------------------------------------------------------------------- tree
+namespace {
+
+enum TrState : uint8_t { TR_AVAIL, TR_INMEM, TR_RELEASED };
+
+struct TreeSched {
+  const Dag& g;
+  int64_t N = 0;
+  int32_t K = 0;
+  std::vector<int64_t> root;                  // root of tree i
+  std::vector<std::vector<int32_t>> ctree;    // u.ctree, ascending
+  std::vector<std::vector<int64_t>> igain;    // T_i.u.igain aligned with ctree[u]
+  std::vector<int64_t> cgain, tgain;
+  std::vector<uint8_t> state;
+  std::vector<int64_t> outav;                 // |u.outAv|
+  struct Ent {
+    int32_t tree;
+    int32_t tau;
+    int32_t delta;
+    uint8_t inpred;  // u in T_tree.pred
+  };
+  std::vector<std::vector<Ent>> S;            // tau/delta of u, set by PROCESS-NODE
+  std::vector<int32_t> slot_of;               // scratch: tree -> index in S[u]
+  std::vector<int64_t> slot_owner;
+  std::vector<uint8_t> alive, dirty_flag;
+  std::vector<int32_t> dirty;
+  std::vector<int64_t> visit_stamp;
+  std::vector<int64_t> order;
+
+  explicit TreeSched(const Dag& d) : g(d) {}
+
+  bool in_tree(int64_t u, int32_t i) const {
+    const auto& c = ctree[u];
+    return std::binary_search(c.begin(), c.end(), i);
+  }
+  void touch(int32_t i) {
+    if (!dirty_flag[i]) { dirty_flag[i] = 1; dirty.push_back(i); }
+  }
+
+  void init() {  // Alg. 5 TR-INIT
+    N = (int64_t)g.nodes.size();
+    for (int64_t u = 0; u < N; ++u)
+      if (!g.nodes[u].is_leaf() && g.nodes[u].parents.empty()) root.push_back(u);
+    K = (int32_t)root.size();
+    ctree.assign(N, {});
+    igain.assign(N, {});
+    state.assign(N, TR_AVAIL);
+    outav.assign(N, 0);
+    for (int64_t u = 0; u < N; ++u) outav[u] = (int64_t)g.nodes[u].parents.size();
+    cgain.assign(K, 0);
+    tgain.assign(K, 0);
+    std::vector<int64_t> mark(N, -1), stack;
+    for (int32_t i = 0; i < K; ++i) {  // u.ctree: descendant closure of each root
+      stack.clear();
+      stack.push_back(root[i]);
+      mark[root[i]] = i;
+      while (!stack.empty()) {
+        int64_t u = stack.back();
+        stack.pop_back();
+        ctree[u].push_back(i);
+        const Node& n = g.nodes[u];
+        for (int c = 0; c < n.n_children(); ++c) {
+          int64_t v = n.child(c);
+          if (mark[v] != i) { mark[v] = i; stack.push_back(v); }
+        }
+      }
+    }
+    // individual gains: g(u, T_i) = |outAv(u)| - #{parents of u in T_i}
+    for (int64_t u = 0; u < N; ++u) {
+      const auto& cu = ctree[u];
+      igain[u].assign(cu.size(), 0);
+      for (size_t k = 0; k < cu.size(); ++k) {
+        int64_t gcount = (int64_t)g.nodes[u].parents.size();
+        for (int64_t v : g.nodes[u].parents)
+          if (in_tree(v, cu[k])) --gcount;
+        igain[u][k] = gcount == 0 ? 0 : -g.size_bytes(u);
+        tgain[cu[k]] += igain[u][k];
+      }
+    }
+    S.assign(N, {});
+    slot_of.assign(K, -1);
+    slot_owner.assign(K, -1);
+    alive.assign(K, 1);
+    dirty_flag.assign(K, 0);
+    visit_stamp.assign(N, -1);
+  }
+
+  void process_child(int64_t u, int64_t x) {  // Alg. 7
+    const int64_t sz = g.size_bytes(x);
+    for (Ent& e : S[x]) {
+      if (!e.inpred) continue;
+      if (in_tree(u, e.tree)) {  // cases 1a-1c
+        if (e.tau == 1 && e.delta == 0) {
+          cgain[e.tree] -= sz;
+          tgain[e.tree] -= sz;
+          touch(e.tree);
+        }
+        if (--e.tau == 0) e.inpred = 0;
+      } else {  // cases 2a-2b
+        if (e.delta == 1) {
+          cgain[e.tree] += sz;
+          tgain[e.tree] += sz;
+          touch(e.tree);
+        }
+        --e.delta;
+      }
+    }
+    if (--outav[x] == 0) state[x] = TR_RELEASED;
+  }
+
+  void process_node(int64_t u) {  // Alg. 8
+    const int64_t sz = g.size_bytes(u);
+    const auto& cu = ctree[u];
+    for (size_t k = 0; k < cu.size(); ++k) {
+      if (igain[u][k] != 0) {
+        tgain[cu[k]] -= igain[u][k];
+        touch(cu[k]);
+      }
+    }
+    // every consumer of an AVAIL node is AVAIL, so u.outAv = u.parents here
+    const int32_t n_out = (int32_t)outav[u];
+    std::vector<Ent>& su = S[u];
+    su.clear();
+    for (int64_t v : g.nodes[u].parents) {
+      for (int32_t i : ctree[v]) {
+        if (slot_owner[i] != u) {
+          slot_owner[i] = u;
+          slot_of[i] = (int32_t)su.size();
+          su.push_back(Ent{i, 0, n_out, 1});
+        }
+        Ent& e = su[slot_of[i]];
+        --e.delta;
+        ++e.tau;
+      }
+    }
+    for (Ent& e : su) {
+      if (e.delta == 0) {
+        cgain[e.tree] += sz;
+        tgain[e.tree] += sz;
+        touch(e.tree);
+      }
+    }
+    state[u] = outav[u] == 0 ? TR_RELEASED : TR_INMEM;
+  }
+
+  void process_ctree(int32_t i) {  // Alg. 6
+    // post-order from the root, left operand first, AVAIL nodes only
+    struct Frame { int64_t u; int c; };
+    std::vector<Frame> st;
+    int64_t r = root[i];
+    if (state[r] != TR_AVAIL) return;
+    visit_stamp[r] = i;
+    st.push_back({r, 0});
+    while (!st.empty()) {
+      Frame& f = st.back();
+      const Node& n = g.nodes[f.u];
+      if (f.c < n.n_children()) {
+        int64_t v = n.child(f.c++);
+        if (state[v] == TR_AVAIL && visit_stamp[v] != i) {
+          visit_stamp[v] = i;
+          st.push_back({v, 0});
+        }
+        continue;
+      }
+      int64_t u = f.u;
+      st.pop_back();
+      if (!n.is_leaf())
+        for (int c = 0; c < n.n_children(); ++c) process_child(u, n.child(c));
+      process_node(u);
+      if (!n.is_leaf()) order.push_back(u);
+    }
+  }
+
+  void run() {  // Alg. 4
+    init();
+    // max-heap on (tgain, -index) with lazy invalidation
+    typedef std::pair<int64_t, int32_t> E;
+    auto cmp = [](const E& a, const E& b) {
+      if (a.first != b.first) return a.first < b.first;
+      return a.second > b.second;
+    };
+    std::priority_queue<E, std::vector<E>, decltype(cmp)> heap(cmp);
+    for (int32_t i = 0; i < K; ++i) heap.push({tgain[i], i});
+    for (int32_t step = 0; step < K; ++step) {
+      for (int32_t i : dirty) {
+        dirty_flag[i] = 0;
+        if (alive[i]) heap.push({tgain[i], i});
+      }
+      dirty.clear();
+      int32_t best = -1;
+      while (!heap.empty()) {
+        E e = heap.top();
+        heap.pop();
+        if (alive[e.second] && e.first == tgain[e.second]) { best = e.second; break; }
+      }
+      if (best < 0) throw std::runtime_error("tree scheduler: empty selection");
+      alive[best] = 0;
+      process_ctree(best);
+    }
+  }
+};
+
+}  // namespace
+
+std::vector<int64_t> schedule_tree(const Dag& g) {
+  TreeSched t(g);
+  t.run();
+  return t.order;
+}
+
+}  // namespace lqc

@@ -1,0 +1,166 @@
+"""The native schedulers and planner (C ABI) against the oracle, bit-exact.
+
+* orders of naive / sibling / tree identical to the oracle's on random DAGs
+  and on every synthetic workload;
+* planned op lists and every figure (peak_paper, peak_exec, evictions,
+  H2D/D2H counts and bytes) identical to the oracle's replay, for every
+  topological order of tiny DAGs (exhaustive enumeration) under several
+  budgets and both eviction policies;
+* DAG build: merging of identical requests gives the oracle's node ids.
+No GPU is needed: leaves are registered without data.
+"""
+import pytest
+
+import synth
+from oracle import dag as D
+from oracle import memory as M
+from oracle import schedule as S
+from oracle.enumerate import topological_orders
+from tests.dagutil import random_spec
+
+L = pytest.importorskip("paper_2511_02257_b300")
+
+POL = {"naive": "naive", "sibling": "sibling", "tree": "tree"}
+EV = {M.LRU: "lru", M.NEXT_USE: "next_use"}
+STAT_KEYS = ("peak_paper", "peak_exec", "n_evict", "n_h2d", "n_d2h", "h2d_bytes", "d2h_bytes")
+
+
+def native_from_spec(lt, leaves, contr):
+    d = L.Dag(lt)
+    for ext in leaves:
+        d.add_leaf(ext)
+    for (l, r, la, ra) in contr:
+        d.add_contraction(l, r, la, ra)
+    return d
+
+
+def stats_tuple(st):
+    return tuple(st[k] for k in STAT_KEYS)
+
+
+def test_library_exports_every_header_symbol():
+    import ctypes
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "lqc.h")).read()
+    names = set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(lqc_\w+)\s*\(", hdr, re.M))
+    assert len(names) >= 25
+    lib = ctypes.CDLL(L.library_path)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_dedup_ids_match_oracle(seed):
+    lt, leaves, contr = random_spec(seed, n_leaves=5, n_contr=12)
+    contr = contr + contr[: len(contr) // 2]   # repeated requests merge
+    od = D.from_spec(lt, leaves, contr)
+    nd = native_from_spec(lt, leaves, contr)
+    assert nd.num_nodes() == len(od.nodes)
+    for u in range(len(od.nodes)):
+        info = nd.node_info(u)
+        assert info["size"] == od.size(u)
+        assert info["is_leaf"] == od.nodes[u].is_leaf
+        assert info["rank"] == len(od.nodes[u].extents)
+
+
+@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("sched", ["naive", "sibling", "tree"])
+def test_orders_bit_exact_random(seed, sched):
+    lt, leaves, contr = random_spec(500 + seed, n_leaves=6, n_contr=16, share=0.7)
+    od = D.from_spec(lt, leaves, contr)
+    nd = native_from_spec(lt, leaves, contr)
+    nd.schedule(POL[sched])
+    assert nd.order() == S.SCHEDULERS[sched](od)
+
+
+@pytest.mark.parametrize("name", ["tiny", "multi_meson", "memory_pressure", "baryon"])
+def test_orders_and_plans_bit_exact_workloads(name):
+    wl = synth.make_workload(name)
+    od, _ = D.build_from_workload(wl)
+    nd, ids = L.build_dag(wl, with_data=False)
+    assert nd.num_nodes() == len(od.nodes)
+    budget = wl.budget_bytes or None
+    for sched in ("naive", "sibling", "tree"):
+        order = S.SCHEDULERS[sched](od)
+        for pol in (M.LRU, M.NEXT_USE):
+            st = nd.schedule(POL[sched], EV[pol], budget or 0)
+            assert nd.order() == order, (name, sched)
+            plan = M.replay(od, order, budget=budget, policy=pol)
+            assert stats_tuple(st) == plan.stats.as_tuple(), (name, sched, pol)
+            got = nd.plan()
+            assert len(got) == len(plan.ops)
+            assert got == [(k, u, f) for (k, u, f) in plan.ops]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_plans_bit_exact_exhaustive(seed):
+    lt, leaves, contr = random_spec(2000 + seed, n_leaves=5, n_contr=7, share=0.6)
+    od = D.from_spec(lt, leaves, contr)
+    nd = native_from_spec(lt, leaves, contr)
+    n_orders = 0
+    for order in topological_orders(od):
+        n_orders += 1
+        free = M.replay(od, order)
+        need = max(sum(od.size(x) for x in od.nodes[c].children) + od.size(c) for c in order)
+        for budget in sorted({None, need, (need + free.stats.peak_exec) // 2}, key=lambda b: b or 0):
+            for pol in (M.LRU, M.NEXT_USE):
+                plan = M.replay(od, order, budget=budget, policy=pol)
+                st = nd.set_order(order, EV[pol], budget or 0)
+                assert stats_tuple(st) == plan.stats.as_tuple()
+                assert nd.plan() == [(k, u, f) for (k, u, f) in plan.ops]
+        # one byte below the largest single-step need: budget error on both sides
+        with pytest.raises(M.BudgetError):
+            M.replay(od, order, budget=need - 1)
+        with pytest.raises(L.LqcError) as ei:
+            nd.set_order(order, "lru", need - 1)
+        assert ei.value.code == L.LQC_ERR_BUDGET
+        if n_orders >= 150:
+            break
+
+
+def test_table1_schedules_native():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table1.json")))
+    from tests.test_oracle_memory import _named_dag, UNIT
+    od, idx, names = _named_dag(g)
+    lt = 1
+    nd = native_from_spec(lt, [od.nodes[u].extents for u in range(4)],
+                          [(od.nodes[u].left, od.nodes[u].right, od.nodes[u].la, od.nodes[u].ra)
+                           for u in range(4, len(od.nodes))])
+    for sname in ("S1", "S2"):
+        st = nd.set_order([idx[n] for n in g[sname]["order"]])
+        assert st["peak_paper"] // UNIT == g["peak"][sname]
+    h = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_traces.json")))
+    nd.schedule("sibling")
+    assert [names[u] for u in nd.order()] == h["sibling"]["order"]
+    nd.schedule("tree")
+    assert [names[u] for u in nd.order()] == h["tree"]["order"]
+
+
+def test_argument_errors():
+    d = L.Dag(2)
+    a = d.add_leaf((3, 4))
+    b = d.add_leaf((4, 5))
+    with pytest.raises(L.LqcError) as ei:
+        d.add_contraction(a, b, [0], [0])      # extents 3 vs 4
+    assert ei.value.code == L.LQC_ERR_ARG
+    with pytest.raises(L.LqcError):
+        d.add_contraction(a, 7, [1], [0])      # no such node
+    with pytest.raises(L.LqcError):
+        d.add_contraction(a, b, [1, 1], [0, 0])  # axis paired twice
+    c = d.add_contraction(a, b, [1], [0])
+    assert d.add_contraction(a, b, [1], [0]) == c   # identical request merged
+    with pytest.raises(L.LqcError) as ei:
+        d.execute()
+    assert ei.value.code == L.LQC_ERR_STATE
+    with pytest.raises(L.LqcError) as ei:
+        d.order()
+    assert ei.value.code == L.LQC_ERR_STATE
+    d.schedule("tree")
+    with pytest.raises(L.LqcError) as ei:
+        d.add_leaf((2,))                        # frozen after scheduling
+    assert ei.value.code == L.LQC_ERR_STATE
+    with pytest.raises(L.LqcError):
+        d.set_order([c, c])

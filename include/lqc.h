@@ -265,6 +265,38 @@ int lqc_contract_all_fp64(const double* A, int rank_a, const int64_t* ext_a,
                           double* C, void* scratch, void* stream);
 int64_t lqc_contract_all_scratch_bytes(int64_t lt, int64_t elems_per_slice);
 
+/* Exterior contraction in a mixed precision (LQC_PREC_TF32X3 or
+ * LQC_PREC_BF16X3) on complex64 device tensors (interleaved floats), same
+ * shapes / semantics as lqc_contract_fp64: each operand is split into hi and
+ * lo parts of the tensor-core type, the products lo*hi + hi*lo + hi*hi are
+ * accumulated in FP32 on the tensor cores (tcgen05), and long contractions are
+ * split over the paired indices into FP32 partials summed in FP64.
+ * `scratch` (caller-owned device memory, contents ignored) must hold
+ * lqc_contract_mixed_scratch_bytes(...) bytes.  Errors: LQC_ERR_ARG,
+ * LQC_ERR_CUDA.  A kernel that gives up on a bounded internal wait records it
+ * in a device error word read by lqc_mixed_error. */
+int lqc_contract_mixed(const float* A, int rank_a, const int64_t* ext_a,
+                       const float* B, int rank_b, const int64_t* ext_b,
+                       int npairs, const int* la, const int* ra, int64_t lt,
+                       lqc_precision prec, float* C, void* scratch, void* stream);
+int64_t lqc_contract_mixed_scratch_bytes(int rank_a, const int64_t* ext_a,
+                                         int rank_b, const int64_t* ext_b,
+                                         int npairs, const int* la, const int* ra,
+                                         int64_t lt, lqc_precision prec);
+
+/* Contract-all of two complex64 device tensors with FP64 accumulation,
+ * result (complex128, lt values) multiplied by `scale`; scratch as for
+ * lqc_contract_all_fp64. */
+int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a,
+                         const float* B, int rank_b, const int64_t* ext_b,
+                         int npairs, const int* la, const int* ra, int64_t lt,
+                         double scale, double* C, void* scratch, void* stream);
+
+/* Device error word of the tensor-core kernels: 0 = none, 1 = a bounded wait
+ * expired (the kernel returned without a result).  Synchronous; reset != 0
+ * clears it.  Returns -1 if it cannot be read. */
+int lqc_mixed_error(int reset);
+
 /* Diagnostic (no counterpart in the paper): measure this device's FP64 FMA
  * throughput with a register-resident FMA loop on every SM, ~20 ms,
  * synchronous.  *tflops receives 2 * FMAs / second / 1e12 (the denominator

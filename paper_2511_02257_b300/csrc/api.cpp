@@ -1,5 +1,7 @@
 // C ABI: DAG construction with merging of identical requests (Sec. II-B),
 // scheduling + planning, and the thin wrappers around the executor.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -176,6 +178,7 @@ int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs,
     n.la[i] = la[i];
     n.ra[i] = ra[i];
   }
+  n.scale_exp = L.scale_exp + R.scale_exp;
   n.rank = 0;
   n.elems = 1;
   for (int a = 0; a < L.rank; ++a)
@@ -314,9 +317,20 @@ int lqc_dag_set_leaf_data(lqc_dag* h, int64_t id, const double* data) {
   if (g.prec == LQC_PREC_FP64) {
     std::memcpy(n.host, data, (size_t)cnt * 16);
   } else {
-    // complex64 storage: values are rounded to float once here, in FP64
+    // complex64 storage with FP64 normalisation: scale by the power of two
+    // that brings the largest |component| into [0.5, 1), then round once
+    double mx = 0.0;
+    for (int64_t i = 0; i < 2 * cnt; ++i) mx = std::max(mx, std::fabs(data[i]));
+    int e = 0;
+    if (mx > 0.0 && std::isfinite(mx)) std::frexp(mx, &e);
+    n.scale_exp = e;
     float* dst = static_cast<float*>(n.host);
-    for (int64_t i = 0; i < 2 * cnt; ++i) dst[i] = (float)data[i];
+    for (int64_t i = 0; i < 2 * cnt; ++i) dst[i] = (float)std::ldexp(data[i], -e);
+    // consumers registered before the data changed keep their exponents in sync
+    for (size_t u = (size_t)id + 1; u < g.nodes.size(); ++u) {
+      Node& c = g.nodes[u];
+      if (!c.is_leaf()) c.scale_exp = g.nodes[c.left].scale_exp + g.nodes[c.right].scale_exp;
+    }
   }
   lqc::exec_invalidate_plan(g);  // staged leaf copies are stale
   return LQC_OK;

@@ -15,12 +15,14 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <thread>
 
 #include "internal.hpp"
 #include "kernels.hpp"
+#include "kernels_mixed.hpp"
 
 namespace lqc {
 
@@ -114,6 +116,9 @@ struct ExecState {
   std::vector<Instr> prog;
   std::vector<ContractDesc> cdesc;        // per instruction (CONTRACT)
   std::vector<ContractAllDesc> adesc;     // per instruction (CONTRACT_ALL)
+  std::vector<MixedDesc> mdesc;           // per instruction (CONTRACT, mixed precisions)
+  char* mscratch = nullptr;               // operand planes / split partials
+  int64_t mscratch_bytes = 0;
   bool prog_valid = false;
   int64_t arena_bytes = 0;
   char* arena = nullptr;
@@ -183,6 +188,9 @@ void free_program(ExecState& x) {
   if (x.arena) { cudaFree(x.arena); x.arena = nullptr; }
   if (x.results) { cudaFree(x.results); x.results = nullptr; }
   if (x.scratch) { cudaFree(x.scratch); x.scratch = nullptr; }
+  if (x.mscratch) { cudaFree(x.mscratch); x.mscratch = nullptr; }
+  x.mscratch_bytes = 0;
+  x.mdesc.clear();
   for (void* p : x.host_slot)
     if (p) cudaFreeHost(p);
   x.host_slot.clear();
@@ -215,7 +223,7 @@ int build_program(Dag& g) {
   x.host_slot.assign(N, nullptr);
   x.host_slot_bytes.assign(N, 0);
   Placer pl;
-  int64_t scratch_need = 0;
+  int64_t scratch_need = 0, mscratch_need = 0;
   std::vector<Instr>& P = x.prog;
   auto add_wait = [&](Instr& in, int32_t on) {
     if (on < 0 || P[on].stream == in.stream) return;
@@ -239,6 +247,7 @@ int build_program(Dag& g) {
       P.push_back(in);
       x.cdesc.emplace_back();
       x.adesc.emplace_back();
+      x.mdesc.emplace_back();
       dep[S_COMPUTE] = (int32_t)P.size() - 1;
     }
     pl.release(off[u], g.size_bytes(u), dep);
@@ -264,6 +273,7 @@ int build_program(Dag& g) {
       P.push_back(in);
       x.cdesc.emplace_back();
       x.adesc.emplace_back();
+      x.mdesc.emplace_back();
       last_h2d[u] = (int32_t)P.size() - 1;
       last_compute[u] = -1;
       last_d2h[u] = -1;
@@ -283,6 +293,7 @@ int build_program(Dag& g) {
         P.push_back(in);
         x.cdesc.emplace_back();
         x.adesc.emplace_back();
+        x.mdesc.emplace_back();
         last_d2h[u] = (int32_t)P.size() - 1;
         wb_instr[u] = last_d2h[u];
         x.host_slot_bytes[u] = in.bytes;
@@ -336,9 +347,18 @@ int build_program(Dag& g) {
         add_wait(in, dep[S_D2H]);
         off[u] = in.dst;
       }
+      MixedDesc md{};
+      if (g.prec != LQC_PREC_FP64 && in.kind == I_CONTRACT) {
+        if (!make_mixed_desc(cd, g.prec == LQC_PREC_BF16X3, &md)) {
+          g.err = "contraction too large for the mixed-precision kernels";
+          return LQC_ERR_ARG;
+        }
+        mscratch_need = std::max(mscratch_need, md.scratch_bytes);
+      }
       P.push_back(in);
       x.cdesc.push_back(cd);
       x.adesc.push_back(ad);
+      x.mdesc.push_back(md);
       const int32_t me = (int32_t)P.size() - 1;
       for (int k = 0; k < n.n_children(); ++k) last_compute[n.child(k)] = me;
       if (n.rank != 0) {
@@ -386,6 +406,9 @@ int build_program(Dag& g) {
     CK(cudaMalloc((void**)&x.results, (size_t)(x.n_results * g.lt * 16)), "results cudaMalloc");
   x.scratch_bytes = scratch_need;
   if (scratch_need > 0) CK(cudaMalloc((void**)&x.scratch, (size_t)scratch_need), "scratch cudaMalloc");
+  x.mscratch_bytes = mscratch_need;
+  if (mscratch_need > 0)
+    CK(cudaMalloc((void**)&x.mscratch, (size_t)mscratch_need), "plane scratch cudaMalloc");
   for (int64_t u = 0; u < N; ++u)
     if (x.host_slot_bytes[u] > 0)
       CK(cudaHostAlloc(&x.host_slot[u], (size_t)x.host_slot_bytes[u], cudaHostAllocDefault),
@@ -451,16 +474,32 @@ int issue(Dag& g, cudaStream_t cs) {
         int nk;
         const bool timed = g.opt_timing && tk < x.tev_kind.size();
         if (timed) CK(cudaEventRecord(x.tev[x.tset][2 * tk], s), "timing record");
+        const bool mixed = g.prec != LQC_PREC_FP64;
         if (in.kind == I_CONTRACT) {
           const ContractDesc& d = x.cdesc[j];
-          nk = launch_contract_fp64(d, (const double*)op[0], (const double*)op[1],
-                                    (double*)(x.arena + in.dst), s);
+          if (mixed)
+            nk = launch_contract_mixed(x.mdesc[j], (const float*)op[0], (const float*)op[1],
+                                       (float*)(x.arena + in.dst), x.mscratch, s);
+          else
+            nk = launch_contract_fp64(d, (const double*)op[0], (const double*)op[1],
+                                      (double*)(x.arena + in.dst), s);
           x.flops += 8 * d.lt * d.M * d.N * d.K;
         } else {
           const ContractAllDesc& d = x.adesc[j];
-          nk = launch_contract_all_fp64(d, (const double*)op[0], (const double*)op[1],
-                                        x.results + 2 * g.lt * in.root_slot, x.scratch, s);
+          if (mixed)
+            nk = launch_contract_all_c64(d, (const float*)op[0], (const float*)op[1],
+                                         x.results + 2 * g.lt * in.root_slot, x.scratch,
+                                         std::ldexp(1.0, g.nodes[n.left].scale_exp +
+                                                             g.nodes[n.right].scale_exp),
+                                         s);
+          else
+            nk = launch_contract_all_fp64(d, (const double*)op[0], (const double*)op[1],
+                                          x.results + 2 * g.lt * in.root_slot, x.scratch, s);
           x.flops += 8 * d.lt * d.S;
+        }
+        if (nk == -2) {
+          g.err = "TMA tensor map encoding failed";
+          return LQC_ERR_CUDA;
         }
         if (nk < 0) return cuda_fail(g, cudaGetLastError(), "contraction launch");
         if (timed) {
@@ -637,7 +676,17 @@ int exec_wait(Dag& g, int64_t timeout_ms) {
   int sleep_us = 20;
   while (true) {
     cudaError_t e = cudaEventQuery(x.done_ev);
-    if (e == cudaSuccess) return LQC_OK;
+    if (e == cudaSuccess) {
+      if (g.prec != LQC_PREC_FP64) {
+        int st = mixed_error_status(true);
+        if (st != 0) {
+          g.err = st < 0 ? "cannot read the device error word"
+                         : "a tensor-core kernel gave up on a bounded wait";
+          return st < 0 ? LQC_ERR_CUDA : LQC_ERR_TIMEOUT;
+        }
+      }
+      return LQC_OK;
+    }
     if (e != cudaErrorNotReady) return cuda_fail(g, e, "execution failed");
     auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
                   std::chrono::steady_clock::now() - t0).count();

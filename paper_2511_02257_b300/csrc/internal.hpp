@@ -26,6 +26,9 @@ struct Node {
   // the DAG's storage precision; nullptr until data is given
   void* host = nullptr;
   bool host_pinned = false;
+  // mixed precisions: stored values are the tensor times 2^-scale_exp
+  // (leaves: FP64 normalisation; contractions: sum of the operands')
+  int scale_exp = 0;
   bool is_leaf() const { return left < 0; }
   // distinct children: [left] or [left, right]
   int n_children() const { return is_leaf() ? 0 : (left == right ? 1 : 2); }

@@ -1,0 +1,660 @@
+// Mixed-precision kernels: complex64 storage, split (hi + lo) tensor-core
+// products with FP32 accumulation in TMEM, FP64 where sums form results.
+//
+// K3  pack: gathers one operand of a binary contraction (any axis
+//     permutation, folded into the loads) and writes its hi/lo planes in the
+//     real-embedded GEMM layout:
+//       A' [m][2k]   = Re A(m,k),  A' [m][2k+1]  = Im A(m,k)
+//       B'T[2n][2k]  = Re B(k,n),  B'T[2n][2k+1] = -Im B(k,n)
+//       B'T[2n+1][2k]= Im B(k,n),  B'T[2n+1][2k+1]= Re B(k,n)
+//     so that the real product A' B' is the complex product already
+//     interleaved as (re, im): D'[m][2n] = Re C(m,n), D'[m][2n+1] = Im C(m,n).
+//     hi = x rounded to the tensor-core type, lo = (x - hi) rounded.
+// K4  gemm: TMA (128-byte swizzle) feeds a 3-stage shared-memory ring; one
+//     thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 inputs)
+//     for lo*hi + hi*lo + hi*hi into one FP32 accumulator in TMEM; the
+//     epilogue reads TMEM with tcgen05.ld.  Long contractions are split over
+//     k into FP32 partial tiles summed in FP64 by K4r.
+// K2m contract-all on complex64 operands with FP64 accumulation.
+//
+// Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
+// kernel records an error code, drains what it started and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "kernels.hpp"
+#include "kernels_mixed.hpp"
+
+namespace lqc {
+
+namespace {
+
+constexpr int kBM = 128;        // UMMA M (rows of A' per CTA)
+constexpr int kBN = 128;        // UMMA N (real columns of D' per CTA)
+constexpr int kStages = 3;
+constexpr int kGemmThreads = 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ int g_mixed_error = 0;  // first error code seen by a mixed kernel
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false after kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity)) {
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of
+// 1024 B (stride-dimension offset), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+template <bool BF16>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accum) {
+  if (BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// instruction descriptor: D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16),
+// both K-major, M = 128, N = kBN
+template <bool BF16>
+__host__ __device__ constexpr uint32_t make_idesc() {
+  return (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
+         ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+// ------------------------------------------------------------ K4 GEMM
+struct GemmArgs {
+  int M;          // rows of A'
+  int Nr;         // rows of B'T = real columns of D'
+  int kblocks;    // k blocks (of kBK elements) per split
+  int splits;     // k splits (grid.z = lt * splits)
+  int lt;
+  float* out;     // splits == 1: D' [lt][M][Nr]; else partial [splits][lt][M][Nr]
+};
+
+template <bool BF16>
+struct GemmCfg {
+  static constexpr int kElem = BF16 ? 2 : 4;
+  static constexpr int kBK = 128 / kElem;           // elements per 128-byte row
+  static constexpr int kUmmaK = 32 / kElem;         // elements per MMA k-step
+  static constexpr int kATile = kBM * 128;          // bytes of one A plane tile
+  static constexpr int kBTile = kBN * 128;
+  static constexpr int kStageBytes = 2 * kATile + 2 * kBTile;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 /* align */ + 256 /* barriers */;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+              const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+              const GemmArgs p) {
+  using C = GemmCfg<BF16>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
+  const int t = blockIdx.z % p.lt, split = blockIdx.z / p.lt;
+  const int kb0 = split * p.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    for (int i = 0; i < p.kblocks; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; break; }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * C::kStageBytes;
+      mbar_expect_tx(&full[s], C::kStageBytes);
+      const int k0 = (kb0 + i) * C::kBK;
+      tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
+      tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
+      tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
+      tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
+      ++issued;
+    }
+    // drain: every issued stage must have landed before the CTA exits
+    for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+      if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) break;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = make_idesc<BF16>();
+    int i = 0;
+    for (; i < p.kblocks; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+      if (!mbar_wait(&full[s], ph) || *abort_flag) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * C::kStageBytes);
+      const uint32_t ahi = base, alo = base + C::kATile;
+      const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
+#pragma unroll
+      for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
+        const uint32_t off = kk * 32;
+        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+        umma<BF16>(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
+        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, 1u);
+      }
+      umma_commit(&empty[s]);  // stage reusable once these MMAs have read it
+    }
+    umma_commit(done);         // accumulator complete (or abandoned)
+  }
+  __syncwarp();
+
+  // ---- epilogue: all four warps, warp w owns TMEM lanes [32w, 32w + 32);
+  // the decision is made by lane 0 and broadcast so that every lane takes
+  // part in the collective TMEM loads together
+  int ok = 0;
+  if (lane == 0) {
+    ok = mbar_wait(done, 0) ? 1 : 0;
+    if (!ok) *abort_flag = 1;
+    ok = ok && !*abort_flag;
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    float* dst = p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < kBN; c += 16) {
+      uint32_t r[16];
+      tmem_ld16(tbase + c, r);  // collective: every lane loads, in-range or not
+      if (row < p.M) {
+        const int col = n0 + c;
+        if (col + 16 <= p.Nr && (p.Nr & 3) == 0) {
+          float4* d4 = reinterpret_cast<float4*>(dst + col);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            d4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        } else {
+          for (int q = 0; q < 16; ++q)
+            if (col + q < p.Nr) dst[col + q] = __uint_as_float(r[q]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicCAS(&g_mixed_error, 0, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
+}
+
+// K4r: out c64 [lt][M][N] = sum over splits of the FP32 partials, in FP64
+__global__ void k_reduce_splits(const float* __restrict__ part, float* __restrict__ out,
+                                long long per_split, int splits) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per_split;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)part[(long long)k * per_split + i];
+    out[i] = (float)s;
+  }
+}
+
+// ------------------------------------------------------------ K3 pack
+__device__ __forceinline__ long long goff(const Group& g, unsigned idx) {
+  long long off = 0;
+#pragma unroll
+  for (int d = LQC_MAX_RANK - 1; d >= 0; --d) {
+    if (d < g.n) {
+      unsigned e = (unsigned)g.ext[d];
+      unsigned q = idx / e;
+      off += (long long)(idx - q * e) * g.stride[d];
+      idx = q;
+    }
+  }
+  return off;
+}
+
+template <bool BF16>
+struct Split;
+template <>
+struct Split<false> {
+  typedef float T;
+  __device__ static void split(float x, float& hi, float& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+    lo = __uint_as_float(l);
+  }
+  __device__ static void store2(float* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
+};
+template <>
+struct Split<true> {
+  typedef __nv_bfloat16 T;
+  __device__ static void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+  }
+  __device__ static void store2(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
+    __nv_bfloat162 v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<__nv_bfloat162*>(p) = v;
+  }
+};
+
+// One 32 (rows) x 32 (complex k) block per CTA through shared memory, so that
+// both the gather (along the operand's unit-stride axis) and the plane
+// writes (along k) are coalesced.  which = 0: A operand, 1: B operand.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_pack(const float2* __restrict__ X, typename Split<BF16>::T* __restrict__ hi,
+       typename Split<BF16>::T* __restrict__ lo, const PackArgs p) {
+  typedef typename Split<BF16>::T T;
+  __shared__ float2 tile[32][33];
+  const int t = blockIdx.z;
+  const unsigned r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  X += (long long)t * p.ts;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    unsigned r, k;
+    if (p.k_fast) { k = k0 + tx; r = r0 + ty + 8 * j; }
+    else { r = r0 + tx; k = k0 + ty + 8 * j; }
+    float2 v = make_float2(0.f, 0.f);
+    if (r < (unsigned)p.rows && k < (unsigned)p.K) v = X[goff(p.rg, r) + goff(p.kg, k)];
+    tile[r - r0][k - k0] = v;
+  }
+  __syncthreads();
+  const size_t plane_rows = p.which == 0 ? (size_t)p.rows : 2 * (size_t)p.rows;
+  T* Hb = hi + (size_t)t * plane_rows * p.kp;
+  T* Lb = lo + (size_t)t * plane_rows * p.kp;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const unsigned r = r0 + ty + 8 * j, k = k0 + tx;
+    if (r >= (unsigned)p.rows || 2 * k >= (unsigned)p.kp) continue;
+    const float2 v = tile[r - r0][k - k0];  // zero beyond K: fills the padding
+    T hr, lr, hi_, li;
+    Split<BF16>::split(v.x, hr, lr);
+    Split<BF16>::split(v.y, hi_, li);
+    if (p.which == 0) {
+      Split<BF16>::store2(Hb + (size_t)r * p.kp + 2 * k, hr, hi_);
+      Split<BF16>::store2(Lb + (size_t)r * p.kp + 2 * k, lr, li);
+    } else {
+      T hni, lni;  // -Im
+      Split<BF16>::split(-v.y, hni, lni);
+      Split<BF16>::store2(Hb + (size_t)(2 * r) * p.kp + 2 * k, hr, hni);
+      Split<BF16>::store2(Lb + (size_t)(2 * r) * p.kp + 2 * k, lr, lni);
+      Split<BF16>::store2(Hb + (size_t)(2 * r + 1) * p.kp + 2 * k, hi_, hr);
+      Split<BF16>::store2(Lb + (size_t)(2 * r + 1) * p.kp + 2 * k, li, lr);
+    }
+  }
+}
+
+// ------------------------------------------------------------ K2m
+__global__ void __launch_bounds__(256)
+k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
+                   double2* __restrict__ part, const ContractAllDesc p) {
+  const long long t = blockIdx.y;
+  const int c = blockIdx.x;
+  const unsigned S = (unsigned)p.S;
+  const unsigned lo = (unsigned)(((unsigned long long)S * c) / p.chunks);
+  const unsigned hi = (unsigned)(((unsigned long long)S * (c + 1)) / p.chunks);
+  A += t * p.S;
+  B += t * p.S;
+  double re = 0.0, im = 0.0;
+  for (unsigned i = lo + threadIdx.x; i < hi; i += 256) {
+    const float2 a = A[i];
+    const float2 b = B[goff(p.bp, i)];
+    re = fma((double)a.x, (double)b.x, re);
+    re = fma(-(double)a.y, (double)b.y, re);
+    im = fma((double)a.x, (double)b.y, im);
+    im = fma((double)a.y, (double)b.x, im);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  __shared__ double2 w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_double2(re, im);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = w[0];
+    for (int k = 1; k < 8; ++k) { s.x += w[k].x; s.y += w[k].y; }
+    part[t * p.chunks + c] = s;
+  }
+}
+
+__global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
+                                            double2* __restrict__ C, long long lt, int chunks,
+                                            double scale) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= lt) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int c = 0; c < chunks; ++c) {
+    double2 v = part[t * chunks + c];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  C[t] = make_double2(s.x * scale, s.y * scale);
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D map over planes [lt][rows][kp], box (128-byte row, 128 rows, 1)
+bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t rows, int64_t lt) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)lt};
+  cuuint64_t strides[2] = {(cuuint64_t)(kp * es), (cuuint64_t)(kp * rows * es)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), 128u, 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
+  std::memset(d, 0, sizeof(*d));
+  d->bf16 = bf16;
+  d->cd = cd;
+  const int es = bf16 ? 2 : 4;
+  d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA
+  const int64_t bk = 128 / es;                  // elements per k block
+  const int64_t kblocks = (d->kp + bk - 1) / bk;
+  // split k when the output tiles alone cannot fill the GPU, keeping at
+  // least 4 k blocks per split
+  const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
+  int64_t splits = 1;
+  while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
+  // and keep FP32 accumulation chunks to <= 1024 real k (error control)
+  while ((kblocks + splits - 1) / splits * bk > 1024 && splits < 64) splits *= 2;
+  d->splits = (int)splits;
+  d->kblocks = (int)((kblocks + splits - 1) / splits);
+  const int64_t plane_a = cd.lt * cd.M * d->kp * es;
+  const int64_t plane_b = cd.lt * 2 * cd.N * d->kp * es;
+  d->a_off = 0;
+  d->b_off = round_up(2 * plane_a, 256);
+  d->part_off = round_up(d->b_off + 2 * plane_b, 256);
+  d->scratch_bytes = d->part_off + (splits > 1 ? splits * cd.lt * cd.M * 2 * cd.N * 4 : 0);
+  d->plane_a = plane_a;
+  d->plane_b = plane_b;
+  return cd.M < (1 << 30) && 2 * cd.N < (1 << 30) && d->kp < (1 << 30);
+}
+
+static PackArgs pack_args(const ContractDesc& cd, int which, int64_t kp) {
+  PackArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.which = which;
+  a.K = (int)cd.K;
+  a.kp = kp;
+  if (which == 0) {
+    a.rows = (int)cd.M;
+    a.rg = cd.am;
+    a.kg = cd.ak;
+    a.ts = cd.a_ts;
+    a.k_fast = cd.a_kfast;
+  } else {
+    a.rows = (int)cd.N;
+    a.rg = cd.bn;
+    a.kg = cd.bk;
+    a.ts = cd.b_ts;
+    a.k_fast = cd.b_kfast;
+  }
+  return a;
+}
+
+int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, float* C,
+                          void* scratch, cudaStream_t s) {
+  const ContractDesc& cd = d.cd;
+  char* sc = static_cast<char*>(scratch);
+  void* ahi = sc + d.a_off;
+  void* alo = sc + d.a_off + d.plane_a;
+  void* bhi = sc + d.b_off;
+  void* blo = sc + d.b_off + d.plane_b;
+  int nk = 0;
+  for (int which = 0; which < 2; ++which) {
+    PackArgs pa = pack_args(cd, which, d.kp);
+    const int64_t kc = std::max<int64_t>(cd.K, d.kp / 2);  // complex columns incl. padding
+    dim3 grid((unsigned)((kc + 31) / 32), (unsigned)((pa.rows + 31) / 32), (unsigned)cd.lt);
+    const float2* X = reinterpret_cast<const float2*>(which == 0 ? A : B);
+    if (d.bf16)
+      k_pack<true><<<grid, 256, 0, s>>>(X, (__nv_bfloat16*)(which ? bhi : ahi),
+                                         (__nv_bfloat16*)(which ? blo : alo), pa);
+    else
+      k_pack<false><<<grid, 256, 0, s>>>(X, (float*)(which ? bhi : ahi),
+                                          (float*)(which ? blo : alo), pa);
+    ++nk;
+  }
+  CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
+  if (!make_map(&m_ahi, ahi, d.bf16, d.kp, cd.M, cd.lt) ||
+      !make_map(&m_alo, alo, d.bf16, d.kp, cd.M, cd.lt) ||
+      !make_map(&m_bhi, bhi, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
+      !make_map(&m_blo, blo, d.bf16, d.kp, 2 * cd.N, cd.lt))
+    return -2;
+  GemmArgs g;
+  g.M = (int)cd.M;
+  g.Nr = (int)(2 * cd.N);
+  g.kblocks = d.kblocks;
+  g.splits = d.splits;
+  g.lt = (int)cd.lt;
+  g.out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
+  dim3 grid((unsigned)((g.Nr + kBN - 1) / kBN), (unsigned)((g.M + kBM - 1) / kBM),
+            (unsigned)(cd.lt * d.splits));
+  if (d.bf16) {
+    const int smem = GemmCfg<true>::kSmem;
+    cudaFuncSetAttribute(k_gemm_split3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_gemm_split3<true><<<grid, kGemmThreads, smem, s>>>(m_ahi, m_alo, m_bhi, m_blo, g);
+  } else {
+    const int smem = GemmCfg<false>::kSmem;
+    cudaFuncSetAttribute(k_gemm_split3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_gemm_split3<false><<<grid, kGemmThreads, smem, s>>>(m_ahi, m_alo, m_bhi, m_blo, g);
+  }
+  ++nk;
+  if (d.splits > 1) {
+    const long long per = cd.lt * cd.M * 2 * cd.N;
+    unsigned blocks = (unsigned)std::min<long long>((per + 255) / 256, 8 * 148);
+    k_reduce_splits<<<blocks, 256, 0, s>>>(g.out, C, per, d.splits);
+    ++nk;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? nk : -1;
+}
+
+int launch_contract_all_c64(const ContractAllDesc& d, const float* A, const float* B, double* C,
+                            double* scratch, double scale, cudaStream_t s) {
+  if (d.lt > 65535) return -1;
+  dim3 grid((unsigned)d.chunks, (unsigned)d.lt);
+  double2* part = reinterpret_cast<double2*>(scratch);
+  k_contract_all_c64<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(A),
+                                          reinterpret_cast<const float2*>(B), part, d);
+  k_contract_all_final_scaled<<<(unsigned)((d.lt + 127) / 128), 128, 0, s>>>(
+      part, reinterpret_cast<double2*>(C), d.lt, d.chunks, scale);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+}
+
+int mixed_error_status(bool reset) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_mixed_error, sizeof(int)) != cudaSuccess) return -1;
+  if (reset && v) {
+    int z = 0;
+    cudaMemcpyToSymbol(g_mixed_error, &z, sizeof(int));
+  }
+  return v;
+}
+
+}  // namespace lqc
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+int64_t lqc_contract_mixed_scratch_bytes(int rank_a, const int64_t* ext_a, int rank_b,
+                                         const int64_t* ext_b, int npairs, const int* la,
+                                         const int* ra, int64_t lt, lqc_precision prec) {
+  if (!ext_a || !ext_b || !la || !ra || lt < 1) return 0;
+  if (prec != LQC_PREC_TF32X3 && prec != LQC_PREC_BF16X3) return 0;
+  lqc::ContractDesc cd;
+  lqc::MixedDesc md;
+  std::string err;
+  if (!lqc::make_contract_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &cd, &err))
+    return 0;
+  if (!lqc::make_mixed_desc(cd, prec == LQC_PREC_BF16X3, &md)) return 0;
+  return md.scratch_bytes;
+}
+
+int lqc_contract_mixed(const float* A, int rank_a, const int64_t* ext_a, const float* B,
+                       int rank_b, const int64_t* ext_b, int npairs, const int* la,
+                       const int* ra, int64_t lt, lqc_precision prec, float* C, void* scratch,
+                       void* stream) {
+  if (!A || !B || !C || !scratch || !ext_a || !ext_b || !la || !ra || lt < 1) return LQC_ERR_ARG;
+  if (prec != LQC_PREC_TF32X3 && prec != LQC_PREC_BF16X3) return LQC_ERR_ARG;
+  lqc::ContractDesc cd;
+  lqc::MixedDesc md;
+  std::string err;
+  if (!lqc::make_contract_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &cd, &err))
+    return LQC_ERR_ARG;
+  if (!lqc::make_mixed_desc(cd, prec == LQC_PREC_BF16X3, &md)) return LQC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return LQC_ERR_ARG;
+  int k = lqc::launch_contract_mixed(md, A, B, C, scratch, static_cast<cudaStream_t>(stream));
+  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+}
+
+int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a, const float* B,
+                         int rank_b, const int64_t* ext_b, int npairs, const int* la,
+                         const int* ra, int64_t lt, double scale, double* C, void* scratch,
+                         void* stream) {
+  if (!A || !B || !C || !scratch || !ext_a || !ext_b || !la || !ra || lt < 1) return LQC_ERR_ARG;
+  lqc::ContractAllDesc d;
+  std::string err;
+  if (!lqc::make_contract_all_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &d, &err))
+    return LQC_ERR_ARG;
+  int k = lqc::launch_contract_all_c64(d, A, B, C, static_cast<double*>(scratch), scale,
+                                       static_cast<cudaStream_t>(stream));
+  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+}
+
+int lqc_mixed_error(int reset) { return lqc::mixed_error_status(reset != 0); }
+
+}  // extern "C"

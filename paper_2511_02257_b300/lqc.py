@@ -97,6 +97,15 @@ _sig("lqc_contract_all_fp64", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, ct
                                              ctypes.c_int, P_int, P_int, c_i64, c_vp, c_vp, c_vp])
 _sig("lqc_contract_all_scratch_bytes", c_i64, [c_i64, c_i64])
 _sig("lqc_measure_fp64_peak", ctypes.c_int, [P_dbl])
+_sig("lqc_contract_mixed", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, ctypes.c_int, P_i64,
+                                          ctypes.c_int, P_int, P_int, c_i64, ctypes.c_int, c_vp,
+                                          c_vp, c_vp])
+_sig("lqc_contract_mixed_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c_int, P_i64,
+                                                 ctypes.c_int, P_int, P_int, c_i64, ctypes.c_int])
+_sig("lqc_contract_all_c64", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, ctypes.c_int, P_i64,
+                                            ctypes.c_int, P_int, P_int, c_i64, ctypes.c_double,
+                                            c_vp, c_vp, c_vp])
+_sig("lqc_mixed_error", ctypes.c_int, [ctypes.c_int])
 
 # re-export the raw entry points under their C names
 for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
@@ -106,7 +115,8 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_
            "lqc_dag_read_all_correlators", "lqc_dag_get_roots", "lqc_dag_num_nodes",
            "lqc_dag_node_info", "lqc_dag_get_stats", "lqc_dag_get_exec_info", "lqc_last_error",
            "lqc_contract_fp64", "lqc_contract_all_fp64", "lqc_contract_all_scratch_bytes",
-           "lqc_measure_fp64_peak"):
+           "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
+           "lqc_contract_all_c64", "lqc_mixed_error"):
     globals()[_n] = getattr(_lib, _n)
 
 

@@ -1,0 +1,180 @@
+"""GPU parity of the mixed-precision path (complex64 storage, split TF32x3 /
+BF16x3 tensor-core products, FP64 correlator sums) against the oracle.
+
+* Integer-valued operands small enough to be exact in the hi part: the
+  tensor-core contraction must equal the oracle exactly (this pins the
+  operand packing, the swizzled tile layout and the epilogue indexing
+  independently of rounding).
+* Random operands: per-contraction norm-wise relative error <= 1e-6 for
+  TF32x3; whole DAGs: every correlator within 1e-6 of the FP64 oracle.
+* BF16x3 error is reported, with a looser bound (16 significant bits).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import contract as C
+from oracle import dag as D
+
+torch = pytest.importorskip("torch")
+L = pytest.importorskip("paper_2511_02257_b300")
+
+pytestmark = pytest.mark.gpu
+TOL_TF32X3 = 1e-6
+TOL_BF16X3 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_err(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def _ext(shape):
+    a = np.asarray(shape, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _pairs(xs):
+    a = np.asarray(xs, dtype=np.intc)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def run_mixed(A, B, la, ra, prec):
+    lt = A.shape[0]
+    sa, sb = A.shape[1:], B.shape[1:]
+    ea, pa = _ext(sa)
+    eb, pb = _ext(sb)
+    xla, pla = _pairs(la)
+    xra, pra = _pairs(ra)
+    nbytes = L.lqc_contract_mixed_scratch_bytes(len(sa), pa, len(sb), pb, len(la), pla, pra, lt,
+                                                prec)
+    assert nbytes > 0
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dA = torch.from_numpy(np.ascontiguousarray(A.astype(np.complex64))).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B.astype(np.complex64))).cuda()
+    out_shape = (lt,) + tuple(e for i, e in enumerate(sa) if i not in la) + \
+        tuple(e for j, e in enumerate(sb) if j not in ra)
+    dC = torch.full(out_shape, complex("nan"), dtype=torch.complex64, device="cuda")
+    rc = L.lqc_contract_mixed(_ptr(dA), len(sa), pa, _ptr(dB), len(sb), pb, len(la), pla, pra, lt,
+                              prec, _ptr(dC), _ptr(scratch), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert L.lqc_mixed_error(1) == 0
+    return dC.cpu().numpy()
+
+
+CASES = [
+    ((17, 33), (33, 9), (1,), (0,)),
+    ((64, 64), (64, 64), (1,), (0,)),
+    ((64, 64), (64, 64), (0,), (1,)),
+    ((4, 4, 19, 21), (21, 13), (3,), (0,)),
+    ((4, 4, 24, 24), (4, 4, 24, 24), (1, 3), (0, 2)),
+    ((12, 12, 12), (12, 12, 12), (1, 2), (0, 1)),
+    ((12, 12, 12), (12, 7), (2,), (0,)),
+    ((5, 3, 7, 2), (2, 7, 6), (3, 2), (0, 1)),
+    ((70,), (70, 3), (0,), (0,)),
+    ((3, 130), (130,), (1,), (0,)),
+    ((129, 65), (65, 131), (1,), (0,)),
+    ((200, 300), (300, 150), (1,), (0,)),
+    ((16, 16, 16), (16, 16, 16), (1, 2), (0, 1)),   # long k: split over k
+    ((40, 1100), (1100, 40), (1,), (0,)),              # k not a multiple of the tile
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", [L.LQC_PREC_TF32X3, L.LQC_PREC_BF16X3])
+def test_mixed_exact_on_small_integers(case, prec):
+    sa, sb, la, ra = case
+    lt = 3
+    rng = np.random.default_rng(11)
+    A = (rng.integers(-3, 4, (lt,) + sa) + 1j * rng.integers(-3, 4, (lt,) + sa))
+    B = (rng.integers(-3, 4, (lt,) + sb) + 1j * rng.integers(-3, 4, (lt,) + sb))
+    ref = C.contract_pair(A, B, la, ra)
+    got = run_mixed(A, B, la, ra, prec)
+    assert np.array_equal(got.astype(np.complex128), ref)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("lt", [1, 4])
+def test_mixed_tf32x3_random(case, lt):
+    sa, sb, la, ra = case
+    rng = np.random.default_rng(hash((sa, sb, lt)) % 2 ** 32)
+    A = (rng.standard_normal((lt,) + sa) + 1j * rng.standard_normal((lt,) + sa)).astype(np.complex64)
+    B = (rng.standard_normal((lt,) + sb) + 1j * rng.standard_normal((lt,) + sb)).astype(np.complex64)
+    ref = C.contract_pair(A.astype(np.complex128), B.astype(np.complex128), la, ra)
+    got = run_mixed(A, B, la, ra, L.LQC_PREC_TF32X3)
+    assert rel_err(got.astype(np.complex128), ref) < TOL_TF32X3
+    got = run_mixed(A, B, la, ra, L.LQC_PREC_BF16X3)
+    assert rel_err(got.astype(np.complex128), ref) < TOL_BF16X3
+
+
+def _oracle(wl, roots=None):
+    od, _ = D.build_from_workload(wl)
+    cache = {}
+
+    def lf(u):
+        li = od.nodes[u].leaf_index
+        if li not in cache:
+            cache[li] = synth.leaf_data(wl, li)
+        return cache[li]
+    return od, C.evaluate(od, lf, roots)
+
+
+def _run(wl, prec, roots=None, policy="tree"):
+    nd, _ = L.build_dag(wl, precision=prec, leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    planned = nd.schedule(policy, "lru", 0)
+    nd.execute(torch.cuda.current_stream().cuda_stream)
+    nd.wait()
+    return nd, planned, {r: nd.read_correlator(r) for r in (roots or nd.roots())}
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tiny_dag_tf32x3(seed):
+    wl = synth.make_workload("tiny", seed=seed)
+    od, ref = _oracle(wl)
+    nd, planned, vals = _run(wl, "tf32x3")
+    errs = [rel_err(vals[r], ref[r]) for r in ref]
+    assert max(errs) < TOL_TF32X3, errs
+    assert nd.stats() == planned
+    # storage is complex64: half the bytes of the FP64 path
+    nd64, planned64, _ = _run(wl, "fp64")
+    assert planned["peak_paper"] * 2 == planned64["peak_paper"]
+
+
+def test_multi_meson_tf32x3_all_roots():
+    wl = synth.make_workload("multi_meson")
+    od, ref = _oracle(wl)
+    nd, planned, vals = _run(wl, "tf32x3")
+    errs = np.array([rel_err(vals[r], ref[r]) for r in ref])
+    assert errs.max() < TOL_TF32X3, (errs.max(), np.median(errs))
+
+
+def test_multi_meson_bf16x3_error_reported():
+    wl = synth.make_workload("multi_meson", n_functions=30)
+    od, ref = _oracle(wl)
+    nd, planned, vals = _run(wl, "bf16x3")
+    errs = np.array([rel_err(vals[r], ref[r]) for r in ref])
+    print("bf16x3 correlator error: max %.2e median %.2e" % (errs.max(), np.median(errs)))
+    assert errs.max() < 1e-3
+
+
+def test_baryon_tf32x3_sampled_roots():
+    wl = synth.make_workload("baryon")
+    od, _ = D.build_from_workload(wl)
+    rng = np.random.default_rng(5)
+    roots = [int(r) for r in rng.choice(od.roots(), size=24, replace=False)]
+    _, ref = _oracle(wl, roots)
+    nd, planned, vals = _run(wl, "tf32x3", roots)
+    errs = [rel_err(vals[r], ref[r]) for r in roots]
+    assert max(errs) < TOL_TF32X3, errs

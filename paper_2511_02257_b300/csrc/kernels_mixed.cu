@@ -152,7 +152,6 @@ template <bool BF16>
 struct GemmCfg {
   static constexpr int kElem = BF16 ? 2 : 4;
   static constexpr int kBK = 128 / kElem;           // elements per 128-byte row
-  static constexpr int kUmmaK = 32 / kElem;         // elements per MMA k-step
   static constexpr int kATile = kBM * 128;          // bytes of one A plane tile
   static constexpr int kBTile = kBN * 128;
   static constexpr int kStageBytes = 2 * kATile + 2 * kBTile;

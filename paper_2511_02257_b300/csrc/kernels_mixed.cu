@@ -11,10 +11,13 @@
 //     interleaved as (re, im): D'[m][2n] = Re C(m,n), D'[m][2n+1] = Im C(m,n).
 //     hi = x rounded to the tensor-core type, lo = (x - hi) rounded.
 // K4  gemm: TMA (128-byte swizzle) feeds a 3-stage shared-memory ring; one
-//     thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 inputs)
-//     for lo*hi + hi*lo + hi*hi into one FP32 accumulator in TMEM; the
-//     epilogue reads TMEM with tcgen05.ld.  Long contractions are split over
-//     k into FP32 partial tiles summed in FP64 by K4r.
+//     thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 inputs):
+//     hi*hi into one FP32 accumulator in TMEM and the two correction
+//     products lo*hi + hi*lo into a second one, so the small terms never
+//     round against the large running sum; the epilogue reads both with
+//     tcgen05.ld and adds them.  Long contractions are split over k into
+//     FP32 partial tiles summed in FP64 by K4r (bounds the number of FP32
+//     accumulation steps of the main accumulator).
 // K2m contract-all on complex64 operands with FP64 accumulation.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
@@ -38,6 +41,8 @@ namespace {
 constexpr int kBM = 128;        // UMMA M (rows of A' per CTA)
 constexpr int kBN = 128;        // UMMA N (real columns of D' per CTA)
 constexpr int kStages = 3;
+constexpr int kTmemCols = 2 * kBN;  // main accumulator + correction accumulator
+constexpr int64_t kMaxChunk = 256;   // real k accumulated in FP32 before an FP64 sum
 constexpr int kGemmThreads = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
@@ -190,7 +195,7 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kBN));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -234,9 +239,9 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
       for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
         const uint32_t off = kk * 32;
         const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-        umma<BF16>(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
-        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
-        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, 1u);
+        umma<BF16>(tmem + kBN, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
+        umma<BF16>(tmem + kBN, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
       }
       umma_commit(&empty[s]);  // stage reusable once these MMAs have read it
     }
@@ -262,8 +267,12 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c = 0; c < kBN; c += 16) {
-      uint32_t r[16];
+      uint32_t r[16], rc[16];
       tmem_ld16(tbase + c, r);  // collective: every lane loads, in-range or not
+      tmem_ld16(tbase + kBN + c, rc);
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(rc[q]));
       if (row < p.M) {
         const int col = n0 + c;
         if (col + 16 <= p.Nr && (p.Nr & 3) == 0) {
@@ -283,7 +292,8 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) atomicCAS(&g_mixed_error, 0, 1);
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
 }
 
 // K4r: out c64 [lt][M][N] = sum over splits of the FP32 partials, in FP64
@@ -489,8 +499,8 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
   const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
   int64_t splits = 1;
   while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
-  // and keep FP32 accumulation chunks to <= 1024 real k (error control)
-  while ((kblocks + splits - 1) / splits * bk > 1024 && splits < 64) splits *= 2;
+  // and keep FP32 accumulation chunks to <= kMaxChunk real k (error control)
+  while ((kblocks + splits - 1) / splits * bk > kMaxChunk && splits < 64) splits *= 2;
   d->splits = (int)splits;
   d->kblocks = (int)((kblocks + splits - 1) / splits);
   const int64_t plane_a = cd.lt * cd.M * d->kp * es;

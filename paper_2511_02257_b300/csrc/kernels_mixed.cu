@@ -14,10 +14,12 @@
 //     thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 inputs):
 //     hi*hi into one FP32 accumulator in TMEM and the two correction
 //     products lo*hi + hi*lo into a second one, so the small terms never
-//     round against the large running sum; the epilogue reads both with
-//     tcgen05.ld and adds them.  Long contractions are split over k into
-//     FP32 partial tiles summed in FP64 by K4r (bounds the number of FP32
-//     accumulation steps of the main accumulator).
+//     round against the large running sum.  The tensor core's own FP32
+//     accumulation is kept short: every kChunkBlocks k-blocks the MMA thread
+//     switches to the other of two TMEM buffers and four drain warps add the
+//     finished buffer into FP32 registers (round-to-nearest adds), one output
+//     row per thread.  Contractions longer than kMaxChunk real k are split
+//     over k into FP32 partial tiles summed in FP64 by K4r.
 // K2m contract-all on complex64 operands with FP64 accumulation.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
@@ -41,9 +43,11 @@ namespace {
 constexpr int kBM = 128;        // UMMA M (rows of A' per CTA)
 constexpr int kBN = 128;        // UMMA N (real columns of D' per CTA)
 constexpr int kStages = 3;
-constexpr int kTmemCols = 2 * kBN;  // main accumulator + correction accumulator
-constexpr int64_t kMaxChunk = 256;   // real k accumulated in FP32 before an FP64 sum
-constexpr int kGemmThreads = 128;
+constexpr int kTmemCols = 4 * kBN;  // 2 buffers x (main + correction accumulator)
+constexpr int64_t kMaxChunk = 1024;  // real k summed in FP32 registers before an FP64 sum
+constexpr int kDrainWarps = 8;  // two per TMEM lane quarter, one per column half
+constexpr int kGemmThreads = 64 + 32 * kDrainWarps;
+constexpr int kChunkBlocks = 2;     // k-blocks per TMEM accumulation before a drain
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 __device__ int g_mixed_error = 0;  // first error code seen by a mixed kernel
@@ -163,6 +167,15 @@ struct GemmCfg {
   static constexpr int kSmem = kStages * kStageBytes + 1024 /* align */ + 256 /* barriers */;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
+// warps 2..9 = drain/epilogue (warp w reads TMEM lanes 32*(w%4) .. +31, i.e.
+// one output row per thread, and one half of the kBN columns).  TMEM holds two accumulator buffers of
+// 2*kBN columns each (main + correction); the MMA thread fills one while the
+// drain warps empty the other into FP32 registers every kChunkBlocks k-blocks.
 template <bool BF16>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
@@ -174,7 +187,9 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
                                              ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
+  uint64_t* tfull = empty + kStages;   // [2] accumulator buffer ready to drain
+  uint64_t* tempty = tfull + 2;        // [2] accumulator buffer drained
+  uint64_t* done = tempty + 2;         // every MMA issued has completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -182,11 +197,16 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
   const int t = blockIdx.z % p.lt, split = blockIdx.z / p.lt;
   const int kb0 = split * p.kblocks;
+  const int nchunks = (p.kblocks + kChunkBlocks - 1) / kChunkBlocks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kDrainWarps);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -203,90 +223,118 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    int issued = 0;
-    for (int i = 0; i < p.kblocks; ++i) {
-      const int s = i % kStages;
-      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; break; }
-      if (*abort_flag) break;
-      uint8_t* st = smem + s * C::kStageBytes;
-      mbar_expect_tx(&full[s], C::kStageBytes);
-      const int k0 = (kb0 + i) * C::kBK;
-      tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
-      tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
-      tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
-      tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
-      ++issued;
-    }
-    // drain: every issued stage must have landed before the CTA exits
-    for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
-      if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) break;
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = make_idesc<BF16>();
-    int i = 0;
-    for (; i < p.kblocks; ++i) {
-      const int s = i % kStages;
-      const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (!mbar_wait(&full[s], ph) || *abort_flag) { *abort_flag = 1; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + s * C::kStageBytes);
-      const uint32_t ahi = base, alo = base + C::kATile;
-      const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
-#pragma unroll
-      for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
-        const uint32_t off = kk * 32;
-        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-        umma<BF16>(tmem + kBN, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
-        umma<BF16>(tmem + kBN, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
-        umma<BF16>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int issued = 0;
+      for (int i = 0; i < p.kblocks; ++i) {
+        const int s = i % kStages;
+        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        uint8_t* st = smem + s * C::kStageBytes;
+        mbar_expect_tx(&full[s], C::kStageBytes);
+        const int k0 = (kb0 + i) * C::kBK;
+        tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
+        tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
+        tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
+        tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
+        ++issued;
       }
-      umma_commit(&empty[s]);  // stage reusable once these MMAs have read it
+      // drain: every issued stage must have landed before the CTA exits
+      for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+        if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) break;
     }
-    umma_commit(done);         // accumulator complete (or abandoned)
-  }
-  __syncwarp();
-
-  // ---- epilogue: all four warps, warp w owns TMEM lanes [32w, 32w + 32);
-  // the decision is made by lane 0 and broadcast so that every lane takes
-  // part in the collective TMEM loads together
-  int ok = 0;
-  if (lane == 0) {
-    ok = mbar_wait(done, 0) ? 1 : 0;
-    if (!ok) *abort_flag = 1;
-    ok = ok && !*abort_flag;
-  }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    float* dst = p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c = 0; c < kBN; c += 16) {
-      uint32_t r[16], rc[16];
-      tmem_ld16(tbase + c, r);  // collective: every lane loads, in-range or not
-      tmem_ld16(tbase + kBN + c, rc);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = make_idesc<BF16>();
+      for (int i = 0; i < p.kblocks; ++i) {
+        const int c = i / kChunkBlocks, b = c & 1;
+        const bool first = (i % kChunkBlocks) == 0;
+        const bool last = (i % kChunkBlocks) == kChunkBlocks - 1 || i == p.kblocks - 1;
+        if (first) {  // wait until the drain warps have emptied this buffer
+          if (!mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const int s = i % kStages;
+        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+        if (!mbar_wait(&full[s], ph) || *abort_flag) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem + s * C::kStageBytes);
+        const uint32_t ahi = base, alo = base + C::kATile;
+        const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
+        const uint32_t dmain = tmem + (uint32_t)(b * 2 * kBN), dcorr = dmain + kBN;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(rc[q]));
-      if (row < p.M) {
-        const int col = n0 + c;
-        if (col + 16 <= p.Nr && (p.Nr & 3) == 0) {
-          float4* d4 = reinterpret_cast<float4*>(dst + col);
+        for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
+          const uint32_t off = kk * 32;
+          const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
+          umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
+          umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+          umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+        }
+        umma_commit(&empty[s]);      // stage reusable once these MMAs have read it
+        if (last) umma_commit(&tfull[b]);
+      }
+      umma_commit(done);             // all issued MMAs complete (or abandoned)
+    }
+  } else {
+    // ---- drain / epilogue warps
+    constexpr int kHalf = kBN / 2;
+    const int q = warp & 3;          // TMEM lane quarter of this warp
+    const int c0 = ((warp - 2) >> 2) * kHalf;  // first column of this warp's half
+    const int row = m0 + q * 32 + lane;
+    const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+    float acc[kHalf];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            d4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-        } else {
-          for (int q = 0; q < 16; ++q)
-            if (col + q < p.Nr) dst[col + q] = __uint_as_float(r[q]);
+    for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
+    int ok = 1;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      if (lane == 0) {
+        if (!mbar_wait(&tfull[b], (uint32_t)(c >> 1) & 1u) || *abort_flag) {
+          *abort_flag = 1;
+          ok = 0;
         }
       }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tb = tmem + tlane + (uint32_t)(b * 2 * kBN);
+#pragma unroll
+      for (int j = 0; j < kHalf; j += 16) {
+        uint32_t r[16], rc[16];
+        tmem_ld16(tb + j, r);        // collective: every lane loads, in-range or not
+        tmem_ld16(tb + kBN + j, rc);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          acc[j + u] += __uint_as_float(r[u]) + __uint_as_float(rc[u]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
+    if (ok && row < p.M) {
+      float* dst = p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
+      const int col = n0 + c0;
+      if (col + kHalf <= p.Nr && (p.Nr & 3) == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst + col);
+#pragma unroll
+        for (int u = 0; u < kHalf / 4; ++u)
+          d4[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kHalf; ++u)
+          if (col + u < p.Nr) dst[col + u] = acc[u];
+      }
+    }
+  }
+  // teardown: no MMA may still write TMEM when it is released
+  if (warp == 1 && lane == 0) {
+    if (!mbar_wait(done, 0)) *abort_flag = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

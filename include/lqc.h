@@ -265,6 +265,25 @@ int lqc_contract_all_fp64(const double* A, int rank_a, const int64_t* ext_a,
                           double* C, void* scratch, void* stream);
 int64_t lqc_contract_all_scratch_bytes(int64_t lt, int64_t elems_per_slice);
 
+/* Allocation-free variant of lqc_contract_all_fp64 (the paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they run a contraction -- code inside a stream capture that must not
+ * gain allocation nodes, plugins whose host framework owns every device
+ * allocation, loops that must not block on an allocator).  Same arguments
+ * and result as lqc_contract_all_fp64 minus `scratch`: the partial sums live
+ * in a fixed 64 KiB array inside the library (4096 complex128 slots, kept on
+ * every GPU that loads the library until exit), so the call allocates
+ * nothing.  LQC_ERR_ARG when lt * chunks exceeds the array (lt > 4096 slices
+ * always does).  The first call on a device looks up the array's device
+ * address (make it before any stream capture).  All calls on a device share
+ * the array: calls that overlap on the GPU (unordered streams) race and give
+ * wrong sums; calls on one stream are safe.  Nothing needs clearing between
+ * calls: each call writes every slot it reads. */
+int lqc_contract_all_fp64_noalloc(const double* A, int rank_a, const int64_t* ext_a,
+                                  const double* B, int rank_b, const int64_t* ext_b,
+                                  int npairs, const int* la, const int* ra, int64_t lt,
+                                  double* C, void* stream);
+
 /* Exterior contraction in a mixed precision (LQC_PREC_TF32X3 or
  * LQC_PREC_BF16X3) on complex64 device tensors (interleaved floats), same
  * shapes / semantics as lqc_contract_fp64: each operand is split into hi and

@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--policy", default="tree")
     ap.add_argument("--evict", default="lru")
     ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: replay the whole execute as one CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -249,6 +251,7 @@ def main():
     # ---- device-resident leaves: the kernel-level metric
     nd.stage_leaves(stream)
     nd.set_option(L.LQC_OPT_TIMING, 1)
+    nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
     for _ in range(args.warmup):
         nd.execute(stream)
     nd.wait()
@@ -324,7 +327,8 @@ def main():
             "config": {"workload": args.workload, "lt": wl.lt, "nvec": wl.nvec,
                        "functions": len(wl.functions), "contractions": len(nd.order()),
                        "policy": args.policy, "evict": args.evict, "budget_bytes": budget,
-                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+                       "precision": args.precision, "cuda_graph": bool(args.graph),
+                       "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
                              % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,
                                 info1["arena_bytes"] / 1e9)},

@@ -615,8 +615,11 @@ int exec_run(Dag& g, void* stream) {
     }
   }
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (g.opt_graph) x.tset = 0;  // a captured graph always records timing set 0
   if (g.opt_timing && x.timing_pending[x.tset]) {
-    rc = collect_set(g, x.tset);  // the execute two steps back: normally long done
+    // the execute that last recorded this set: two steps back (normally long
+    // done), or the previous graph replay
+    rc = collect_set(g, x.tset);
     if (rc != LQC_OK) return rc;
   }
   if (g.opt_graph) {
@@ -656,7 +659,7 @@ int exec_run(Dag& g, void* stream) {
   x.ran = true;
   if (g.opt_timing && !x.tev_kind.empty()) {
     x.timing_pending[x.tset] = true;
-    x.tset ^= 1;
+    if (!g.opt_graph) x.tset ^= 1;
   }
   g.measured = x.counted;
   g.info.n_kernels = x.n_kernels;

@@ -422,7 +422,9 @@ int build_program(Dag& g) {
 }
 
 // Issue the program on the streams (also used under graph capture).
-int issue(Dag& g, cudaStream_t cs) {
+int issue(Dag& g, cudaStream_t cs, bool capturing) {
+  // timing events inside a stream capture must become event-record nodes
+  const unsigned tflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   ExecState& x = *g.ex;
   cudaStream_t st[3] = {cs, x.side[S_H2D], x.side[S_D2H]};
   // side streams start after everything already queued on the compute stream
@@ -473,7 +475,7 @@ int issue(Dag& g, cudaStream_t cs) {
         }
         int nk;
         const bool timed = g.opt_timing && tk < x.tev_kind.size();
-        if (timed) CK(cudaEventRecord(x.tev[x.tset][2 * tk], s), "timing record");
+        if (timed) CK(cudaEventRecordWithFlags(x.tev[x.tset][2 * tk], s, tflag), "timing record");
         const bool mixed = g.prec != LQC_PREC_FP64;
         if (in.kind == I_CONTRACT) {
           const ContractDesc& d = x.cdesc[j];
@@ -503,7 +505,7 @@ int issue(Dag& g, cudaStream_t cs) {
         }
         if (nk < 0) return cuda_fail(g, cudaGetLastError(), "contraction launch");
         if (timed) {
-          CK(cudaEventRecord(x.tev[x.tset][2 * tk + 1], s), "timing record");
+          CK(cudaEventRecordWithFlags(x.tev[x.tset][2 * tk + 1], s, tflag), "timing record");
           ++tk;
         }
         x.n_kernels += nk;
@@ -632,7 +634,7 @@ int exec_run(Dag& g, void* stream) {
         own = true;
       }
       CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-      rc = issue(g, cap);
+      rc = issue(g, cap, true);
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamEndCapture(cap, &graph);
       if (rc != LQC_OK) {
@@ -652,7 +654,7 @@ int exec_run(Dag& g, void* stream) {
     }
     CK(cudaGraphLaunch(x.graph, cs), "graph launch");
   } else {
-    rc = issue(g, cs);
+    rc = issue(g, cs, false);
     if (rc != LQC_OK) return rc;
   }
   CK(cudaEventRecord(x.done_ev, cs), "record done");

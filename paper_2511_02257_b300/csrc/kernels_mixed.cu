@@ -402,17 +402,32 @@ struct Split<true> {
   }
 };
 
-// One 32 (rows) x 32 (complex k) block per CTA through shared memory, so that
-// both the gather (along the operand's unit-stride axis) and the plane
-// writes (along k) are coalesced.  which = 0: A operand, 1: B operand.
+template <bool BF16>
+struct PackPair {
+  PackArgs op[2];                          // [0] A operand, [1] B operand
+  const float2* X[2];
+  typename Split<BF16>::T* hi[2];
+  typename Split<BF16>::T* lo[2];
+  int lt;
+};
+
+// Both operands of one contraction in one launch (grid.z = 2 * lt).  One 32
+// (rows) x 32 (complex k) block per CTA through shared memory, so that both
+// the gather (along the operand's unit-stride axis) and the plane writes
+// (along k) are coalesced.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
-k_pack(const float2* __restrict__ X, typename Split<BF16>::T* __restrict__ hi,
-       typename Split<BF16>::T* __restrict__ lo, const PackArgs p) {
+k_pack(const __grid_constant__ PackPair<BF16> pp) {
   typedef typename Split<BF16>::T T;
   __shared__ float2 tile[32][33];
-  const int t = blockIdx.z;
+  const int which = blockIdx.z >= (unsigned)pp.lt ? 1 : 0;
+  const int t = blockIdx.z - which * pp.lt;
+  const PackArgs& p = pp.op[which];
+  const float2* X = pp.X[which];
+  T* hi = pp.hi[which];
+  T* lo = pp.lo[which];
   const unsigned r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  if (r0 >= (unsigned)p.rows) return;  // the grid spans the larger operand
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   X += (long long)t * p.ts;
 #pragma unroll
@@ -451,6 +466,18 @@ k_pack(const float2* __restrict__ X, typename Split<BF16>::T* __restrict__ hi,
 }
 
 // ------------------------------------------------------------ K2m
+// (sh, sl) += a * b without rounding loss: the product's exact error from an
+// FMA and Knuth's TwoSum for the addition; the _rn intrinsics keep the
+// compiler from contracting these steps into other FMAs.
+__device__ __forceinline__ void df_acc_prod(float& sh, float& sl, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
 __global__ void __launch_bounds__(256)
 k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
                    double2* __restrict__ part, const ContractAllDesc p) {
@@ -461,15 +488,18 @@ k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
   const unsigned hi = (unsigned)(((unsigned long long)S * (c + 1)) / p.chunks);
   A += t * p.S;
   B += t * p.S;
-  double re = 0.0, im = 0.0;
+  // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
+  // ~44 significant bits) at FP32 throughput; across threads and blocks: FP64
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (unsigned i = lo + threadIdx.x; i < hi; i += 256) {
     const float2 a = A[i];
     const float2 b = B[goff(p.bp, i)];
-    re = fma((double)a.x, (double)b.x, re);
-    re = fma(-(double)a.y, (double)b.y, re);
-    im = fma((double)a.x, (double)b.y, im);
-    im = fma((double)a.y, (double)b.x, im);
+    df_acc_prod(rh, rl, a.x, b.x);
+    df_acc_prod(rh, rl, -a.y, b.y);
+    df_acc_prod(ih, il, a.x, b.y);
+    df_acc_prod(ih, il, a.y, b.x);
   }
+  double re = (double)rh + (double)rl, im = (double)ih + (double)il;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     re += __shfl_down_sync(0xffffffffu, re, o);
@@ -593,17 +623,35 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
   void* bhi = sc + d.b_off;
   void* blo = sc + d.b_off + d.plane_b;
   int nk = 0;
-  for (int which = 0; which < 2; ++which) {
-    PackArgs pa = pack_args(cd, which, d.kp);
+  {
     const int64_t kc = std::max<int64_t>(cd.K, d.kp / 2);  // complex columns incl. padding
-    dim3 grid((unsigned)((kc + 31) / 32), (unsigned)((pa.rows + 31) / 32), (unsigned)cd.lt);
-    const float2* X = reinterpret_cast<const float2*>(which == 0 ? A : B);
-    if (d.bf16)
-      k_pack<true><<<grid, 256, 0, s>>>(X, (__nv_bfloat16*)(which ? bhi : ahi),
-                                         (__nv_bfloat16*)(which ? blo : alo), pa);
-    else
-      k_pack<false><<<grid, 256, 0, s>>>(X, (float*)(which ? bhi : ahi),
-                                          (float*)(which ? blo : alo), pa);
+    const int64_t rows = std::max<int64_t>(cd.M, cd.N);
+    dim3 grid((unsigned)((kc + 31) / 32), (unsigned)((rows + 31) / 32), (unsigned)(2 * cd.lt));
+    if (d.bf16) {
+      PackPair<true> pp;
+      pp.op[0] = pack_args(cd, 0, d.kp);
+      pp.op[1] = pack_args(cd, 1, d.kp);
+      pp.X[0] = reinterpret_cast<const float2*>(A);
+      pp.X[1] = reinterpret_cast<const float2*>(B);
+      pp.hi[0] = (__nv_bfloat16*)ahi;
+      pp.lo[0] = (__nv_bfloat16*)alo;
+      pp.hi[1] = (__nv_bfloat16*)bhi;
+      pp.lo[1] = (__nv_bfloat16*)blo;
+      pp.lt = (int)cd.lt;
+      k_pack<true><<<grid, 256, 0, s>>>(pp);
+    } else {
+      PackPair<false> pp;
+      pp.op[0] = pack_args(cd, 0, d.kp);
+      pp.op[1] = pack_args(cd, 1, d.kp);
+      pp.X[0] = reinterpret_cast<const float2*>(A);
+      pp.X[1] = reinterpret_cast<const float2*>(B);
+      pp.hi[0] = (float*)ahi;
+      pp.lo[0] = (float*)alo;
+      pp.hi[1] = (float*)bhi;
+      pp.lo[1] = (float*)blo;
+      pp.lt = (int)cd.lt;
+      k_pack<false><<<grid, 256, 0, s>>>(pp);
+    }
     ++nk;
   }
   CUtensorMap m_ahi, m_alo, m_bhi, m_blo;

@@ -106,6 +106,7 @@ typedef struct {
   int64_t n_contract, n_contract_all;     /* launches                         */
   double ms_contract, ms_contract_all;    /* summed kernel time (ms)          */
   int64_t flops_contract, flops_contract_all;
+  int64_t host_arena_bytes; /* pinned host bytes holding written-back tensors */
 } lqc_exec_info;
 
 /* Option keys for lqc_dag_set_option. */

@@ -128,8 +128,8 @@ struct ExecState {
   std::vector<int32_t> slot_of;           // node -> results slot (-1)
   double* scratch = nullptr;
   int64_t scratch_bytes = 0;
-  std::vector<void*> host_slot;           // write-back copies (pinned)
-  std::vector<int64_t> host_slot_bytes;
+  char* host_arena = nullptr;             // pinned write-back copies, placed per plan
+  int64_t host_arena_bytes = 0;
   std::vector<void*> staged;              // node -> device copy of a leaf
   bool staged_valid = false;
   int64_t flops = 0, copy_h2d = 0, copy_d2h = 0, n_kernels = 0;
@@ -191,10 +191,8 @@ void free_program(ExecState& x) {
   if (x.mscratch) { cudaFree(x.mscratch); x.mscratch = nullptr; }
   x.mscratch_bytes = 0;
   x.mdesc.clear();
-  for (void* p : x.host_slot)
-    if (p) cudaFreeHost(p);
-  x.host_slot.clear();
-  x.host_slot_bytes.clear();
+  if (x.host_arena) { cudaFreeHost(x.host_arena); x.host_arena = nullptr; }
+  x.host_arena_bytes = 0;
   x.prog.clear();
   x.cdesc.clear();
   x.adesc.clear();
@@ -211,6 +209,11 @@ int build_program(Dag& g) {
   std::vector<int64_t> off(N, -1);
   std::vector<int32_t> last_compute(N, -1), last_h2d(N, -1), last_d2h(N, -1), writer(N, -1);
   std::vector<int32_t> wb_instr(N, -1);  // write-back that filled the node's host slot
+  // host copies of written-back tensors live from their write-back to the
+  // tensor's final release; their bytes are placed like the device arena, a
+  // write-back into reused bytes waiting for the reloads of the previous owner
+  std::vector<int64_t> hoff(N, -1);
+  Placer hpl;
   std::vector<uint8_t> waited_for_load(N, 0);
   x.slot_of.assign(N, -1);
   x.root_ids.clear();
@@ -220,8 +223,6 @@ int build_program(Dag& g) {
       x.root_ids.push_back(u);
     }
   x.n_results = (int64_t)x.root_ids.size();
-  x.host_slot.assign(N, nullptr);
-  x.host_slot_bytes.assign(N, 0);
   Placer pl;
   int64_t scratch_need = 0, mscratch_need = 0;
   std::vector<Instr>& P = x.prog;
@@ -268,7 +269,10 @@ int build_program(Dag& g) {
       in.dst = pl.alloc(in.bytes, dep);
       add_wait(in, dep[S_COMPUTE]);
       add_wait(in, dep[S_D2H]);
-      if (!n.is_leaf()) add_wait(in, wb_instr[u]);  // reload after the write-back landed
+      if (!n.is_leaf()) {
+        add_wait(in, wb_instr[u]);  // reload after the write-back landed
+        in.src[0] = hoff[u];        // host offset of the copy
+      }
       off[u] = in.dst;
       P.push_back(in);
       x.cdesc.emplace_back();
@@ -286,20 +290,27 @@ int build_program(Dag& g) {
         in.stream = S_D2H;
         in.node = u;
         in.bytes = g.size_bytes(u);
-        in.dst = -1;
         in.src[0] = off[u];
         in.src[1] = -1;
+        int32_t hdep[3];
+        in.dst = hpl.alloc(in.bytes, hdep);  // host offset
+        hoff[u] = in.dst;
         add_wait(in, writer[u]);
+        add_wait(in, hdep[S_H2D]);  // the previous owner's reloads have read these bytes
         P.push_back(in);
         x.cdesc.emplace_back();
         x.adesc.emplace_back();
         x.mdesc.emplace_back();
         last_d2h[u] = (int32_t)P.size() - 1;
         wb_instr[u] = last_d2h[u];
-        x.host_slot_bytes[u] = in.bytes;
       }
       release(u);
     } else if (op.kind == OP_FREE) {
+      if (hoff[u] >= 0) {  // final release: the host copy is dead too
+        int32_t hdep[3] = {-1, last_h2d[u], wb_instr[u]};
+        hpl.release(hoff[u], g.size_bytes(u), hdep);
+        hoff[u] = -1;
+      }
       release(u);
     } else {  // CONTRACT
       Instr in{};
@@ -409,10 +420,10 @@ int build_program(Dag& g) {
   x.mscratch_bytes = mscratch_need;
   if (mscratch_need > 0)
     CK(cudaMalloc((void**)&x.mscratch, (size_t)mscratch_need), "plane scratch cudaMalloc");
-  for (int64_t u = 0; u < N; ++u)
-    if (x.host_slot_bytes[u] > 0)
-      CK(cudaHostAlloc(&x.host_slot[u], (size_t)x.host_slot_bytes[u], cudaHostAllocDefault),
-         "pinned write-back slot");
+  x.host_arena_bytes = hpl.top;
+  if (hpl.top > 0)
+    CK(cudaHostAlloc((void**)&x.host_arena, (size_t)hpl.top, cudaHostAllocDefault),
+       "pinned write-back arena");
   x.prog_valid = true;
   x.tset = 0;
   g.info.n_contract = g.info.n_contract_all = 0;
@@ -443,7 +454,7 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
     const Node& n = g.nodes[in.node];
     switch (in.kind) {
       case I_LOAD: {
-        const void* src = n.is_leaf() ? n.host : x.host_slot[in.node];
+        const void* src = n.is_leaf() ? n.host : (const void*)(x.host_arena + in.src[0]);
         CK(cudaMemcpyAsync(x.arena + in.dst, src, (size_t)in.bytes, cudaMemcpyHostToDevice, s),
            "H2D load");
         x.copy_h2d += in.bytes;
@@ -452,7 +463,7 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
         break;
       }
       case I_WRITEBACK: {
-        CK(cudaMemcpyAsync(x.host_slot[in.node], x.arena + in.src[0], (size_t)in.bytes,
+        CK(cudaMemcpyAsync(x.host_arena + in.dst, x.arena + in.src[0], (size_t)in.bytes,
                            cudaMemcpyDeviceToHost, s),
            "D2H write-back");
         x.copy_d2h += in.bytes;
@@ -667,6 +678,7 @@ int exec_run(Dag& g, void* stream) {
   g.info.n_kernels = x.n_kernels;
   g.info.flops = x.flops;
   g.info.arena_bytes = x.arena_bytes;
+  g.info.host_arena_bytes = x.host_arena_bytes;
   g.info.copied_h2d = x.copy_h2d;
   g.info.copied_d2h = x.copy_d2h;
   g.info.n_ops = (int64_t)g.ops.size();

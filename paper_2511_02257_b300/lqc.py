@@ -54,7 +54,7 @@ class lqc_exec_info(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in ("n_kernels", "flops", "arena_bytes", "copied_h2d",
                                      "copied_d2h", "n_ops", "n_contract", "n_contract_all")] + \
         [("ms_contract", ctypes.c_double), ("ms_contract_all", ctypes.c_double),
-         ("flops_contract", c_i64), ("flops_contract_all", c_i64)]
+         ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

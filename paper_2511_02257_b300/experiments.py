@@ -14,6 +14,11 @@ copy), so a schedule can change the time but never a result.
 
 Prints one JSON line per policy, then a summary line with ratios to the
 naive order.
+
+  python -m paper_2511_02257_b300.experiments kernel --shape pxp --n 64 --lt 64
+         [--precision tf32x3|bf16x3|fp64] [--reps 20]
+
+times one contraction shape through the single-contraction C ABI.
 """
 from __future__ import annotations
 
@@ -29,7 +34,87 @@ import numpy as np
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 
+SHAPES = {
+    # name: (left extents, right extents, la, ra) with N = distillation size
+    "pxp": lambda n: ((4, 4, n, n), (4, 4, n, n), (1, 3), (0, 2)),   # over spin + distillation
+    "pxm": lambda n: ((4, 4, n, n), (n, n), (3,), (0,)),             # propagator x meson
+    "mxm": lambda n: ((n, n), (n, n), (1,), (0,)),                   # meson x meson
+    "bxb": lambda n: ((n, n, n), (n, n, n), (1, 2), (0, 1)),         # baryon x baryon, 2 legs
+}
+
+
+def kernel_bench(argv):
+    """One contraction shape through the single-contraction C ABI, timed with
+    CUDA events over `--reps` launches after warm-up."""
+    import ctypes
+    import torch
+    import paper_2511_02257_b300 as L
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", default="pxp", choices=sorted(SHAPES))
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--lt", type=int, default=64)
+    ap.add_argument("--precision", default="tf32x3")
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args(argv)
+    sa, sb, la, ra = SHAPES[args.shape](args.n)
+    lt = args.lt
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PI = ctypes.POINTER(ctypes.c_int)
+    ea = np.asarray(sa, np.int64)
+    eb = np.asarray(sb, np.int64)
+    xa = np.asarray(la, np.intc)
+    xb = np.asarray(ra, np.intc)
+    pa, pb = ea.ctypes.data_as(P64), eb.ctypes.data_as(P64)
+    pla, pra = xa.ctypes.data_as(PI), xb.ctypes.data_as(PI)
+    K = int(np.prod([sa[i] for i in la]))
+    M = int(np.prod(sa)) // K
+    N = int(np.prod(sb)) // K
+    out_elems = lt * M * N
+    g = torch.Generator(device="cuda").manual_seed(1)
+    prec = L.PRECISIONS[args.precision]
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    if prec == L.LQC_PREC_FP64:
+        A = torch.randn((lt,) + sa, dtype=torch.complex128, device="cuda", generator=g)
+        B = torch.randn((lt,) + sb, dtype=torch.complex128, device="cuda", generator=g)
+        C = torch.empty(out_elems, dtype=torch.complex128, device="cuda")
+
+        def run():
+            assert L.lqc_contract_fp64(vp(A), len(sa), pa, vp(B), len(sb), pb, len(la), pla, pra,
+                                       lt, vp(C), None) == 0
+    else:
+        A = torch.randn((lt,) + sa, dtype=torch.complex64, device="cuda", generator=g)
+        B = torch.randn((lt,) + sb, dtype=torch.complex64, device="cuda", generator=g)
+        C = torch.empty(out_elems, dtype=torch.complex64, device="cuda")
+        nbytes = L.lqc_contract_mixed_scratch_bytes(len(sa), pa, len(sb), pb, len(la), pla, pra,
+                                                    lt, prec)
+        S = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+        def run():
+            assert L.lqc_contract_mixed(vp(A), len(sa), pa, vp(B), len(sb), pb, len(la), pla, pra,
+                                        lt, prec, vp(C), vp(S), None) == 0
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    flops = 8.0 * lt * M * N * K
+    elem = 16 if prec == L.LQC_PREC_FP64 else 8
+    alg_bytes = lt * (M * K + K * N + M * N) * elem
+    print(json.dumps({"shape": args.shape, "n": args.n, "lt": lt, "M": M, "N": N, "K": K,
+                      "precision": args.precision, "ms_per_contraction": ms,
+                      "complex_tflops": flops / ms / 1e9,
+                      "tensor_tflops": (3 if prec != L.LQC_PREC_FP64 else 1) * flops / ms / 1e9,
+                      "algorithmic_gbs": alg_bytes / ms / 1e6}), flush=True)
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "kernel":
+        return kernel_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

@@ -171,11 +171,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Warp roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
-// warps 2..9 = drain/epilogue (warp w reads TMEM lanes 32*(w%4) .. +31, i.e.
-// one output row per thread, and one half of the kBN columns).  TMEM holds two accumulator buffers of
-// 2*kBN columns each (main + correction); the MMA thread fills one while the
-// drain warps empty the other into FP32 registers every kChunkBlocks k-blocks.
+// Persistent: CTA c handles tiles c, c + gridDim.x, ...; tiles are ordered
+// n-tile fastest, then m-tile, then (slice, k split), so neighbouring CTAs
+// share operand tiles in L2.  Warp roles: warp 0 lane 0 = TMA producer,
+// warp 1 lane 0 = MMA issuer, warps 2..9 = drain/epilogue (warp w reads TMEM
+// lanes 32*(w%4) .. +31, i.e. one output row per thread, and one half of the
+// kBN columns).  All roles walk the same flattened (tile, k-block) sequence:
+// the shared-memory ring and the two TMEM accumulator buffers (each 2*kBN
+// columns: main + correction) keep cycling across tiles, so a tile's store
+// overlaps the next tile's MMAs.  The drain warps empty a buffer every
+// kChunkBlocks k-blocks into FP32 registers.
 template <bool BF16>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
@@ -194,10 +199,9 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
-  const int t = blockIdx.z % p.lt, split = blockIdx.z / p.lt;
-  const int kb0 = split * p.kblocks;
-  const int nchunks = (p.kblocks + kChunkBlocks - 1) / kChunkBlocks;
+  const int ntn = (p.Nr + kBN - 1) / kBN, ntm = (p.M + kBM - 1) / kBM;
+  const int ntiles = ntn * ntm * p.lt * p.splits;
+  const int chunks_per_tile = (p.kblocks + kChunkBlocks - 1) / kChunkBlocks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -226,22 +230,31 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer
-      int issued = 0;
-      for (int i = 0; i < p.kblocks; ++i) {
-        const int s = i % kStages;
-        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; break; }
-        if (*abort_flag) break;
-        uint8_t* st = smem + s * C::kStageBytes;
-        mbar_expect_tx(&full[s], C::kStageBytes);
-        const int k0 = (kb0 + i) * C::kBK;
-        tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
-        tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
-        tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
-        tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
-        ++issued;
+      int g = 0, issued = 0;  // k-blocks walked / issued by this CTA
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        const int tn = tile % ntn, tm = (tile / ntn) % ntm, z = tile / (ntn * ntm);
+        const int t = z % p.lt, split = z / p.lt;
+        const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * p.kblocks;
+        for (int i = 0; i < p.kblocks; ++i, ++g) {
+          const int s = g % kStages;
+          const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          uint8_t* st = smem + s * C::kStageBytes;
+          mbar_expect_tx(&full[s], C::kStageBytes);
+          const int k0 = (kb0 + i) * C::kBK;
+          tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
+          tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
+          tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
+          tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
+          issued = g + 1;
+        }
       }
-      // drain: every issued stage must have landed before the CTA exits
+      // every issued stage must have landed before the CTA exits
       for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
         if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) break;
     }
@@ -249,35 +262,47 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
     if (lane == 0) {
       // ---- MMA issuer
       constexpr uint32_t idesc = make_idesc<BF16>();
-      for (int i = 0; i < p.kblocks; ++i) {
-        const int c = i / kChunkBlocks, b = c & 1;
-        const bool first = (i % kChunkBlocks) == 0;
-        const bool last = (i % kChunkBlocks) == kChunkBlocks - 1 || i == p.kblocks - 1;
-        if (first) {  // wait until the drain warps have emptied this buffer
-          if (!mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u) || *abort_flag) {
+      int g = 0, cc = 0;  // k-blocks and accumulation chunks walked
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        for (int i = 0; i < p.kblocks; ++i, ++g) {
+          const int b = cc & 1;
+          const bool first = (i % kChunkBlocks) == 0;
+          const bool last = (i % kChunkBlocks) == kChunkBlocks - 1 || i == p.kblocks - 1;
+          if (first) {  // wait until the drain warps have emptied this buffer
+            if (!mbar_wait(&tempty[b], ((uint32_t)(cc >> 1) & 1u) ^ 1u) || *abort_flag) {
+              *abort_flag = 1;
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          const int s = g % kStages;
+          const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph) || *abort_flag) {
             *abort_flag = 1;
+            stop = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        }
-        const int s = i % kStages;
-        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-        if (!mbar_wait(&full[s], ph) || *abort_flag) { *abort_flag = 1; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t base = smem_u32(smem + s * C::kStageBytes);
-        const uint32_t ahi = base, alo = base + C::kATile;
-        const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
-        const uint32_t dmain = tmem + (uint32_t)(b * 2 * kBN), dcorr = dmain + kBN;
+          const uint32_t base = smem_u32(smem + s * C::kStageBytes);
+          const uint32_t ahi = base, alo = base + C::kATile;
+          const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
+          const uint32_t dmain = tmem + (uint32_t)(b * 2 * kBN), dcorr = dmain + kBN;
 #pragma unroll
-        for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
-          const uint32_t off = kk * 32;
-          const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
-          umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
-          umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
-          umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+          for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
+            const uint32_t off = kk * 32;
+            const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
+            umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
+            umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+            umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+          }
+          umma_commit(&empty[s]);    // stage reusable once these MMAs have read it
+          if (last) {
+            umma_commit(&tfull[b]);
+            ++cc;
+          }
         }
-        umma_commit(&empty[s]);      // stage reusable once these MMAs have read it
-        if (last) umma_commit(&tfull[b]);
       }
       umma_commit(done);             // all issued MMAs complete (or abandoned)
     }
@@ -286,49 +311,54 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
     constexpr int kHalf = kBN / 2;
     const int q = warp & 3;          // TMEM lane quarter of this warp
     const int c0 = ((warp - 2) >> 2) * kHalf;  // first column of this warp's half
-    const int row = m0 + q * 32 + lane;
     const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-    float acc[kHalf];
+    int cc = 0, ok = 1;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int tn = tile % ntn, tm = (tile / ntn) % ntm, z = tile / (ntn * ntm);
+      const int t = z % p.lt, split = z / p.lt;
+      const int row = tm * kBM + q * 32 + lane;
+      float acc[kHalf];
 #pragma unroll
-    for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
-    int ok = 1;
-    for (int c = 0; c < nchunks; ++c) {
-      const int b = c & 1;
-      if (lane == 0) {
-        if (!mbar_wait(&tfull[b], (uint32_t)(c >> 1) & 1u) || *abort_flag) {
-          *abort_flag = 1;
-          ok = 0;
+      for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
+      for (int c = 0; c < chunks_per_tile; ++c, ++cc) {
+        const int b = cc & 1;
+        if (lane == 0) {
+          if (!mbar_wait(&tfull[b], (uint32_t)(cc >> 1) & 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tb = tmem + tlane + (uint32_t)(b * 2 * kBN);
+#pragma unroll
+        for (int j = 0; j < kHalf; j += 16) {
+          uint32_t r[16], rc[16];
+          tmem_ld16(tb + j, r);      // collective: every lane loads, in-range or not
+          tmem_ld16(tb + kBN + j, rc);
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            acc[j + u] += __uint_as_float(r[u]) + __uint_as_float(rc[u]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t tb = tmem + tlane + (uint32_t)(b * 2 * kBN);
+      if (ok && row < p.M) {
+        float* dst =
+            p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
+        const int col = tn * kBN + c0;
+        if (col + kHalf <= p.Nr && (p.Nr & 3) == 0) {
+          float4* d4 = reinterpret_cast<float4*>(dst + col);
 #pragma unroll
-      for (int j = 0; j < kHalf; j += 16) {
-        uint32_t r[16], rc[16];
-        tmem_ld16(tb + j, r);        // collective: every lane loads, in-range or not
-        tmem_ld16(tb + kBN + j, rc);
+          for (int u = 0; u < kHalf / 4; ++u)
+            d4[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          acc[j + u] += __uint_as_float(r[u]) + __uint_as_float(rc[u]);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
-    }
-    if (ok && row < p.M) {
-      float* dst = p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
-      const int col = n0 + c0;
-      if (col + kHalf <= p.Nr && (p.Nr & 3) == 0) {
-        float4* d4 = reinterpret_cast<float4*>(dst + col);
-#pragma unroll
-        for (int u = 0; u < kHalf / 4; ++u)
-          d4[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < kHalf; ++u)
-          if (col + u < p.Nr) dst[col + u] = acc[u];
+          for (int u = 0; u < kHalf; ++u)
+            if (col + u < p.Nr) dst[col + u] = acc[u];
+        }
       }
     }
   }
@@ -430,13 +460,23 @@ k_pack(const __grid_constant__ PackPair<BF16> pp) {
   if (r0 >= (unsigned)p.rows) return;  // the grid spans the larger operand
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   X += (long long)t * p.ts;
+  // the index decompositions of this block's 32 rows and 32 k once, not per element
+  __shared__ long long roff[32], koff[32];
+  if (threadIdx.x < 32) {
+    const unsigned r = r0 + threadIdx.x;
+    roff[threadIdx.x] = r < (unsigned)p.rows ? goff(p.rg, r) : 0;
+  } else if (threadIdx.x < 64) {
+    const unsigned k = k0 + threadIdx.x - 32;
+    koff[threadIdx.x - 32] = k < (unsigned)p.K ? goff(p.kg, k) : 0;
+  }
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     unsigned r, k;
     if (p.k_fast) { k = k0 + tx; r = r0 + ty + 8 * j; }
     else { r = r0 + tx; k = k0 + ty + 8 * j; }
     float2 v = make_float2(0.f, 0.f);
-    if (r < (unsigned)p.rows && k < (unsigned)p.K) v = X[goff(p.rg, r) + goff(p.kg, k)];
+    if (r < (unsigned)p.rows && k < (unsigned)p.K) v = X[roff[r - r0] + koff[k - k0]];
     tile[r - r0][k - k0] = v;
   }
   __syncthreads();
@@ -562,6 +602,18 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t r
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+int num_sms() {  // SMs of the current device (one persistent CTA each)
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 148;
+  }
+  return cached[dev];
+}
+
 }  // namespace
 
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
@@ -667,8 +719,8 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
   g.splits = d.splits;
   g.lt = (int)cd.lt;
   g.out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
-  dim3 grid((unsigned)((g.Nr + kBN - 1) / kBN), (unsigned)((g.M + kBM - 1) / kBM),
-            (unsigned)(cd.lt * d.splits));
+  const int64_t tiles = ((g.Nr + kBN - 1) / kBN) * ((g.M + kBM - 1) / kBM) * cd.lt * d.splits;
+  dim3 grid((unsigned)std::min<int64_t>(tiles, num_sms()));
   if (d.bf16) {
     const int smem = GemmCfg<true>::kSmem;
     cudaFuncSetAttribute(k_gemm_split3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

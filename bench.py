@@ -215,6 +215,27 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def shape_breakdown(wl, ids, times, n_exec):
+    """Kernel ms per execution grouped by contraction shape (M, N, K per slice;
+    K alone for a correlator), largest first."""
+    ext = wl.stream_extents()
+    shape = {}
+    for j, rq in enumerate(wl.requests):
+        le = ext[rq.left]
+        k = int(np.prod([le[a] for a in rq.la]))
+        m = int(np.prod(le)) // k
+        n = int(np.prod(ext[rq.right])) // k
+        shape[ids[len(wl.leaves) + j]] = "corr K=%d" % k if not ext[len(wl.leaves) + j] \
+            else "%dx%dx%d" % (m, n, k)
+    agg = {}
+    for node, ms in times.items():
+        key = shape.get(node, "?")
+        c, t = agg.get(key, (0, 0.0))
+        agg[key] = (c + 1, t + ms / max(n_exec, 1))
+    top = sorted(agg.items(), key=lambda kv: -kv[1][1])[:8]
+    return [{"shape": k, "count": c, "ms": round(t, 3)} for k, (c, t) in top]
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init()
@@ -239,8 +260,8 @@ def main():
     wl = synth.make_workload(args.workload, seed=rank)
     budget = wl.budget_bytes
     t0 = time.perf_counter()
-    nd, _ = L.build_dag(wl, precision=args.precision,
-                        leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd, ids = L.build_dag(wl, precision=args.precision,
+                          leaf_data_fn=lambda li: synth.leaf_data(wl, li))
     t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
     planned = nd.schedule(args.policy, args.evict, budget)
@@ -281,6 +302,7 @@ def main():
     fl_c = info1["flops_contract"] - info0["flops_contract"]
     ms_a = info1["ms_contract_all"] - info0["ms_contract_all"]
     achieved = fl_c / (ms_c * 1e-3) / 1e12 if ms_c > 0 else None
+    breakdown = shape_breakdown(wl, ids, nd.kernel_times(), args.warmup + args.steps)
     probe = L.measure_fp64_peak()
     kernels = info1["n_kernels"]
 
@@ -347,6 +369,7 @@ def main():
                          "traffic": TRAFFIC_PER_LAUNCH,
                          "launches": n_c, "kernel_ms_per_step": ms_c / args.steps,
                          "contract_all_ms_per_step": ms_a / args.steps},
+            "kernel_ms_by_shape": breakdown,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -234,6 +234,13 @@ int lqc_dag_node_info(lqc_dag* dag, int64_t id, int64_t* size_bytes, int* rank,
 int lqc_dag_get_stats(lqc_dag* dag, lqc_stats* measured);
 int lqc_dag_get_exec_info(lqc_dag* dag, lqc_exec_info* info);
 
+/* With LQC_OPT_TIMING: per contraction (exterior or contract-all) of the
+ * plan, its node id and its kernel time in ms summed over the same executes
+ * as lqc_exec_info (waits for them).  Same cap / *n convention as
+ * lqc_dag_get_order; *n = 0 when timing is off. */
+int lqc_dag_get_kernel_times(lqc_dag* dag, int64_t* node, double* ms, int64_t cap,
+                             int64_t* n);
+
 /* Human-readable description of the last error on `dag` ("" if none).  The
  * string is owned by the DAG and valid until its next call. */
 const char* lqc_last_error(const lqc_dag* dag);

@@ -398,6 +398,13 @@ int lqc_dag_get_exec_info(lqc_dag* h, lqc_exec_info* info) {
   LQC_GUARD_END(h)
 }
 
+int lqc_dag_get_kernel_times(lqc_dag* h, int64_t* node, double* ms, int64_t cap, int64_t* n) {
+  if (!h || !n) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  return lqc::exec_kernel_times(h->d, node, ms, cap, n);
+  LQC_GUARD_END(h)
+}
+
 const char* lqc_last_error(const lqc_dag* h) {
   if (!h) return "null DAG handle";
   return h->d.err.c_str();

@@ -142,6 +142,8 @@ struct ExecState {
   std::vector<cudaEvent_t> tev[2];
   std::vector<int32_t> tev_kind;
   std::vector<int64_t> tev_flops;
+  std::vector<int64_t> tev_node;          // node of each timed instruction
+  std::vector<double> tev_ms;             // summed duration per timed instruction
   bool timing_pending[2] = {false, false};
   int tset = 0;
 };
@@ -182,6 +184,8 @@ void free_program(ExecState& x) {
     x.timing_pending[k] = false;
   }
   x.tev_kind.clear();
+  x.tev_node.clear();
+  x.tev_ms.clear();
   x.tev_flops.clear();
   for (cudaEvent_t e : x.ev) cudaEventDestroy(e);
   x.ev.clear();
@@ -407,6 +411,8 @@ int build_program(Dag& g) {
       x.tev_kind.push_back(P[j].kind);
       const ContractDesc& cd = x.cdesc[j];
       const ContractAllDesc& ad = x.adesc[j];
+      x.tev_node.push_back(P[j].node);
+      x.tev_ms.push_back(0.0);
       x.tev_flops.push_back(P[j].kind == I_CONTRACT ? 8 * cd.lt * cd.M * cd.N * cd.K
                                                       : 8 * ad.lt * ad.S);
     }
@@ -595,6 +601,7 @@ int collect_set(Dag& g, int set) {
   for (size_t k = 0; k < x.tev_kind.size(); ++k) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]), "timing elapsed");
+    x.tev_ms[k] += ms;
     if (x.tev_kind[k] == I_CONTRACT) {
       g.info.n_contract++;
       g.info.ms_contract += ms;
@@ -725,6 +732,26 @@ int exec_collect_timing(Dag& g) {
     if (!x.timing_pending[set]) continue;
     int rc = collect_set(g, set);
     if (rc != LQC_OK) return rc;
+  }
+  return LQC_OK;
+}
+
+int exec_kernel_times(Dag& g, int64_t* node, double* ms, int64_t cap, int64_t* n) {
+  int rc = exec_collect_timing(g);
+  if (rc != LQC_OK) return rc;
+  if (!g.ex) {
+    *n = 0;
+    return LQC_OK;
+  }
+  ExecState& x = *g.ex;
+  *n = (int64_t)x.tev_node.size();
+  if (cap < *n || (*n > 0 && (!node || !ms))) {
+    g.err = "output capacity too small";
+    return LQC_ERR_ARG;
+  }
+  for (int64_t k = 0; k < *n; ++k) {
+    node[k] = x.tev_node[k];
+    ms[k] = x.tev_ms[k];
   }
   return LQC_OK;
 }

@@ -93,6 +93,7 @@ int64_t model_peak(const Dag& g, const std::vector<int64_t>& order);
 int exec_run(Dag& g, void* stream);
 int exec_wait(Dag& g, int64_t timeout_ms);
 int exec_collect_timing(Dag& g);
+int exec_kernel_times(Dag& g, int64_t* node, double* ms, int64_t cap, int64_t* n);
 int exec_read(Dag& g, int64_t root, double* out);
 int exec_read_all(Dag& g, double* out, int64_t cap);
 int exec_stage_leaves(Dag& g, void* stream);

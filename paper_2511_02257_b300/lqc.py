@@ -91,6 +91,7 @@ _sig("lqc_dag_node_info", ctypes.c_int, [c_vp, c_i64, P_i64, P_int, P_int])
 _sig("lqc_dag_get_stats", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_stats)])
 _sig("lqc_dag_get_exec_info", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_exec_info)])
 _sig("lqc_last_error", ctypes.c_char_p, [c_vp])
+_sig("lqc_dag_get_kernel_times", ctypes.c_int, [c_vp, P_i64, P_dbl, c_i64, P_i64])
 _sig("lqc_contract_fp64", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, ctypes.c_int, P_i64,
                                          ctypes.c_int, P_int, P_int, c_i64, c_vp, c_vp])
 _sig("lqc_contract_all_fp64", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, ctypes.c_int, P_i64,
@@ -114,6 +115,7 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_
            "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_read_correlator",
            "lqc_dag_read_all_correlators", "lqc_dag_get_roots", "lqc_dag_num_nodes",
            "lqc_dag_node_info", "lqc_dag_get_stats", "lqc_dag_get_exec_info", "lqc_last_error",
+           "lqc_dag_get_kernel_times",
            "lqc_contract_fp64", "lqc_contract_all_fp64", "lqc_contract_all_scratch_bytes",
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
            "lqc_contract_all_c64", "lqc_mixed_error"):
@@ -289,6 +291,19 @@ class Dag:
         st = lqc_stats()
         self._check(_lib.lqc_dag_get_stats(self.h, ctypes.byref(st)), "get_stats")
         return st.as_dict()
+
+    def kernel_times(self):
+        """{node id: summed kernel ms} of the timed contractions."""
+        n = c_i64()
+        self._check(_lib.lqc_dag_get_kernel_times(self.h, None, None, 0, ctypes.byref(n)),
+                    "get_kernel_times")
+        m = max(n.value, 1)
+        nodes = np.zeros(m, dtype=np.int64)
+        ms = np.zeros(m, dtype=np.float64)
+        self._check(_lib.lqc_dag_get_kernel_times(self.h, nodes.ctypes.data_as(P_i64),
+                                                  ms.ctypes.data_as(P_dbl), m, ctypes.byref(n)),
+                    "get_kernel_times")
+        return {int(nodes[i]): float(ms[i]) for i in range(n.value)}
 
     def exec_info(self) -> dict:
         info = lqc_exec_info()

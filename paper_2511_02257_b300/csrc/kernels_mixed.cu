@@ -148,14 +148,38 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 }
 
 // ------------------------------------------------------------ K4 GEMM
-struct GemmArgs {
-  int M;          // rows of A'
-  int Nr;         // rows of B'T = real columns of D'
-  int kblocks;    // k blocks (of kBK elements) per split
-  int splits;     // k splits (grid.z = lt * splits)
-  int lt;
-  float* out;     // splits == 1: D' [lt][M][Nr]; else partial [splits][lt][M][Nr]
+// One GEMM of the split form: tensor maps of the four planes, output and
+// tiling.  A launch covers one task (single contraction, passed as a kernel
+// parameter) or a table of tasks in global memory (a grouped window level);
+// tiles of all tasks form one sequence, task k owning
+// [tile_start, tile_start + tiles).
+struct alignas(64) GemmTask {
+  CUtensorMap map[4];   // Ahi, Alo, Bhi, Blo
+  float* out;           // splits == 1: D' [lt][M][Nr]; else partials [splits][lt][M][Nr]
+  int M, Nr, kblocks, splits, lt, ntn, ntm, tiles;
+  long long tile_start;
 };
+
+struct GemmParams {
+  GemmTask single;        // used when tasks == nullptr
+  const GemmTask* tasks;  // grouped launch: task table in global memory
+  int ntasks;
+  long long total_tiles;
+};
+
+// task owning global tile g; k is a cursor that only moves forward (a CTA's
+// tiles increase)
+__device__ __forceinline__ const GemmTask* tile_task(const GemmParams& gp, long long g, int& k,
+                                                     int& local) {
+  if (!gp.tasks) {
+    local = (int)g;
+    return &gp.single;
+  }
+  while (g >= gp.tasks[k].tile_start + gp.tasks[k].tiles) ++k;
+  local = (int)(g - gp.tasks[k].tile_start);
+  return &gp.tasks[k];
+}
+
 
 template <bool BF16>
 struct GemmCfg {
@@ -171,21 +195,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Persistent: CTA c handles tiles c, c + gridDim.x, ...; tiles are ordered
-// n-tile fastest, then m-tile, then (slice, k split), so neighbouring CTAs
-// share operand tiles in L2.  Warp roles: warp 0 lane 0 = TMA producer,
-// warp 1 lane 0 = MMA issuer, warps 2..9 = drain/epilogue (warp w reads TMEM
-// lanes 32*(w%4) .. +31, i.e. one output row per thread, and one half of the
-// kBN columns).  All roles walk the same flattened (tile, k-block) sequence:
-// the shared-memory ring and the two TMEM accumulator buffers (each 2*kBN
-// columns: main + correction) keep cycling across tiles, so a tile's store
-// overlaps the next tile's MMAs.  The drain warps empty a buffer every
-// kChunkBlocks k-blocks into FP32 registers.
+// Persistent: CTA c handles tiles c, c + gridDim.x, ... of the launch's tile
+// sequence; inside a task, tiles are ordered n-tile fastest, then m-tile,
+// then (slice, k split), so neighbouring CTAs share operand tiles in L2.
+// Warp roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
+// warps 2..9 = drain/epilogue (warp w reads TMEM lanes 32*(w%4) .. +31, i.e.
+// one output row per thread, and one half of the kBN columns).  All roles walk
+// the same flattened (tile, k-block) sequence: the shared-memory ring and the
+// two TMEM accumulator buffers (each 2*kBN columns: main + correction) keep
+// cycling across tiles and tasks, so a tile's store overlaps the next tile's
+// MMAs.  The drain warps empty a buffer every kChunkBlocks k-blocks into FP32
+// registers.
 template <bool BF16>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
-              const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-              const GemmArgs p) {
+k_gemm_split3(const __grid_constant__ GemmParams gp) {
   using C = GemmCfg<BF16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -199,9 +222,6 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntn = (p.Nr + kBN - 1) / kBN, ntm = (p.M + kBM - 1) / kBM;
-  const int ntiles = ntn * ntm * p.lt * p.splits;
-  const int chunks_per_tile = (p.kblocks + kChunkBlocks - 1) / kChunkBlocks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -230,13 +250,15 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer
-      int g = 0, issued = 0;  // k-blocks walked / issued by this CTA
+      int g = 0, issued = 0, k = 0, local = 0;
       bool stop = false;
-      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
-        const int tn = tile % ntn, tm = (tile / ntn) % ntm, z = tile / (ntn * ntm);
-        const int t = z % p.lt, split = z / p.lt;
-        const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * p.kblocks;
-        for (int i = 0; i < p.kblocks; ++i, ++g) {
+      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+        const GemmTask* tk = tile_task(gp, tile, k, local);
+        const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
+        const int z = local / (tk->ntn * tk->ntm);
+        const int t = z % tk->lt, split = z / tk->lt;
+        const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * tk->kblocks;
+        for (int i = 0; i < tk->kblocks; ++i, ++g) {
           const int s = g % kStages;
           const uint32_t ph = (uint32_t)(g / kStages) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
@@ -247,10 +269,10 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
           uint8_t* st = smem + s * C::kStageBytes;
           mbar_expect_tx(&full[s], C::kStageBytes);
           const int k0 = (kb0 + i) * C::kBK;
-          tma_load_3d(st, &tmAhi, &full[s], k0, m0, t);
-          tma_load_3d(st + C::kATile, &tmAlo, &full[s], k0, m0, t);
-          tma_load_3d(st + 2 * C::kATile, &tmBhi, &full[s], k0, n0, t);
-          tma_load_3d(st + 2 * C::kATile + C::kBTile, &tmBlo, &full[s], k0, n0, t);
+          tma_load_3d(st, &tk->map[0], &full[s], k0, m0, t);
+          tma_load_3d(st + C::kATile, &tk->map[1], &full[s], k0, m0, t);
+          tma_load_3d(st + 2 * C::kATile, &tk->map[2], &full[s], k0, n0, t);
+          tma_load_3d(st + 2 * C::kATile + C::kBTile, &tk->map[3], &full[s], k0, n0, t);
           issued = g + 1;
         }
       }
@@ -262,13 +284,15 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
     if (lane == 0) {
       // ---- MMA issuer
       constexpr uint32_t idesc = make_idesc<BF16>();
-      int g = 0, cc = 0;  // k-blocks and accumulation chunks walked
+      int g = 0, cc = 0, k = 0, local = 0;  // k-blocks and accumulation chunks walked
       bool stop = false;
-      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
-        for (int i = 0; i < p.kblocks; ++i, ++g) {
+      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+        const GemmTask* tk = tile_task(gp, tile, k, local);
+        const int kblocks = tk->kblocks;
+        for (int i = 0; i < kblocks; ++i, ++g) {
           const int b = cc & 1;
           const bool first = (i % kChunkBlocks) == 0;
-          const bool last = (i % kChunkBlocks) == kChunkBlocks - 1 || i == p.kblocks - 1;
+          const bool last = (i % kChunkBlocks) == kChunkBlocks - 1 || i == kblocks - 1;
           if (first) {  // wait until the drain warps have emptied this buffer
             if (!mbar_wait(&tempty[b], ((uint32_t)(cc >> 1) & 1u) ^ 1u) || *abort_flag) {
               *abort_flag = 1;
@@ -312,15 +336,19 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
     const int q = warp & 3;          // TMEM lane quarter of this warp
     const int c0 = ((warp - 2) >> 2) * kHalf;  // first column of this warp's half
     const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-    int cc = 0, ok = 1;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int tn = tile % ntn, tm = (tile / ntn) % ntm, z = tile / (ntn * ntm);
-      const int t = z % p.lt, split = z / p.lt;
+    int cc = 0, ok = 1, k = 0, local = 0;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+      const GemmTask* tk = tile_task(gp, tile, k, local);
+      const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
+      const int z = local / (tk->ntn * tk->ntm);
+      const int t = z % tk->lt, split = z / tk->lt;
+      const int M = tk->M, Nr = tk->Nr;
+      const int chunks = (tk->kblocks + kChunkBlocks - 1) / kChunkBlocks;
       const int row = tm * kBM + q * 32 + lane;
       float acc[kHalf];
 #pragma unroll
       for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
-      for (int c = 0; c < chunks_per_tile; ++c, ++cc) {
+      for (int c = 0; c < chunks; ++c, ++cc) {
         const int b = cc & 1;
         if (lane == 0) {
           if (!mbar_wait(&tfull[b], (uint32_t)(cc >> 1) & 1u) || *abort_flag) {
@@ -345,11 +373,10 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      if (ok && row < p.M) {
-        float* dst =
-            p.out + ((size_t)split * p.lt + t) * (size_t)p.M * p.Nr + (size_t)row * p.Nr;
+      if (ok && row < M) {
+        float* dst = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr + (size_t)row * Nr;
         const int col = tn * kBN + c0;
-        if (col + kHalf <= p.Nr && (p.Nr & 3) == 0) {
+        if (col + kHalf <= Nr && (Nr & 3) == 0) {
           float4* d4 = reinterpret_cast<float4*>(dst + col);
 #pragma unroll
           for (int u = 0; u < kHalf / 4; ++u)
@@ -357,7 +384,7 @@ k_gemm_split3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__
         } else {
 #pragma unroll
           for (int u = 0; u < kHalf; ++u)
-            if (col + u < p.Nr) dst[col + u] = acc[u];
+            if (col + u < Nr) dst[col + u] = acc[u];
         }
       }
     }
@@ -666,6 +693,43 @@ static PackArgs pack_args(const ContractDesc& cd, int which, int64_t kp) {
   return a;
 }
 
+// task of one contraction whose planes / partials live in `scratch`
+bool fill_gemm_task(const MixedDesc& d, void* scratch, float* C, GemmTask* t) {
+  const ContractDesc& cd = d.cd;
+  char* sc = static_cast<char*>(scratch);
+  std::memset(t, 0, sizeof(*t));
+  if (!make_map(&t->map[0], sc + d.a_off, d.bf16, d.kp, cd.M, cd.lt) ||
+      !make_map(&t->map[1], sc + d.a_off + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
+      !make_map(&t->map[2], sc + d.b_off, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
+      !make_map(&t->map[3], sc + d.b_off + d.plane_b, d.bf16, d.kp, 2 * cd.N, cd.lt))
+    return false;
+  t->M = (int)cd.M;
+  t->Nr = (int)(2 * cd.N);
+  t->kblocks = d.kblocks;
+  t->splits = d.splits;
+  t->lt = (int)cd.lt;
+  t->ntn = (t->Nr + kBN - 1) / kBN;
+  t->ntm = (t->M + kBM - 1) / kBM;
+  t->tiles = t->ntn * t->ntm * t->lt * t->splits;
+  t->out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
+  return true;
+}
+
+int launch_gemm(const GemmParams& gp, bool bf16, cudaStream_t s) {
+  if (gp.total_tiles <= 0) return 0;
+  dim3 grid((unsigned)std::min<long long>(gp.total_tiles, num_sms()));
+  if (bf16) {
+    const int smem = GemmCfg<true>::kSmem;
+    cudaFuncSetAttribute(k_gemm_split3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_gemm_split3<true><<<grid, kGemmThreads, smem, s>>>(gp);
+  } else {
+    const int smem = GemmCfg<false>::kSmem;
+    cudaFuncSetAttribute(k_gemm_split3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_gemm_split3<false><<<grid, kGemmThreads, smem, s>>>(gp);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, float* C,
                           void* scratch, cudaStream_t s) {
   const ContractDesc& cd = d.cd;
@@ -706,35 +770,16 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
     }
     ++nk;
   }
-  CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
-  if (!make_map(&m_ahi, ahi, d.bf16, d.kp, cd.M, cd.lt) ||
-      !make_map(&m_alo, alo, d.bf16, d.kp, cd.M, cd.lt) ||
-      !make_map(&m_bhi, bhi, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
-      !make_map(&m_blo, blo, d.bf16, d.kp, 2 * cd.N, cd.lt))
-    return -2;
-  GemmArgs g;
-  g.M = (int)cd.M;
-  g.Nr = (int)(2 * cd.N);
-  g.kblocks = d.kblocks;
-  g.splits = d.splits;
-  g.lt = (int)cd.lt;
-  g.out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
-  const int64_t tiles = ((g.Nr + kBN - 1) / kBN) * ((g.M + kBM - 1) / kBM) * cd.lt * d.splits;
-  dim3 grid((unsigned)std::min<int64_t>(tiles, num_sms()));
-  if (d.bf16) {
-    const int smem = GemmCfg<true>::kSmem;
-    cudaFuncSetAttribute(k_gemm_split3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_gemm_split3<true><<<grid, kGemmThreads, smem, s>>>(m_ahi, m_alo, m_bhi, m_blo, g);
-  } else {
-    const int smem = GemmCfg<false>::kSmem;
-    cudaFuncSetAttribute(k_gemm_split3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_gemm_split3<false><<<grid, kGemmThreads, smem, s>>>(m_ahi, m_alo, m_bhi, m_blo, g);
-  }
+  GemmParams gp;
+  std::memset(&gp, 0, sizeof(gp));
+  if (!fill_gemm_task(d, scratch, C, &gp.single)) return -2;
+  gp.total_tiles = gp.single.tiles;
+  if (launch_gemm(gp, d.bf16, s) < 0) return -1;
   ++nk;
   if (d.splits > 1) {
     const long long per = cd.lt * cd.M * 2 * cd.N;
     unsigned blocks = (unsigned)std::min<long long>((per + 255) / 256, 8 * 148);
-    k_reduce_splits<<<blocks, 256, 0, s>>>(g.out, C, per, d.splits);
+    k_reduce_splits<<<blocks, 256, 0, s>>>(gp.single.out, C, per, d.splits);
     ++nk;
   }
   return cudaPeekAtLastError() == cudaSuccess ? nk : -1;

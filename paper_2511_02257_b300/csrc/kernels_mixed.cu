@@ -473,18 +473,30 @@ struct PackPair {
 // the gather (along the operand's unit-stride axis) and the plane writes
 // (along k) are coalesced.
 template <bool BF16>
+__device__ __forceinline__ void pack_block(const PackArgs& p, const float2* __restrict__ X,
+                                           typename Split<BF16>::T* __restrict__ hi,
+                                           typename Split<BF16>::T* __restrict__ lo, int t,
+                                           unsigned r0, unsigned k0);
+
+template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_pack(const __grid_constant__ PackPair<BF16> pp) {
-  typedef typename Split<BF16>::T T;
-  __shared__ float2 tile[32][33];
   const int which = blockIdx.z >= (unsigned)pp.lt ? 1 : 0;
   const int t = blockIdx.z - which * pp.lt;
   const PackArgs& p = pp.op[which];
-  const float2* X = pp.X[which];
-  T* hi = pp.hi[which];
-  T* lo = pp.lo[which];
   const unsigned r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   if (r0 >= (unsigned)p.rows) return;  // the grid spans the larger operand
+  pack_block<BF16>(p, pp.X[which], pp.hi[which], pp.lo[which], t, r0, k0);
+}
+
+// one 32 x 32 block of one operand (see k_pack)
+template <bool BF16>
+__device__ __forceinline__ void pack_block(const PackArgs& p, const float2* __restrict__ X,
+                                           typename Split<BF16>::T* __restrict__ hi,
+                                           typename Split<BF16>::T* __restrict__ lo, int t,
+                                           unsigned r0, unsigned k0) {
+  typedef typename Split<BF16>::T T;
+  __shared__ float2 tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   X += (long long)t * p.ts;
   // the index decompositions of this block's 32 rows and 32 k once, not per element
@@ -545,11 +557,11 @@ __device__ __forceinline__ void df_acc_prod(float& sh, float& sl, float a, float
   sh = t;
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
-__global__ void __launch_bounds__(256)
-k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
-                   double2* __restrict__ part, const ContractAllDesc p) {
-  const long long t = blockIdx.y;
-  const int c = blockIdx.x;
+// partial sum of block c of slice t of one correlator (fixed reduction order)
+__device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
+                                                 const float2* __restrict__ B,
+                                                 double2* __restrict__ part,
+                                                 const ContractAllDesc& p, long long t, int c) {
   const unsigned S = (unsigned)p.S;
   const unsigned lo = (unsigned)(((unsigned long long)S * c) / p.chunks);
   const unsigned hi = (unsigned)(((unsigned long long)S * (c + 1)) / p.chunks);
@@ -582,6 +594,12 @@ k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
   }
 }
 
+__global__ void __launch_bounds__(256)
+k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
+                   double2* __restrict__ part, const ContractAllDesc p) {
+  ca_partial_block(A, B, part, p, blockIdx.y, blockIdx.x);
+}
+
 __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
                                             double2* __restrict__ C, long long lt, int chunks,
                                             double scale) {
@@ -594,6 +612,108 @@ __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
     s.y += v.y;
   }
   C[t] = make_double2(s.x * scale, s.y * scale);
+}
+
+// ------------------------------------------------------------ grouped
+// One level of a grouped window: independent contractions run together, a
+// handful of launches per level instead of a few per contraction.  Every
+// launch walks a task table in global memory; a block finds its task by
+// binary search over the tasks' first block index.
+struct PackTask {
+  PackArgs op[2];
+  const float2* X[2];
+  void* hi[2];
+  void* lo[2];
+  int lt, kblk, rblk;
+  long long block_start;
+};
+
+struct CATask {
+  const float2* A;
+  const float2* B;
+  double2* out;
+  double2* part;
+  ContractAllDesc d;
+  double scale;
+  long long block_start, t_start;
+};
+
+struct ReduceTask {
+  const float* part;
+  float* out;
+  long long per;
+  int splits;
+  long long block_start;
+};
+
+constexpr int kReduceElems = 2048;  // elements per block of the grouped reduction
+
+template <typename T>
+__device__ __forceinline__ int find_task(const T* tasks, int n, long long b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].block_start <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_pack_grouped(const PackTask* __restrict__ tasks, int n) {
+  typedef typename Split<BF16>::T T;
+  const PackTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+  const long long local = blockIdx.x - tk.block_start;
+  const int bx = (int)(local % tk.kblk), by = (int)((local / tk.kblk) % tk.rblk);
+  const int bz = (int)(local / ((long long)tk.kblk * tk.rblk));
+  const int which = bz >= tk.lt ? 1 : 0;
+  const int t = bz - which * tk.lt;
+  const unsigned r0 = by * 32, k0 = bx * 32;
+  if (r0 >= (unsigned)tk.op[which].rows) return;
+  pack_block<BF16>(tk.op[which], tk.X[which], static_cast<T*>(tk.hi[which]),
+                   static_cast<T*>(tk.lo[which]), t, r0, k0);
+}
+
+__global__ void __launch_bounds__(256)
+k_contract_all_grouped(const CATask* __restrict__ tasks, int n) {
+  const CATask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+  const long long local = blockIdx.x - tk.block_start;
+  ca_partial_block(tk.A, tk.B, tk.part, tk.d, local / tk.d.chunks, (int)(local % tk.d.chunks));
+}
+
+__global__ void k_contract_all_final_grouped(const CATask* __restrict__ tasks, int n,
+                                             long long total) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = n - 1;  // task owning slice g (by t_start)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].t_start <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const CATask& tk = tasks[lo];
+  const long long t = g - tk.t_start;
+  double2 s = make_double2(0.0, 0.0);
+  for (int c = 0; c < tk.d.chunks; ++c) {
+    const double2 v = tk.part[t * tk.d.chunks + c];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  tk.out[t] = make_double2(s.x * tk.scale, s.y * tk.scale);
+}
+
+__global__ void __launch_bounds__(256)
+k_reduce_grouped(const ReduceTask* __restrict__ tasks, int n) {
+  const ReduceTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+  const long long base = (blockIdx.x - tk.block_start) * (long long)kReduceElems;
+  for (int e = threadIdx.x; e < kReduceElems; e += 256) {
+    const long long i = base + e;
+    if (i >= tk.per) break;
+    double acc = 0.0;
+    for (int k = 0; k < tk.splits; ++k) acc += (double)tk.part[(long long)k * tk.per + i];
+    tk.out[i] = (float)acc;
+  }
 }
 
 // ------------------------------------------------------------ host side
@@ -805,6 +925,138 @@ int mixed_error_status(bool reset) {
     cudaMemcpyToSymbol(g_mixed_error, &z, sizeof(int));
   }
   return v;
+}
+
+}  // namespace lqc
+
+// ---------------------------------------------------------------- grouped host side
+namespace lqc {
+namespace {
+size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
+template <typename T>
+size_t append(std::vector<char>* buf, const std::vector<T>& v, size_t align) {
+  const size_t off = align_to(buf->size(), align);
+  buf->resize(off + sizeof(T) * v.size());
+  if (!v.empty()) std::memcpy(buf->data() + off, v.data(), sizeof(T) * v.size());
+  return off;
+}
+}  // namespace
+
+bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<GroupRoot>& roots,
+                        bool bf16, std::vector<char>* buf, LevelDev* lvl) {
+  std::memset(lvl, 0, sizeof(*lvl));
+  std::vector<PackTask> pk;
+  std::vector<GemmTask> gm;
+  std::vector<ReduceTask> rd;
+  std::vector<CATask> ca;
+  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0;
+  for (const GroupExt& e : ext) {
+    const MixedDesc& d = *e.d;
+    const ContractDesc& cd = d.cd;
+    char* sc = e.scratch;
+    PackTask p;
+    std::memset(&p, 0, sizeof(p));
+    p.op[0] = pack_args(cd, 0, d.kp);
+    p.op[1] = pack_args(cd, 1, d.kp);
+    p.X[0] = reinterpret_cast<const float2*>(e.A);
+    p.X[1] = reinterpret_cast<const float2*>(e.B);
+    p.hi[0] = sc + d.a_off;
+    p.lo[0] = sc + d.a_off + d.plane_a;
+    p.hi[1] = sc + d.b_off;
+    p.lo[1] = sc + d.b_off + d.plane_b;
+    p.lt = (int)cd.lt;
+    const int64_t kc = std::max<int64_t>(cd.K, d.kp / 2);
+    p.kblk = (int)((kc + 31) / 32);
+    p.rblk = (int)((std::max<int64_t>(cd.M, cd.N) + 31) / 32);
+    p.block_start = pb;
+    pb += (long long)p.kblk * p.rblk * 2 * p.lt;
+    pk.push_back(p);
+    GemmTask g;
+    if (!fill_gemm_task(d, e.scratch, e.C, &g)) return false;
+    g.tile_start = tiles;
+    tiles += g.tiles;
+    gm.push_back(g);
+    if (d.splits > 1) {
+      ReduceTask r;
+      r.part = g.out;
+      r.out = e.C;
+      r.per = cd.lt * cd.M * 2 * cd.N;
+      r.splits = d.splits;
+      r.block_start = rb;
+      rb += (r.per + kReduceElems - 1) / kReduceElems;
+      rd.push_back(r);
+    }
+  }
+  for (const GroupRoot& r : roots) {
+    CATask c;
+    std::memset(&c, 0, sizeof(c));
+    c.A = reinterpret_cast<const float2*>(r.A);
+    c.B = reinterpret_cast<const float2*>(r.B);
+    c.out = reinterpret_cast<double2*>(r.C);
+    c.part = reinterpret_cast<double2*>(r.part);
+    c.d = *r.d;
+    c.scale = r.scale;
+    c.block_start = cb;
+    c.t_start = ct;
+    cb += (long long)c.d.chunks * c.d.lt;
+    ct += c.d.lt;
+    ca.push_back(c);
+  }
+  lvl->pack = reinterpret_cast<const void*>(append(buf, pk, 64));
+  lvl->npack = (int)pk.size();
+  lvl->pack_blocks = pb;
+  lvl->gemm = reinterpret_cast<const void*>(append(buf, gm, 64));
+  lvl->ngemm = (int)gm.size();
+  lvl->gemm_tiles = tiles;
+  lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
+  lvl->nred = (int)rd.size();
+  lvl->red_blocks = rb;
+  lvl->ca = reinterpret_cast<const void*>(append(buf, ca, 64));
+  lvl->nca = (int)ca.size();
+  lvl->ca_blocks = cb;
+  lvl->ca_threads = ct;
+  lvl->bf16 = bf16;
+  return true;
+}
+
+void rebase_level(LevelDev* lvl, const char* base) {
+  lvl->pack = base + reinterpret_cast<uintptr_t>(lvl->pack);
+  lvl->gemm = base + reinterpret_cast<uintptr_t>(lvl->gemm);
+  lvl->red = base + reinterpret_cast<uintptr_t>(lvl->red);
+  lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
+}
+
+int launch_level(const LevelDev& L, cudaStream_t s) {
+  int nk = 0;
+  if (L.npack > 0) {
+    if (L.bf16)
+      k_pack_grouped<true><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
+          static_cast<const PackTask*>(L.pack), L.npack);
+    else
+      k_pack_grouped<false><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
+          static_cast<const PackTask*>(L.pack), L.npack);
+    ++nk;
+    GemmParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.tasks = static_cast<const GemmTask*>(L.gemm);
+    gp.ntasks = L.ngemm;
+    gp.total_tiles = L.gemm_tiles;
+    if (launch_gemm(gp, L.bf16, s) < 0) return -1;
+    ++nk;
+  }
+  if (L.nred > 0) {
+    k_reduce_grouped<<<(unsigned)L.red_blocks, 256, 0, s>>>(
+        static_cast<const ReduceTask*>(L.red), L.nred);
+    ++nk;
+  }
+  if (L.nca > 0) {
+    k_contract_all_grouped<<<(unsigned)L.ca_blocks, 256, 0, s>>>(
+        static_cast<const CATask*>(L.ca), L.nca);
+    k_contract_all_final_grouped<<<(unsigned)((L.ca_threads + 127) / 128), 128, 0, s>>>(
+        static_cast<const CATask*>(L.ca), L.nca, L.ca_threads);
+    nk += 2;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? nk : -1;
 }
 
 }  // namespace lqc

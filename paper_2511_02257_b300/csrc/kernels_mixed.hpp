@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "kernels.hpp"
 
@@ -36,6 +37,51 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
 // Correlator of two complex64 tensors, FP64 accumulation, times `scale`.
 int launch_contract_all_c64(const ContractAllDesc& d, const float* A, const float* B, double* C,
                             double* scratch, double scale, cudaStream_t s);
+// ---- grouped window levels (mixed precisions)
+// one exterior contraction of a level: its descriptor, operands, output and
+// its own scratch region (planes, split partials) of d->scratch_bytes
+struct GroupExt {
+  const MixedDesc* d;
+  const float* A;
+  const float* B;
+  float* C;
+  char* scratch;
+};
+// one correlator of a level: partial sums in `part` (lt * chunks complex128)
+struct GroupRoot {
+  const ContractAllDesc* d;
+  const float* A;
+  const float* B;
+  double* C;
+  double* part;
+  double scale;
+};
+// task tables of one level (device pointers after rebase_level)
+struct LevelDev {
+  const void* pack;
+  int npack;
+  long long pack_blocks;
+  const void* gemm;
+  int ngemm;
+  long long gemm_tiles;
+  const void* red;
+  int nred;
+  long long red_blocks;
+  const void* ca;
+  int nca;
+  long long ca_blocks, ca_threads;
+  bool bf16;
+};
+// Append a level's task tables to `buf` (offsets stored in *lvl, relative to
+// the start of buf); false if a tensor map cannot be encoded.  Pointers in
+// the members must already be final device addresses.
+bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<GroupRoot>& roots,
+                        bool bf16, std::vector<char>* buf, LevelDev* lvl);
+// turn the offsets into device addresses once buf has been copied to `base`
+void rebase_level(LevelDev* lvl, const char* base);
+// launch one level on `s`; returns kernels launched or -1
+int launch_level(const LevelDev& lvl, cudaStream_t s);
+
 // First error code recorded by a mixed kernel (bounded wait expired), or 0;
 // -1 if it cannot be read.  reset = clear it after reading.
 int mixed_error_status(bool reset);

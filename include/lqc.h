@@ -115,9 +115,15 @@ typedef enum {
                              the first execute and replay it afterwards    */
   LQC_OPT_POISON = 2,     /* 1: fill each freed / evicted device tensor with
                              NaN (use-after-free shows as a NaN result)    */
-  LQC_OPT_TIMING = 3      /* 1: bracket every contraction kernel with CUDA
+  LQC_OPT_TIMING = 3,     /* 1: bracket every contraction kernel with CUDA
                              events on the compute stream; lqc_dag_get_exec_info
                              then reports summed per-kind kernel time        */
+  LQC_OPT_WINDOW = 4      /* mixed precisions, plans without evictions: run up
+                             to this many consecutive contractions of the order
+                             as one grouped window (frees deferred to its end;
+                             each dependency level a few grouped launches).
+                             0 or 1 = one contraction at a time; default 64.
+                             Timing then covers whole windows              */
 } lqc_option;
 
 /* Create an empty DAG.  lt >= 1 time slices; prec selects storage and

@@ -270,6 +270,10 @@ int lqc_dag_set_option(lqc_dag* h, int option, int64_t value) {
     case LQC_OPT_CUDA_GRAPH: h->d.opt_graph = value ? 1 : 0; break;
     case LQC_OPT_POISON: h->d.opt_poison = value ? 1 : 0; break;
     case LQC_OPT_TIMING: h->d.opt_timing = value ? 1 : 0; break;
+    case LQC_OPT_WINDOW:
+      if (value < 0 || value > 4096) return fail(h, LQC_ERR_ARG, "window size out of range");
+      h->d.opt_window = value;
+      break;
     default: return fail(h, LQC_ERR_ARG, "unknown option");
   }
   lqc::exec_invalidate_plan(h->d);

@@ -29,7 +29,14 @@ namespace lqc {
 namespace {
 
 enum Stream { S_COMPUTE = 0, S_H2D = 1, S_D2H = 2 };
-enum IKind { I_LOAD = 0, I_WRITEBACK = 1, I_CONTRACT = 2, I_CONTRACT_ALL = 3, I_POISON = 4 };
+enum IKind {
+  I_LOAD = 0,
+  I_WRITEBACK = 1,
+  I_CONTRACT = 2,
+  I_CONTRACT_ALL = 3,
+  I_POISON = 4,
+  I_WINDOW = 5  // a grouped window: its member contractions run as level launches
+};
 
 struct Instr {
   int kind;
@@ -42,6 +49,20 @@ struct Instr {
   int32_t wait[6];
   int32_t rec = -1;   // event slot recorded after this instruction
   int32_t root_slot = -1;
+  int32_t win = -1;    // I_WINDOW: index of its window record
+  bool member = false; // issued through its window, not on its own
+};
+
+// A grouped window: up to W consecutive contractions of the plan whose frees
+// are deferred to the window's end, run level by level (a level = members
+// whose operands are all produced before it).
+struct WinRec {
+  std::vector<int32_t> members;              // instruction indices, plan order
+  std::vector<std::vector<int32_t>> levels;  // members per level
+  std::vector<int32_t> waits;                // cross-stream waits of the members
+  std::vector<LevelDev> ldev;                // task tables per level
+  int64_t flops = 0;
+  bool any_exterior = false;
 };
 
 struct Seg {
@@ -117,6 +138,10 @@ struct ExecState {
   std::vector<ContractDesc> cdesc;        // per instruction (CONTRACT)
   std::vector<ContractAllDesc> adesc;     // per instruction (CONTRACT_ALL)
   std::vector<MixedDesc> mdesc;           // per instruction (CONTRACT, mixed precisions)
+  std::vector<WinRec> wins;               // grouped windows
+  char* wscratch = nullptr;               // planes / partials of one window level
+  int64_t wscratch_bytes = 0;
+  char* taskbuf = nullptr;                // task tables of every window level
   char* mscratch = nullptr;               // operand planes / split partials
   int64_t mscratch_bytes = 0;
   bool prog_valid = false;
@@ -194,6 +219,10 @@ void free_program(ExecState& x) {
   if (x.scratch) { cudaFree(x.scratch); x.scratch = nullptr; }
   if (x.mscratch) { cudaFree(x.mscratch); x.mscratch = nullptr; }
   x.mscratch_bytes = 0;
+  if (x.wscratch) { cudaFree(x.wscratch); x.wscratch = nullptr; }
+  x.wscratch_bytes = 0;
+  if (x.taskbuf) { cudaFree(x.taskbuf); x.taskbuf = nullptr; }
+  x.wins.clear();
   x.mdesc.clear();
   if (x.host_arena) { cudaFreeHost(x.host_arena); x.host_arena = nullptr; }
   x.host_arena_bytes = 0;
@@ -230,6 +259,16 @@ int build_program(Dag& g) {
   Placer pl;
   int64_t scratch_need = 0, mscratch_need = 0;
   std::vector<Instr>& P = x.prog;
+  // grouped windows: mixed precisions, plans without evictions
+  bool evicts = false;
+  for (const Op& op : g.ops) evicts = evicts || op.kind == OP_EVICT;
+  const int W = (g.prec != LQC_PREC_FP64 && g.opt_window > 1 && !evicts) ? (int)g.opt_window : 0;
+  std::vector<int32_t> win;            // open window: member instructions
+  std::vector<int64_t> win_free;       // frees deferred to the window's end
+  std::vector<int32_t> node_level(N, -1);
+  std::vector<int64_t> lvl_need;       // scratch bytes per level of the open window
+  std::vector<int32_t> owner;          // member instruction -> its window instruction
+  const int64_t kLevelScratchCap = (int64_t)2 << 30;
   auto add_wait = [&](Instr& in, int32_t on) {
     if (on < 0 || P[on].stream == in.stream) return;
     for (int k = 0; k < in.nwait; ++k)
@@ -257,6 +296,53 @@ int build_program(Dag& g) {
     }
     pl.release(off[u], g.size_bytes(u), dep);
     off[u] = -1;
+  };
+  auto member_need = [&](int32_t j) -> int64_t {
+    if (P[j].kind == I_CONTRACT) return (x.mdesc[j].scratch_bytes + 255) & ~int64_t(255);
+    return (contract_all_scratch_bytes(x.adesc[j]) + 255) & ~int64_t(255);
+  };
+  auto flush = [&]() {
+    if (win.empty()) return;
+    WinRec rec;
+    rec.members = win;
+    int max_level = 0;
+    for (int32_t m : win) max_level = std::max(max_level, node_level[P[m].node]);
+    rec.levels.assign(max_level + 1, {});
+    for (int32_t m : win) {
+      rec.levels[node_level[P[m].node]].push_back(m);
+      for (int k = 0; k < P[m].nwait; ++k)
+        if (std::find(rec.waits.begin(), rec.waits.end(), P[m].wait[k]) == rec.waits.end())
+          rec.waits.push_back(P[m].wait[k]);
+      const ContractDesc& cd = x.cdesc[m];
+      const ContractAllDesc& ad = x.adesc[m];
+      if (P[m].kind == I_CONTRACT) {
+        rec.flops += 8 * cd.lt * cd.M * cd.N * cd.K;
+        rec.any_exterior = true;
+      } else {
+        rec.flops += 8 * ad.lt * ad.S;
+      }
+    }
+    Instr wi{};
+    wi.kind = I_WINDOW;
+    wi.stream = S_COMPUTE;
+    wi.node = P[win[0]].node;
+    wi.src[0] = wi.src[1] = -1;
+    wi.win = (int32_t)x.wins.size();
+    x.wins.push_back(std::move(rec));
+    P.push_back(wi);
+    x.cdesc.emplace_back();
+    x.adesc.emplace_back();
+    x.mdesc.emplace_back();
+    const int32_t wj = (int32_t)P.size() - 1;
+    owner.resize(P.size(), -1);
+    for (int32_t m : win) {
+      owner[m] = wj;
+      node_level[P[m].node] = -1;
+    }
+    win.clear();
+    lvl_need.clear();
+    for (int64_t u : win_free) release(u);
+    win_free.clear();
   };
   for (const Op& op : g.ops) {
     const int64_t u = op.node;
@@ -309,6 +395,8 @@ int build_program(Dag& g) {
         wb_instr[u] = last_d2h[u];
       }
       release(u);
+    } else if (op.kind == OP_FREE && W > 0 && !win.empty()) {
+      win_free.push_back(u);  // no evictions in windowed plans: no host copy to drop
     } else if (op.kind == OP_FREE) {
       if (hoff[u] >= 0) {  // final release: the host copy is dead too
         int32_t hdep[3] = {-1, last_h2d[u], wb_instr[u]};
@@ -370,11 +458,34 @@ int build_program(Dag& g) {
         }
         mscratch_need = std::max(mscratch_need, md.scratch_bytes);
       }
+      if (W > 0) {
+        int level = 0;
+        for (int k = 0; k < n.n_children(); ++k) {
+          const int lc = node_level[n.child(k)];
+          if (lc >= 0) level = std::max(level, lc + 1);
+        }
+        const int64_t need = (in.kind == I_CONTRACT)
+                                 ? ((md.scratch_bytes + 255) & ~int64_t(255))
+                                 : ((contract_all_scratch_bytes(ad) + 255) & ~int64_t(255));
+        if (!win.empty() && level < (int)lvl_need.size() &&
+            lvl_need[level] + need > std::max(kLevelScratchCap, need)) {
+          flush();
+          level = 0;
+        }
+        if ((int)lvl_need.size() <= level) lvl_need.resize(level + 1, 0);
+        lvl_need[level] += need;
+        in.member = true;
+        node_level[u] = level;
+      }
       P.push_back(in);
       x.cdesc.push_back(cd);
       x.adesc.push_back(ad);
       x.mdesc.push_back(md);
       const int32_t me = (int32_t)P.size() - 1;
+      if (W > 0) {
+        win.push_back(me);
+        (void)member_need;
+      }
       for (int k = 0; k < n.n_children(); ++k) last_compute[n.child(k)] = me;
       if (n.rank != 0) {
         last_compute[u] = me;
@@ -384,23 +495,55 @@ int build_program(Dag& g) {
       }
     }
   }
+  flush();
+  // waits on a window member wait on its window
+  owner.resize(P.size(), -1);
+  auto remap = [&](int32_t w) { return (w >= 0 && owner[w] >= 0) ? owner[w] : w; };
+  for (Instr& in : P) {
+    int nw = 0;
+    for (int k = 0; k < in.nwait; ++k) {
+      const int32_t w = remap(in.wait[k]);
+      if (P[w].stream == in.stream) continue;
+      bool dup = false;
+      for (int q = 0; q < nw; ++q) dup = dup || in.wait[q] == w;
+      if (!dup) in.wait[nw++] = w;
+    }
+    in.nwait = nw;
+  }
+  for (WinRec& r : x.wins) {
+    std::vector<int32_t> ws;
+    for (int32_t w : r.waits) {
+      w = remap(w);
+      if (P[w].stream != S_COMPUTE && std::find(ws.begin(), ws.end(), w) == ws.end())
+        ws.push_back(w);
+    }
+    r.waits = ws;
+  }
   // event slots for every instruction somebody waits on
   std::vector<int32_t> slot(P.size(), -1);
   int32_t n_ev = 0;
+  auto need_slot = [&](int32_t j) {
+    if (slot[j] < 0) slot[j] = n_ev++;
+  };
   for (Instr& in : P)
-    for (int k = 0; k < in.nwait; ++k) {
-      int32_t j = in.wait[k];
-      if (slot[j] < 0) slot[j] = n_ev++;
-    }
+    if (!in.member)
+      for (int k = 0; k < in.nwait; ++k) need_slot(in.wait[k]);
+  for (WinRec& r : x.wins)
+    for (int32_t w : r.waits) need_slot(w);
   for (size_t j = 0; j < P.size(); ++j) P[j].rec = slot[j];
   for (Instr& in : P)
-    for (int k = 0; k < in.nwait; ++k) in.wait[k] = slot[in.wait[k]];
+    if (!in.member)
+      for (int k = 0; k < in.nwait; ++k) in.wait[k] = slot[in.wait[k]];
+  for (WinRec& r : x.wins)
+    for (int32_t& w : r.waits) w = slot[w];
   x.ev.resize(n_ev, nullptr);
   for (int32_t k = 0; k < n_ev; ++k)
     CK(cudaEventCreateWithFlags(&x.ev[k], cudaEventDisableTiming), "event create");
   if (g.opt_timing) {
     for (size_t j = 0; j < P.size(); ++j) {
-      if (P[j].kind != I_CONTRACT && P[j].kind != I_CONTRACT_ALL) continue;
+      if (P[j].member) continue;
+      if (P[j].kind != I_CONTRACT && P[j].kind != I_CONTRACT_ALL && P[j].kind != I_WINDOW)
+        continue;
       for (int k = 0; k < 2; ++k) {
         cudaEvent_t b, e;
         CK(cudaEventCreate(&b), "timing event");
@@ -408,13 +551,19 @@ int build_program(Dag& g) {
         x.tev[k].push_back(b);
         x.tev[k].push_back(e);
       }
-      x.tev_kind.push_back(P[j].kind);
       const ContractDesc& cd = x.cdesc[j];
       const ContractAllDesc& ad = x.adesc[j];
       x.tev_node.push_back(P[j].node);
       x.tev_ms.push_back(0.0);
-      x.tev_flops.push_back(P[j].kind == I_CONTRACT ? 8 * cd.lt * cd.M * cd.N * cd.K
-                                                      : 8 * ad.lt * ad.S);
+      if (P[j].kind == I_WINDOW) {
+        const WinRec& r = x.wins[P[j].win];
+        x.tev_kind.push_back(r.any_exterior ? I_CONTRACT : I_CONTRACT_ALL);
+        x.tev_flops.push_back(r.flops);
+      } else {
+        x.tev_kind.push_back(P[j].kind);
+        x.tev_flops.push_back(P[j].kind == I_CONTRACT ? 8 * cd.lt * cd.M * cd.N * cd.K
+                                                        : 8 * ad.lt * ad.S);
+      }
     }
   }
   x.arena_bytes = pl.top;
@@ -426,6 +575,54 @@ int build_program(Dag& g) {
   x.mscratch_bytes = mscratch_need;
   if (mscratch_need > 0)
     CK(cudaMalloc((void**)&x.mscratch, (size_t)mscratch_need), "plane scratch cudaMalloc");
+  // window levels: scratch sized by the largest level, task tables built with
+  // the final device addresses
+  for (const WinRec& r : x.wins)
+    for (const auto& lv : r.levels) {
+      int64_t sum = 0;
+      for (int32_t m : lv) sum += member_need(m);
+      x.wscratch_bytes = std::max(x.wscratch_bytes, sum);
+    }
+  if (x.wscratch_bytes > 0)
+    CK(cudaMalloc((void**)&x.wscratch, (size_t)x.wscratch_bytes), "window scratch cudaMalloc");
+  if (!x.wins.empty()) {
+    std::vector<char> tbuf;
+    auto operand = [&](const Instr& in, int k) -> const float* {
+      const int64_t c = g.nodes[in.node].child(k);
+      return in.src[k] == -2 ? static_cast<const float*>(x.staged[c])
+                             : reinterpret_cast<const float*>(x.arena + in.src[k]);
+    };
+    for (WinRec& r : x.wins) {
+      r.ldev.resize(r.levels.size());
+      for (size_t l = 0; l < r.levels.size(); ++l) {
+        std::vector<GroupExt> ext;
+        std::vector<GroupRoot> roots;
+        int64_t so = 0;
+        for (int32_t m : r.levels[l]) {
+          const Instr& in = P[m];
+          const Node& nn = g.nodes[in.node];
+          if (in.kind == I_CONTRACT) {
+            ext.push_back(GroupExt{&x.mdesc[m], operand(in, 0), operand(in, 1),
+                                   reinterpret_cast<float*>(x.arena + in.dst), x.wscratch + so});
+          } else {
+            roots.push_back(GroupRoot{
+                &x.adesc[m], operand(in, 0), operand(in, 1), x.results + 2 * g.lt * in.root_slot,
+                reinterpret_cast<double*>(x.wscratch + so),
+                std::ldexp(1.0, g.nodes[nn.left].scale_exp + g.nodes[nn.right].scale_exp)});
+          }
+          so += member_need(m);
+        }
+        if (!append_level_tasks(ext, roots, g.prec == LQC_PREC_BF16X3, &tbuf, &r.ldev[l])) {
+          g.err = "TMA tensor map encoding failed";
+          return LQC_ERR_CUDA;
+        }
+      }
+    }
+    CK(cudaMalloc((void**)&x.taskbuf, tbuf.size() + 64), "task table cudaMalloc");
+    CK(cudaMemcpy(x.taskbuf, tbuf.data(), tbuf.size(), cudaMemcpyHostToDevice), "task tables");
+    for (WinRec& r : x.wins)
+      for (LevelDev& d : r.ldev) rebase_level(&d, x.taskbuf);
+  }
   x.host_arena_bytes = hpl.top;
   if (hpl.top > 0)
     CK(cudaHostAlloc((void**)&x.host_arena, (size_t)hpl.top, cudaHostAllocDefault),
@@ -455,8 +652,27 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
   size_t tk = 0;  // timing pair cursor
   for (size_t j = 0; j < x.prog.size(); ++j) {
     const Instr& in = x.prog[j];
+    if (in.member) continue;  // runs inside its window
     cudaStream_t s = st[in.stream];
     for (int k = 0; k < in.nwait; ++k) CK(cudaStreamWaitEvent(s, x.ev[in.wait[k]], 0), "wait");
+    if (in.kind == I_WINDOW) {
+      const WinRec& r = x.wins[in.win];
+      for (int32_t w : r.waits) CK(cudaStreamWaitEvent(s, x.ev[w], 0), "wait");
+      const bool timed = g.opt_timing && tk < x.tev_kind.size();
+      if (timed) CK(cudaEventRecordWithFlags(x.tev[x.tset][2 * tk], s, tflag), "timing record");
+      for (const LevelDev& d : r.ldev) {
+        const int nk = launch_level(d, s);
+        if (nk < 0) return cuda_fail(g, cudaGetLastError(), "window level launch");
+        x.n_kernels += nk;
+      }
+      if (timed) {
+        CK(cudaEventRecordWithFlags(x.tev[x.tset][2 * tk + 1], s, tflag), "timing record");
+        ++tk;
+      }
+      x.flops += r.flops;
+      if (in.rec >= 0) CK(cudaEventRecord(x.ev[in.rec], s), "record");
+      continue;
+    }
     const Node& n = g.nodes[in.node];
     switch (in.kind) {
       case I_LOAD: {

@@ -65,7 +65,7 @@ struct Dag {
   lqc_evict evict = LQC_EVICT_LRU;
   // execution
   ExecState* ex = nullptr;
-  int64_t opt_graph = 0, opt_poison = 0, opt_timing = 0;
+  int64_t opt_graph = 0, opt_poison = 0, opt_timing = 0, opt_window = 64;
   lqc_stats measured{};
   lqc_exec_info info{};
   bool executed = false;

@@ -153,7 +153,7 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 // parameter) or a table of tasks in global memory (a grouped window level);
 // tiles of all tasks form one sequence, task k owning
 // [tile_start, tile_start + tiles).
-struct alignas(64) GemmTask {
+struct GemmTask {  // 64-byte aligned through its tensor maps
   CUtensorMap map[4];   // Ahi, Alo, Bhi, Blo
   float* out;           // splits == 1: D' [lt][M][Nr]; else partials [splits][lt][M][Nr]
   int M, Nr, kblocks, splits, lt, ntn, ntm, tiles;

@@ -32,7 +32,7 @@ LQC_ERR_HOST_MEM, LQC_ERR_STATE, LQC_ERR_TIMEOUT = -4, -5, -6
 LQC_SCHED_NAIVE_TOPO, LQC_SCHED_TREE, LQC_SCHED_SIBLING = 0, 1, 2
 LQC_EVICT_LRU, LQC_EVICT_NEXT_USE = 0, 1
 LQC_PREC_FP64, LQC_PREC_TF32X3, LQC_PREC_BF16X3 = 0, 1, 2
-LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING = 1, 2, 3
+LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING, LQC_OPT_WINDOW = 1, 2, 3, 4
 OP_NAMES = {0: "LOAD", 1: "EVICT", 2: "CONTRACT", 3: "FREE"}
 POLICIES = {"naive": LQC_SCHED_NAIVE_TOPO, "tree": LQC_SCHED_TREE, "sibling": LQC_SCHED_SIBLING}
 EVICTS = {"lru": LQC_EVICT_LRU, "next_use": LQC_EVICT_NEXT_USE}

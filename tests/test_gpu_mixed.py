@@ -178,3 +178,25 @@ def test_baryon_tf32x3_sampled_roots():
     nd, planned, vals = _run(wl, "tf32x3", roots)
     errs = [rel_err(vals[r], ref[r]) for r in roots]
     assert max(errs) < TOL_TF32X3, errs
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_grouped_windows_bit_identical_to_single_launches(precision):
+    """Grouped window execution (independent contractions batched into a few
+    launches per dependency level) performs the same arithmetic per tile as
+    one launch per contraction: the correlators must agree bit for bit, with
+    far fewer kernels."""
+    wl = synth.make_workload("multi_meson", n_functions=40)
+    nd, _ = L.build_dag(wl, precision=precision, leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd.schedule("tree", "lru", 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    kernels = {}
+    for w in (0, 64, 7):
+        nd.set_option(L.LQC_OPT_WINDOW, w)
+        nd.execute(stream)
+        out[w] = nd.read_all_correlators()
+        kernels[w] = nd.exec_info()["n_kernels"]
+    for w in (64, 7):
+        assert np.array_equal(out[w].view(np.float64), out[0].view(np.float64)), w
+    assert kernels[64] * 4 < kernels[0]

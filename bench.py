@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: replay the whole execute as one CUDA graph")
+    ap.add_argument("--window", type=int, default=64,
+                    help="grouped-window size of the mixed path (0 = one contraction at a time)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -273,6 +275,7 @@ def main():
     nd.stage_leaves(stream)
     nd.set_option(L.LQC_OPT_TIMING, 1)
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
+    nd.set_option(L.LQC_OPT_WINDOW, args.window)
     for _ in range(args.warmup):
         nd.execute(stream)
     nd.wait()
@@ -350,6 +353,7 @@ def main():
                        "functions": len(wl.functions), "contractions": len(nd.order()),
                        "policy": args.policy, "evict": args.evict, "budget_bytes": budget,
                        "precision": args.precision, "cuda_graph": bool(args.graph),
+                       "window": args.window if args.precision != "fp64" else 0,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
                              % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,

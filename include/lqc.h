@@ -317,13 +317,22 @@ int64_t lqc_contract_mixed_scratch_bytes(int rank_a, const int64_t* ext_a,
                                          int npairs, const int* la, const int* ra,
                                          int64_t lt, lqc_precision prec);
 
-/* Contract-all of two complex64 device tensors with FP64 accumulation,
- * result (complex128, lt values) multiplied by `scale`; scratch as for
- * lqc_contract_all_fp64. */
+/* Contract-all of two complex64 device tensors with FP64 accumulation
+ * (per-thread double-float sums, FP64 across threads and blocks), result
+ * (complex128, lt values) multiplied by `scale`.  When the pairing does not
+ * walk both operands in the same memory order, the right operand is first
+ * copied into the left operand's order (a coalesced tiled transpose) inside
+ * `scratch`, which must hold lqc_contract_all_c64_scratch_bytes(...) bytes
+ * (caller-owned, contents ignored). */
 int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a,
                          const float* B, int rank_b, const int64_t* ext_b,
                          int npairs, const int* la, const int* ra, int64_t lt,
                          double scale, double* C, void* scratch, void* stream);
+
+int64_t lqc_contract_all_c64_scratch_bytes(int rank_a, const int64_t* ext_a,
+                                           int rank_b, const int64_t* ext_b,
+                                           int npairs, const int* la, const int* ra,
+                                           int64_t lt);
 
 /* Device error word of the tensor-core kernels: 0 = none, 1 = a bounded wait
  * expired (the kernel returned without a result).  Synchronous; reset != 0

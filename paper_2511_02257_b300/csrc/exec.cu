@@ -299,7 +299,7 @@ int build_program(Dag& g) {
   };
   auto member_need = [&](int32_t j) -> int64_t {
     if (P[j].kind == I_CONTRACT) return (x.mdesc[j].scratch_bytes + 255) & ~int64_t(255);
-    return (contract_all_scratch_bytes(x.adesc[j]) + 255) & ~int64_t(255);
+    return (contract_all_c64_scratch_bytes(x.adesc[j]) + 255) & ~int64_t(255);
   };
   auto flush = [&]() {
     if (win.empty()) return;
@@ -436,7 +436,9 @@ int build_program(Dag& g) {
           g.err = err;
           return LQC_ERR_ARG;
         }
-        scratch_need = std::max(scratch_need, contract_all_scratch_bytes(ad));
+        scratch_need = std::max(scratch_need, g.prec == LQC_PREC_FP64
+                                                  ? contract_all_scratch_bytes(ad)
+                                                  : contract_all_c64_scratch_bytes(ad));
       } else {
         in.kind = I_CONTRACT;
         if (!make_contract_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, g.lt, &cd,
@@ -466,7 +468,7 @@ int build_program(Dag& g) {
         }
         const int64_t need = (in.kind == I_CONTRACT)
                                  ? ((md.scratch_bytes + 255) & ~int64_t(255))
-                                 : ((contract_all_scratch_bytes(ad) + 255) & ~int64_t(255));
+                                 : ((contract_all_c64_scratch_bytes(ad) + 255) & ~int64_t(255));
         if (!win.empty() && level < (int)lvl_need.size() &&
             lvl_need[level] + need > std::max(kLevelScratchCap, need)) {
           flush();

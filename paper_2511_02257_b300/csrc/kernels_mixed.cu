@@ -614,6 +614,64 @@ __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
   C[t] = make_double2(s.x * scale, s.y * scale);
 }
 
+// ------------------------------------------------------------ permute
+// outer offsets of outer index o (row-major digits)
+__device__ __forceinline__ void perm_outer(const PermDesc& d, long long o, long long& so,
+                                           long long& dso) {
+  so = 0;
+  dso = 0;
+#pragma unroll
+  for (int a = LQC_MAX_RANK - 1; a >= 0; --a) {
+    if (a < d.nout) {
+      const long long e = d.oext[a];
+      const long long q = o / e;
+      const long long r = o - q * e;
+      so += r * d.osrc[a];
+      dso += r * d.odst[a];
+      o = q;
+    }
+  }
+}
+
+// block b of slice t
+__device__ __forceinline__ void permute_block(const PermDesc& d, const float2* __restrict__ src,
+                                              float2* __restrict__ dst, int t, long long b) {
+  src += (long long)t * d.src_ts;
+  dst += (long long)t * d.n;
+  if (d.mode == 0) {
+    const int xb = (d.X + 255) / 256;
+    const long long o = b / xb;
+    const int x = (int)(b % xb) * 256 + threadIdx.x;
+    long long so, dso;
+    perm_outer(d, o, so, dso);
+    if (x < d.X) dst[dso + x] = src[so + x];
+    return;
+  }
+  __shared__ float2 tile[32][33];
+  const int xb = (d.X + 31) / 32, yb = (d.Y + 31) / 32;
+  const long long o = b / ((long long)xb * yb);
+  const int x0 = (int)(b % xb) * 32, y0 = (int)((b / xb) % yb) * 32;
+  long long so, dso;
+  perm_outer(d, o, so, dso);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // read along the source's unit-stride axis Y
+    const int y = y0 + tx, x = x0 + ty + 8 * j;
+    if (y < d.Y && x < d.X) tile[ty + 8 * j][tx] = src[so + y + (long long)x * d.sX];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // write along the destination's unit-stride axis X
+    const int x = x0 + tx, y = y0 + ty + 8 * j;
+    if (y < d.Y && x < d.X) dst[dso + (long long)y * d.dY + x] = tile[tx][ty + 8 * j];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_permute_c64(const float2* __restrict__ src, float2* __restrict__ dst, const PermDesc d) {
+  permute_block(d, src, dst, blockIdx.y, blockIdx.x);
+}
+
 // ------------------------------------------------------------ grouped
 // One level of a grouped window: independent contractions run together, a
 // handful of launches per level instead of a few per contraction.  Every
@@ -630,12 +688,19 @@ struct PackTask {
 
 struct CATask {
   const float2* A;
-  const float2* B;
+  const float2* B;       // the (reordered, if needed) right operand
   double2* out;
   double2* part;
   ContractAllDesc d;
   double scale;
   long long block_start, t_start;
+};
+
+struct PermTask {
+  PermDesc d;
+  const float2* src;
+  float2* dst;
+  long long block_start;
 };
 
 struct ReduceTask {
@@ -673,6 +738,13 @@ k_pack_grouped(const PackTask* __restrict__ tasks, int n) {
   if (r0 >= (unsigned)tk.op[which].rows) return;
   pack_block<BF16>(tk.op[which], tk.X[which], static_cast<T*>(tk.hi[which]),
                    static_cast<T*>(tk.lo[which]), t, r0, k0);
+}
+
+__global__ void __launch_bounds__(256)
+k_permute_grouped(const PermTask* __restrict__ tasks, int n) {
+  const PermTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+  const long long local = blockIdx.x - tk.block_start;
+  permute_block(tk.d, tk.src, tk.dst, (int)(local / tk.d.blocks), local % tk.d.blocks);
 }
 
 __global__ void __launch_bounds__(256)
@@ -905,16 +977,109 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
   return cudaPeekAtLastError() == cudaSuccess ? nk : -1;
 }
 
-int launch_contract_all_c64(const ContractAllDesc& d, const float* A, const float* B, double* C,
+void make_perm_desc(const Group& g0, int64_t lt, int64_t src_ts, PermDesc* d) {
+  std::memset(d, 0, sizeof(*d));
+  Group g;  // drop axes of extent 1: they move nothing
+  g.n = 0;
+  for (int a = 0; a < g0.n; ++a)
+    if (g0.ext[a] > 1) {
+      g.ext[g.n] = g0.ext[a];
+      g.stride[g.n++] = g0.stride[a];
+    }
+  if (g.n == 0) {
+    g.n = 1;
+    g.ext[0] = 1;
+    g.stride[0] = 1;
+  }
+  d->lt = (int)lt;
+  d->src_ts = src_ts;
+  long long dst_stride[LQC_MAX_RANK];
+  long long n = 1;
+  for (int a = g.n - 1; a >= 0; --a) {
+    dst_stride[a] = n;
+    n *= g.ext[a];
+  }
+  d->n = n;
+  const int last = g.n - 1;
+  int y = -1;
+  for (int a = 0; a < g.n; ++a)
+    if (g.stride[a] == 1) y = a;
+  d->X = g.ext[last];
+  d->mode = (g.stride[last] == 1 || y < 0) ? 0 : 1;
+  if (d->mode == 1) {
+    d->Y = g.ext[y];
+    d->sX = g.stride[last];
+    d->dY = dst_stride[y];
+  }
+  d->outer = 1;
+  for (int a = 0; a < last; ++a) {
+    if (d->mode == 1 && a == y) continue;
+    d->oext[d->nout] = g.ext[a];
+    d->osrc[d->nout] = g.stride[a];
+    d->odst[d->nout++] = dst_stride[a];
+    d->outer *= g.ext[a];
+  }
+  if (d->mode == 0 && g.stride[last] != 1) {
+    // no unit-stride axis at all (cannot happen for a permutation of a
+    // contiguous tensor with an innermost extent > 1): copy element-wise runs
+    // of length 1
+    d->oext[d->nout] = g.ext[last];
+    d->osrc[d->nout] = g.stride[last];
+    d->odst[d->nout++] = 1;
+    d->outer *= g.ext[last];
+    d->X = 1;
+  }
+  d->blocks = d->mode == 0 ? d->outer * ((d->X + 255) / 256)
+                           : d->outer * ((d->X + 31) / 32) * ((d->Y + 31) / 32);
+}
+
+int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStream_t s) {
+  if (d.lt > 65535 || d.blocks <= 0 || d.blocks >= (1ll << 31)) return -1;
+  dim3 grid((unsigned)d.blocks, (unsigned)d.lt);
+  k_permute_c64<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(src),
+                                     reinterpret_cast<float2*>(dst), d);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+namespace {
+bool ca_needs_copy(const ContractAllDesc& d) {
+  return !(d.bp.n == 1 && d.bp.stride[0] == 1);
+}
+int64_t ca_part_bytes(const ContractAllDesc& d) { return (d.lt * (int64_t)d.chunks * 16 + 255) & ~int64_t(255); }
+ContractAllDesc ca_identity(const ContractAllDesc& d) {
+  ContractAllDesc e = d;
+  e.bp.n = 1;
+  e.bp.ext[0] = (int)d.S;
+  e.bp.stride[0] = 1;
+  return e;
+}
+}  // namespace
+
+int64_t contract_all_c64_scratch_bytes(const ContractAllDesc& d) {
+  return ca_part_bytes(d) + (ca_needs_copy(d) ? d.lt * d.S * 8 : 0);
+}
+
+int launch_contract_all_c64(const ContractAllDesc& d0, const float* A, const float* B, double* C,
                             double* scratch, double scale, cudaStream_t s) {
-  if (d.lt > 65535) return -1;
+  if (d0.lt > 65535) return -1;
+  int nk = 0;
+  ContractAllDesc d = d0;
+  if (ca_needs_copy(d0)) {  // right operand into the left operand's order, coalesced
+    PermDesc pd;
+    make_perm_desc(d0.bp, d0.lt, d0.S, &pd);
+    float* copy = reinterpret_cast<float*>(reinterpret_cast<char*>(scratch) + ca_part_bytes(d0));
+    if (launch_permute_c64(pd, B, copy, s) < 0) return -1;
+    ++nk;
+    B = copy;
+    d = ca_identity(d0);
+  }
   dim3 grid((unsigned)d.chunks, (unsigned)d.lt);
   double2* part = reinterpret_cast<double2*>(scratch);
   k_contract_all_c64<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(A),
                                           reinterpret_cast<const float2*>(B), part, d);
   k_contract_all_final_scaled<<<(unsigned)((d.lt + 127) / 128), 128, 0, s>>>(
       part, reinterpret_cast<double2*>(C), d.lt, d.chunks, scale);
-  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? nk + 2 : -1;
 }
 
 int mixed_error_status(bool reset) {
@@ -949,7 +1114,8 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   std::vector<GemmTask> gm;
   std::vector<ReduceTask> rd;
   std::vector<CATask> ca;
-  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0;
+  std::vector<PermTask> pm;
+  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0;
   for (const GroupExt& e : ext) {
     const MixedDesc& d = *e.d;
     const ContractDesc& cd = d.cd;
@@ -995,6 +1161,18 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     c.out = reinterpret_cast<double2*>(r.C);
     c.part = reinterpret_cast<double2*>(r.part);
     c.d = *r.d;
+    if (ca_needs_copy(*r.d)) {
+      PermTask t;
+      std::memset(&t, 0, sizeof(t));
+      make_perm_desc(r.d->bp, r.d->lt, r.d->S, &t.d);
+      t.src = reinterpret_cast<const float2*>(r.B);
+      t.dst = reinterpret_cast<float2*>(reinterpret_cast<char*>(r.part) + ca_part_bytes(*r.d));
+      t.block_start = mb;
+      mb += t.d.blocks * t.d.lt;
+      pm.push_back(t);
+      c.B = t.dst;
+      c.d = ca_identity(*r.d);
+    }
     c.scale = r.scale;
     c.block_start = cb;
     c.t_start = ct;
@@ -1011,6 +1189,9 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
   lvl->nred = (int)rd.size();
   lvl->red_blocks = rb;
+  lvl->perm = reinterpret_cast<const void*>(append(buf, pm, 64));
+  lvl->nperm = (int)pm.size();
+  lvl->perm_blocks = mb;
   lvl->ca = reinterpret_cast<const void*>(append(buf, ca, 64));
   lvl->nca = (int)ca.size();
   lvl->ca_blocks = cb;
@@ -1023,6 +1204,7 @@ void rebase_level(LevelDev* lvl, const char* base) {
   lvl->pack = base + reinterpret_cast<uintptr_t>(lvl->pack);
   lvl->gemm = base + reinterpret_cast<uintptr_t>(lvl->gemm);
   lvl->red = base + reinterpret_cast<uintptr_t>(lvl->red);
+  lvl->perm = base + reinterpret_cast<uintptr_t>(lvl->perm);
   lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
 }
 
@@ -1047,6 +1229,11 @@ int launch_level(const LevelDev& L, cudaStream_t s) {
   if (L.nred > 0) {
     k_reduce_grouped<<<(unsigned)L.red_blocks, 256, 0, s>>>(
         static_cast<const ReduceTask*>(L.red), L.nred);
+    ++nk;
+  }
+  if (L.nperm > 0) {
+    k_permute_grouped<<<(unsigned)L.perm_blocks, 256, 0, s>>>(
+        static_cast<const PermTask*>(L.perm), L.nperm);
     ++nk;
   }
   if (L.nca > 0) {
@@ -1107,6 +1294,17 @@ int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a, const
   int k = lqc::launch_contract_all_c64(d, A, B, C, static_cast<double*>(scratch), scale,
                                        static_cast<cudaStream_t>(stream));
   return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+}
+
+int64_t lqc_contract_all_c64_scratch_bytes(int rank_a, const int64_t* ext_a, int rank_b,
+                                           const int64_t* ext_b, int npairs, const int* la,
+                                           const int* ra, int64_t lt) {
+  if (!ext_a || !ext_b || !la || !ra || lt < 1) return 0;
+  lqc::ContractAllDesc d;
+  std::string err;
+  if (!lqc::make_contract_all_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &d, &err))
+    return 0;
+  return lqc::contract_all_c64_scratch_bytes(d);
 }
 
 int lqc_mixed_error(int reset) { return lqc::mixed_error_status(reset != 0); }

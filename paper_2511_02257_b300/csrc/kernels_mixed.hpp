@@ -30,6 +30,30 @@ struct MixedDesc {
 };
 
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d);
+
+// Permuted copy of a complex64 tensor into a contiguous layout:
+// dst[t][i] = src[t][offset of dst index i], the dst axes listed row-major with
+// their source strides.  Rows that stay contiguous in the source are copied
+// as runs; otherwise 32 x 32 tiles are transposed through shared memory, so
+// both the reads and the writes are coalesced.
+struct PermDesc {
+  int lt;
+  long long n, src_ts;   // elements per slice of dst, of src
+  int mode;              // 0: runs along dst's innermost axis, 1: transposed tiles
+  int X, Y;              // extents: dst innermost axis; (mode 1) the src-contiguous axis
+  long long sX, dY;      // (mode 1) src stride of the dst innermost axis, dst stride of Y
+  int nout;              // outer axes (everything else), row-major
+  int oext[LQC_MAX_RANK];
+  long long osrc[LQC_MAX_RANK], odst[LQC_MAX_RANK];
+  long long outer;       // outer index combinations
+  long long blocks;      // blocks per slice
+};
+// g: dst axes (extent, source stride), row-major order.
+void make_perm_desc(const Group& g, int64_t lt, int64_t src_ts, PermDesc* d);
+int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStream_t s);
+// bytes of scratch the complex64 contract-all needs (partials + a reordered
+// copy of the right operand when its pairing is not contiguous)
+int64_t contract_all_c64_scratch_bytes(const ContractAllDesc& d);
 // A, B, C: complex64 tensors (interleaved floats); scratch: d.scratch_bytes.
 // Returns kernels launched, -1 launch error, -2 tensor-map encode failure.
 int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, float* C,
@@ -47,7 +71,8 @@ struct GroupExt {
   float* C;
   char* scratch;
 };
-// one correlator of a level: partial sums in `part` (lt * chunks complex128)
+// one correlator of a level: its scratch region `part` of
+// contract_all_c64_scratch_bytes (partials, then the reordered right operand)
 struct GroupRoot {
   const ContractAllDesc* d;
   const float* A;
@@ -67,6 +92,9 @@ struct LevelDev {
   const void* red;
   int nred;
   long long red_blocks;
+  const void* perm;
+  int nperm;
+  long long perm_blocks;
   const void* ca;
   int nca;
   long long ca_blocks, ca_threads;

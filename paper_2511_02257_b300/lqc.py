@@ -107,6 +107,8 @@ _sig("lqc_contract_all_c64", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, c_vp, cty
                                             ctypes.c_int, P_int, P_int, c_i64, ctypes.c_double,
                                             c_vp, c_vp, c_vp])
 _sig("lqc_mixed_error", ctypes.c_int, [ctypes.c_int])
+_sig("lqc_contract_all_c64_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c_int, P_i64,
+                                                   ctypes.c_int, P_int, P_int, c_i64])
 
 # re-export the raw entry points under their C names
 for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
@@ -118,7 +120,7 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_
            "lqc_dag_get_kernel_times",
            "lqc_contract_fp64", "lqc_contract_all_fp64", "lqc_contract_all_scratch_bytes",
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
-           "lqc_contract_all_c64", "lqc_mixed_error"):
+           "lqc_contract_all_c64", "lqc_mixed_error", "lqc_contract_all_c64_scratch_bytes"):
     globals()[_n] = getattr(_lib, _n)
 
 

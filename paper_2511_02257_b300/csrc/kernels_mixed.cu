@@ -46,6 +46,7 @@ constexpr int kStages = 3;
 constexpr int kTmemCols = 4 * kBN;  // 2 buffers x (main + correction accumulator)
 constexpr int64_t kMaxChunk = 1024;  // real k summed in FP32 registers before an FP64 sum
 constexpr int kDrainWarps = 8;  // two per TMEM lane quarter, one per column half
+constexpr int kConvWarps = 4;   // fused form: raw complex64 tiles -> hi/lo operand tiles
 constexpr int kGemmThreads = 64 + 32 * kDrainWarps;
 constexpr int kChunkBlocks = 2;     // k-blocks per TMEM accumulation before a drain
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
@@ -139,6 +140,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <bool BF16>
+struct Split;
+template <>
+struct Split<false> {
+  typedef float T;
+  __device__ static void split(float x, float& hi, float& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+    lo = __uint_as_float(l);
+  }
+  __device__ static void store2(float* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
+};
+template <>
+struct Split<true> {
+  typedef __nv_bfloat16 T;
+  __device__ static void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+  }
+  __device__ static void store2(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
+    __nv_bfloat162 v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<__nv_bfloat162*>(p) = v;
+  }
+};
+
 // instruction descriptor: D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16),
 // both K-major, M = 128, N = kBN
 template <bool BF16>
@@ -181,14 +214,25 @@ __device__ __forceinline__ const GemmTask* tile_task(const GemmParams& gp, long 
 }
 
 
-template <bool BF16>
+// FUSED (TF32 only): the producer loads raw complex64 K-major tiles (A: 128
+// rows, B: 64 complex rows, 128 bytes of k each) into a raw ring and
+// converter warps write the hi/lo operand tiles (B' rows 2n / 2n+1 built from
+// complex row n) into the operand ring; otherwise the producer loads the
+// four precomputed planes directly into the operand ring.
+template <bool BF16, bool FUSED = false>
 struct GemmCfg {
   static constexpr int kElem = BF16 ? 2 : 4;
   static constexpr int kBK = 128 / kElem;           // elements per 128-byte row
   static constexpr int kATile = kBM * 128;          // bytes of one A plane tile
   static constexpr int kBTile = kBN * 128;
   static constexpr int kStageBytes = 2 * kATile + 2 * kBTile;
-  static constexpr int kSmem = kStages * kStageBytes + 1024 /* align */ + 256 /* barriers */;
+  static constexpr int kOpStages = FUSED ? 2 : kStages;
+  static constexpr int kRawStages = FUSED ? 3 : 0;
+  static constexpr int kRawA = kBM * 128, kRawB = (kBN / 2) * 128;
+  static constexpr int kRawBytes = kRawA + kRawB;
+  static constexpr int kThreads = kGemmThreads + (FUSED ? 32 * kConvWarps : 0);
+  static constexpr int kSmem = kOpStages * kStageBytes + kRawStages * kRawBytes +
+                               1024 /* align */ + 256 /* barriers */;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -206,27 +250,35 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // cycling across tiles and tasks, so a tile's store overlaps the next tile's
 // MMAs.  The drain warps empty a buffer every kChunkBlocks k-blocks into FP32
 // registers.
-template <bool BF16>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+template <bool BF16, bool FUSED>
+__global__ void __launch_bounds__(GemmCfg<BF16, FUSED>::kThreads, 1)
 k_gemm_split3(const __grid_constant__ GemmParams gp) {
-  using C = GemmCfg<BF16>;
+  using C = GemmCfg<BF16, FUSED>;
+  constexpr int S = C::kOpStages, R = C::kRawStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* tfull = empty + kStages;   // [2] accumulator buffer ready to drain
+  uint8_t* raw = smem + S * C::kStageBytes;  // FUSED: raw complex64 ring
+  uint64_t* full = reinterpret_cast<uint64_t*>(raw + R * C::kRawBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;         // [2] accumulator buffer ready to drain
   uint64_t* tempty = tfull + 2;        // [2] accumulator buffer drained
   uint64_t* done = tempty + 2;         // every MMA issued has completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* rfull = done + 1;          // FUSED [R] raw stage landed
+  uint64_t* rempty = rfull + R;        // FUSED [R] raw stage converted
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], FUSED ? kConvWarps : 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < R; ++i) {
+      mbar_init(&rfull[i], 1);
+      mbar_init(&rempty[i], kConvWarps);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -250,6 +302,9 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer
+      constexpr int RS = FUSED ? R : S;  // ring the producer fills
+      uint64_t* rf = FUSED ? rfull : full;
+      uint64_t* re = FUSED ? rempty : empty;
       int g = 0, issued = 0, k = 0, local = 0;
       bool stop = false;
       for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
@@ -259,26 +314,33 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         const int t = z % tk->lt, split = z / tk->lt;
         const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * tk->kblocks;
         for (int i = 0; i < tk->kblocks; ++i, ++g) {
-          const int s = g % kStages;
-          const uint32_t ph = (uint32_t)(g / kStages) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
+          const int st = g % RS;
+          const uint32_t ph = (uint32_t)(g / RS) & 1u;
+          if (!mbar_wait(&re[st], ph ^ 1u) || *abort_flag) {
             *abort_flag = 1;
             stop = true;
             break;
           }
-          uint8_t* st = smem + s * C::kStageBytes;
-          mbar_expect_tx(&full[s], C::kStageBytes);
           const int k0 = (kb0 + i) * C::kBK;
-          tma_load_3d(st, &tk->map[0], &full[s], k0, m0, t);
-          tma_load_3d(st + C::kATile, &tk->map[1], &full[s], k0, m0, t);
-          tma_load_3d(st + 2 * C::kATile, &tk->map[2], &full[s], k0, n0, t);
-          tma_load_3d(st + 2 * C::kATile + C::kBTile, &tk->map[3], &full[s], k0, n0, t);
+          if (FUSED) {
+            uint8_t* rp = raw + st * C::kRawBytes;
+            mbar_expect_tx(&rf[st], C::kRawBytes);
+            tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
+            tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], k0, n0 / 2, t);
+          } else {
+            uint8_t* sp = smem + st * C::kStageBytes;
+            mbar_expect_tx(&rf[st], C::kStageBytes);
+            tma_load_3d(sp, &tk->map[0], &rf[st], k0, m0, t);
+            tma_load_3d(sp + C::kATile, &tk->map[1], &rf[st], k0, m0, t);
+            tma_load_3d(sp + 2 * C::kATile, &tk->map[2], &rf[st], k0, n0, t);
+            tma_load_3d(sp + 2 * C::kATile + C::kBTile, &tk->map[3], &rf[st], k0, n0, t);
+          }
           issued = g + 1;
         }
       }
-      // every issued stage must have landed before the CTA exits
-      for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
-        if (!mbar_wait(&full[i % kStages], (uint32_t)(i / kStages) & 1u)) break;
+      // every issued load must have landed before the CTA exits
+      for (int i = (issued > RS ? issued - RS : 0); i < issued; ++i)
+        if (!mbar_wait(&rf[i % RS], (uint32_t)(i / RS) & 1u)) break;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -301,15 +363,15 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
-          const int s = g % kStages;
-          const uint32_t ph = (uint32_t)(g / kStages) & 1u;
-          if (!mbar_wait(&full[s], ph) || *abort_flag) {
+          const int st = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(&full[st], ph) || *abort_flag) {
             *abort_flag = 1;
             stop = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t base = smem_u32(smem + s * C::kStageBytes);
+          const uint32_t base = smem_u32(smem + st * C::kStageBytes);
           const uint32_t ahi = base, alo = base + C::kATile;
           const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
           const uint32_t dmain = tmem + (uint32_t)(b * 2 * kBN), dcorr = dmain + kBN;
@@ -321,7 +383,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
             umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
           }
-          umma_commit(&empty[s]);    // stage reusable once these MMAs have read it
+          umma_commit(&empty[st]);   // stage reusable once these MMAs have read it
           if (last) {
             umma_commit(&tfull[b]);
             ++cc;
@@ -330,7 +392,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
       }
       umma_commit(done);             // all issued MMAs complete (or abandoned)
     }
-  } else {
+  } else if (warp < 2 + kDrainWarps) {
     // ---- drain / epilogue warps
     constexpr int kHalf = kBN / 2;
     const int q = warp & 3;          // TMEM lane quarter of this warp
@@ -388,6 +450,69 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         }
       }
     }
+  } else if (FUSED) {
+    // ---- converter warps: raw complex64 tiles -> hi/lo operand tiles
+    const int ct = threadIdx.x - 32 * (2 + kDrainWarps);  // 0 .. 32*kConvWarps-1
+    constexpr int kCT = 32 * kConvWarps;
+    int g = 0, k = 0, local = 0, ok = 1;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+      const GemmTask* tk = tile_task(gp, tile, k, local);
+      for (int i = 0; i < tk->kblocks; ++i, ++g) {
+        const int r = g % R, st = g % S;
+        if (lane == 0) {
+          if (!mbar_wait(&rfull[r], (uint32_t)(g / R) & 1u) ||
+              !mbar_wait(&empty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const uint8_t* rp = raw + r * C::kRawBytes;
+        uint8_t* sp = smem + st * C::kStageBytes;
+        // A: same 128-byte-swizzled layout in and out, element by element
+#pragma unroll 4
+        for (int c = ct; c < C::kRawA / 16; c += kCT) {
+          const float4 v = *reinterpret_cast<const float4*>(rp + 16 * c);
+          float h0, l0, h1, l1, h2, l2, h3, l3;
+          Split<false>::split(v.x, h0, l0);
+          Split<false>::split(v.y, h1, l1);
+          Split<false>::split(v.z, h2, l2);
+          Split<false>::split(v.w, h3, l3);
+          *reinterpret_cast<float4*>(sp + 16 * c) = make_float4(h0, h1, h2, h3);
+          *reinterpret_cast<float4*>(sp + C::kATile + 16 * c) = make_float4(l0, l1, l2, l3);
+        }
+        // B: complex row n -> B' rows 2n (re, -im) and 2n+1 (im, re); 16-byte
+        // chunk c of row r sits at chunk c ^ (r & 7) (128-byte swizzle)
+#pragma unroll 2
+        for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
+          const int n = it >> 3, c = it & 7;
+          const float4 v =
+              *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 + 16 * (c ^ (n & 7)));
+          const int r0 = 2 * n, r1 = 2 * n + 1;
+          const int o0 = r0 * 128 + 16 * (c ^ (r0 & 7)), o1 = r1 * 128 + 16 * (c ^ (r1 & 7));
+          float h[4], l[4];
+          Split<false>::split(v.x, h[0], l[0]);
+          Split<false>::split(-v.y, h[1], l[1]);
+          Split<false>::split(v.z, h[2], l[2]);
+          Split<false>::split(-v.w, h[3], l[3]);
+          uint8_t* bh = sp + 2 * C::kATile;
+          uint8_t* bl = bh + C::kBTile;
+          *reinterpret_cast<float4*>(bh + o0) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(bl + o0) = make_float4(l[0], l[1], l[2], l[3]);
+          // row 2n+1 = (im, re): the same split parts, re-paired
+          *reinterpret_cast<float4*>(bh + o1) = make_float4(-h[1], h[0], -h[3], h[2]);
+          *reinterpret_cast<float4*>(bl + o1) = make_float4(-l[1], l[0], -l[3], l[2]);
+        }
+        // generic-proxy writes -> visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&full[st]);
+          mbar_arrive(&rempty[r]);
+        }
+      }
+    }
   }
   // teardown: no MMA may still write TMEM when it is released
   if (warp == 1 && lane == 0) {
@@ -426,38 +551,6 @@ __device__ __forceinline__ long long goff(const Group& g, unsigned idx) {
   }
   return off;
 }
-
-template <bool BF16>
-struct Split;
-template <>
-struct Split<false> {
-  typedef float T;
-  __device__ static void split(float x, float& hi, float& lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
-    lo = __uint_as_float(l);
-  }
-  __device__ static void store2(float* p, float a, float b) {
-    *reinterpret_cast<float2*>(p) = make_float2(a, b);
-  }
-};
-template <>
-struct Split<true> {
-  typedef __nv_bfloat16 T;
-  __device__ static void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-  }
-  __device__ static void store2(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
-    __nv_bfloat162 v;
-    v.x = a;
-    v.y = b;
-    *reinterpret_cast<__nv_bfloat162*>(p) = v;
-  }
-};
 
 template <bool BF16>
 struct PackPair {
@@ -821,6 +914,22 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t r
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// 3-D fp32 map over raw complex64 rows: dims (2K floats, rows, lt), strides
+// in complex elements, box (32 floats = 128 bytes, box_rows, 1)
+bool make_raw_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t lt,
+                  int64_t row_stride, int64_t slice_stride, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)k2, (cuuint64_t)std::max<int64_t>(rows, 1), (cuuint64_t)lt};
+  cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 8), (cuuint64_t)(slice_stride * 8)};
+  cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int num_sms() {  // SMs of the current device (one persistent CTA each)
   static int cached[64] = {0};
   int dev = 0;
@@ -839,6 +948,9 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
   std::memset(d, 0, sizeof(*d));
   d->bf16 = bf16;
   d->cd = cd;
+  // fused form: TF32 with an even paired extent (16-byte complex64 rows)
+  d->fused = !bf16 && (cd.K % 2 == 0);
+  if (d->fused) return make_fused_desc(cd, d);
   const int es = bf16 ? 2 : 4;
   d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA
   const int64_t bk = 128 / es;                  // elements per k block
@@ -860,6 +972,66 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
   d->scratch_bytes = d->part_off + (splits > 1 ? splits * cd.lt * cd.M * 2 * cd.N * 4 : 0);
   d->plane_a = plane_a;
   d->plane_b = plane_b;
+  return cd.M < (1 << 30) && 2 * cd.N < (1 << 30) && d->kp < (1 << 30);
+}
+
+namespace {
+// split count: k splits when the output tiles alone cannot fill the GPU
+// (keeping >= 4 k blocks per split), and FP32 chunks of <= kMaxChunk real k
+int64_t choose_splits(const ContractDesc& cd, int64_t kblocks, int64_t bk) {
+  const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
+  int64_t splits = 1;
+  while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
+  while ((kblocks + splits - 1) / splits * bk > kMaxChunk && splits < 64) splits *= 2;
+  return splits;
+}
+// dst axes (rows group, then k group) with the operand's strides
+Group concat_groups(const Group& rows, const Group& ks) {
+  Group g;
+  g.n = 0;
+  for (int a = 0; a < rows.n; ++a) {
+    g.ext[g.n] = rows.ext[a];
+    g.stride[g.n++] = rows.stride[a];
+  }
+  for (int a = 0; a < ks.n; ++a) {
+    g.ext[g.n] = ks.ext[a];
+    g.stride[g.n++] = ks.stride[a];
+  }
+  return g;
+}
+}  // namespace
+
+bool make_fused_desc(const ContractDesc& cd, MixedDesc* d) {
+  d->kp = 2 * cd.K;                              // real k of a complex64 row
+  const int64_t bk = 32;                         // fp32 elements per 128-byte k block
+  const int64_t kblocks = (d->kp + bk - 1) / bk;
+  const int64_t splits = choose_splits(cd, kblocks, bk);
+  d->splits = (int)splits;
+  d->kblocks = (int)((kblocks + splits - 1) / splits);
+  // an operand whose paired axes form its unit-stride axis and whose free
+  // axes collapse to one row stride is read in place; otherwise it is
+  // reordered into [t][rows][K]
+  auto direct = [](const Group& rows, const Group& ks, int kfast) {
+    return kfast && ks.n == 1 && ks.stride[0] == 1 &&
+           (rows.n == 0 || (rows.n == 1 && rows.stride[0] % 2 == 0));
+  };
+  d->a_direct = direct(cd.am, cd.ak, cd.a_kfast) && cd.a_ts % 2 == 0;
+  d->b_direct = direct(cd.bn, cd.bk, cd.b_kfast) && cd.b_ts % 2 == 0;
+  d->a_rowstride = d->a_direct ? (cd.am.n ? cd.am.stride[0] : cd.K) : cd.K;
+  d->b_rowstride = d->b_direct ? (cd.bn.n ? cd.bn.stride[0] : cd.K) : cd.K;
+  int64_t off = 0;
+  d->a_off = off;
+  if (!d->a_direct) {
+    make_perm_desc(concat_groups(cd.am, cd.ak), cd.lt, cd.a_ts, &d->a_perm);
+    off = round_up(off + cd.lt * cd.M * cd.K * 8, 256);
+  }
+  d->b_off = off;
+  if (!d->b_direct) {
+    make_perm_desc(concat_groups(cd.bn, cd.bk), cd.lt, cd.b_ts, &d->b_perm);
+    off = round_up(off + cd.lt * cd.N * cd.K * 8, 256);
+  }
+  d->part_off = off;
+  d->scratch_bytes = off + (splits > 1 ? splits * cd.lt * cd.M * 2 * cd.N * 4 : 0);
   return cd.M < (1 << 30) && 2 * cd.N < (1 << 30) && d->kp < (1 << 30);
 }
 
@@ -886,11 +1058,20 @@ static PackArgs pack_args(const ContractDesc& cd, int which, int64_t kp) {
 }
 
 // task of one contraction whose planes / partials live in `scratch`
-bool fill_gemm_task(const MixedDesc& d, void* scratch, float* C, GemmTask* t) {
+bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* scratch, float* C,
+                    GemmTask* t) {
   const ContractDesc& cd = d.cd;
   char* sc = static_cast<char*>(scratch);
   std::memset(t, 0, sizeof(*t));
-  if (!make_map(&t->map[0], sc + d.a_off, d.bf16, d.kp, cd.M, cd.lt) ||
+  if (d.fused) {
+    const void* a = d.a_direct ? (const void*)A : (const void*)(sc + d.a_off);
+    const void* b = d.b_direct ? (const void*)B : (const void*)(sc + d.b_off);
+    const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
+    const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
+    if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM) ||
+        !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts, kBN / 2))
+      return false;
+  } else if (!make_map(&t->map[0], sc + d.a_off, d.bf16, d.kp, cd.M, cd.lt) ||
       !make_map(&t->map[1], sc + d.a_off + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
       !make_map(&t->map[2], sc + d.b_off, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
       !make_map(&t->map[3], sc + d.b_off + d.plane_b, d.bf16, d.kp, 2 * cd.N, cd.lt))
@@ -907,24 +1088,59 @@ bool fill_gemm_task(const MixedDesc& d, void* scratch, float* C, GemmTask* t) {
   return true;
 }
 
-int launch_gemm(const GemmParams& gp, bool bf16, cudaStream_t s) {
+// operand reorders of a fused contraction (0, 1 or 2 launches)
+int launch_fused_copies(const MixedDesc& d, const float* A, const float* B, void* scratch,
+                        cudaStream_t s) {
+  int nk = 0;
+  char* sc = static_cast<char*>(scratch);
+  if (!d.a_direct) {
+    if (launch_permute_c64(d.a_perm, A, reinterpret_cast<float*>(sc + d.a_off), s) < 0) return -1;
+    ++nk;
+  }
+  if (!d.b_direct) {
+    if (launch_permute_c64(d.b_perm, B, reinterpret_cast<float*>(sc + d.b_off), s) < 0) return -1;
+    ++nk;
+  }
+  return nk;
+}
+
+template <bool BF16, bool FUSED>
+void launch_gemm_t(const GemmParams& gp, dim3 grid, cudaStream_t s) {
+  using C = GemmCfg<BF16, FUSED>;
+  cudaFuncSetAttribute(k_gemm_split3<BF16, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       C::kSmem);
+  k_gemm_split3<BF16, FUSED><<<grid, C::kThreads, C::kSmem, s>>>(gp);
+}
+
+int launch_gemm(const GemmParams& gp, bool bf16, bool fused, cudaStream_t s) {
   if (gp.total_tiles <= 0) return 0;
   dim3 grid((unsigned)std::min<long long>(gp.total_tiles, num_sms()));
-  if (bf16) {
-    const int smem = GemmCfg<true>::kSmem;
-    cudaFuncSetAttribute(k_gemm_split3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_gemm_split3<true><<<grid, kGemmThreads, smem, s>>>(gp);
-  } else {
-    const int smem = GemmCfg<false>::kSmem;
-    cudaFuncSetAttribute(k_gemm_split3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_gemm_split3<false><<<grid, kGemmThreads, smem, s>>>(gp);
-  }
+  if (fused) launch_gemm_t<false, true>(gp, grid, s);
+  else if (bf16) launch_gemm_t<true, false>(gp, grid, s);
+  else launch_gemm_t<false, false>(gp, grid, s);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, float* C,
                           void* scratch, cudaStream_t s) {
   const ContractDesc& cd = d.cd;
+  if (d.fused) {
+    int nk = launch_fused_copies(d, A, B, scratch, s);
+    if (nk < 0) return -1;
+    GemmParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    if (!fill_gemm_task(d, A, B, scratch, C, &gp.single)) return -2;
+    gp.total_tiles = gp.single.tiles;
+    if (launch_gemm(gp, false, true, s) < 0) return -1;
+    ++nk;
+    if (d.splits > 1) {
+      const long long per = cd.lt * cd.M * 2 * cd.N;
+      unsigned blocks = (unsigned)std::min<long long>((per + 255) / 256, 8 * 148);
+      k_reduce_splits<<<blocks, 256, 0, s>>>(gp.single.out, C, per, d.splits);
+      ++nk;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? nk : -1;
+  }
   char* sc = static_cast<char*>(scratch);
   void* ahi = sc + d.a_off;
   void* alo = sc + d.a_off + d.plane_a;
@@ -964,9 +1180,9 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
   }
   GemmParams gp;
   std::memset(&gp, 0, sizeof(gp));
-  if (!fill_gemm_task(d, scratch, C, &gp.single)) return -2;
+  if (!fill_gemm_task(d, A, B, scratch, C, &gp.single)) return -2;
   gp.total_tiles = gp.single.tiles;
-  if (launch_gemm(gp, d.bf16, s) < 0) return -1;
+  if (launch_gemm(gp, d.bf16, false, s) < 0) return -1;
   ++nk;
   if (d.splits > 1) {
     const long long per = cd.lt * cd.M * 2 * cd.N;
@@ -1115,11 +1331,44 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   std::vector<ReduceTask> rd;
   std::vector<CATask> ca;
   std::vector<PermTask> pm;
-  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0;
+  std::vector<GemmTask> gf;  // fused-form GEMM tasks
+  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0, ftiles = 0;
+  auto add_perm = [&](const PermDesc& pd, const void* src, void* dst) {
+    PermTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.d = pd;
+    t.src = static_cast<const float2*>(src);
+    t.dst = static_cast<float2*>(dst);
+    t.block_start = mb;
+    mb += t.d.blocks * t.d.lt;
+    pm.push_back(t);
+  };
+  auto add_reduce = [&](const MixedDesc& d, const GemmTask& g, float* C) {
+    const ContractDesc& cd = d.cd;
+    ReduceTask r;
+    r.part = g.out;
+    r.out = C;
+    r.per = cd.lt * cd.M * 2 * cd.N;
+    r.splits = d.splits;
+    r.block_start = rb;
+    rb += (r.per + kReduceElems - 1) / kReduceElems;
+    rd.push_back(r);
+  };
   for (const GroupExt& e : ext) {
     const MixedDesc& d = *e.d;
     const ContractDesc& cd = d.cd;
     char* sc = e.scratch;
+    if (d.fused) {
+      if (!d.a_direct) add_perm(d.a_perm, e.A, sc + d.a_off);
+      if (!d.b_direct) add_perm(d.b_perm, e.B, sc + d.b_off);
+      GemmTask g;
+      if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g)) return false;
+      g.tile_start = ftiles;
+      ftiles += g.tiles;
+      gf.push_back(g);
+      if (d.splits > 1) add_reduce(d, g, e.C);
+      continue;
+    }
     PackTask p;
     std::memset(&p, 0, sizeof(p));
     p.op[0] = pack_args(cd, 0, d.kp);
@@ -1138,20 +1387,11 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     pb += (long long)p.kblk * p.rblk * 2 * p.lt;
     pk.push_back(p);
     GemmTask g;
-    if (!fill_gemm_task(d, e.scratch, e.C, &g)) return false;
+    if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g)) return false;
     g.tile_start = tiles;
     tiles += g.tiles;
     gm.push_back(g);
-    if (d.splits > 1) {
-      ReduceTask r;
-      r.part = g.out;
-      r.out = e.C;
-      r.per = cd.lt * cd.M * 2 * cd.N;
-      r.splits = d.splits;
-      r.block_start = rb;
-      rb += (r.per + kReduceElems - 1) / kReduceElems;
-      rd.push_back(r);
-    }
+    if (d.splits > 1) add_reduce(d, g, e.C);
   }
   for (const GroupRoot& r : roots) {
     CATask c;
@@ -1162,15 +1402,11 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     c.part = reinterpret_cast<double2*>(r.part);
     c.d = *r.d;
     if (ca_needs_copy(*r.d)) {
-      PermTask t;
-      std::memset(&t, 0, sizeof(t));
-      make_perm_desc(r.d->bp, r.d->lt, r.d->S, &t.d);
-      t.src = reinterpret_cast<const float2*>(r.B);
-      t.dst = reinterpret_cast<float2*>(reinterpret_cast<char*>(r.part) + ca_part_bytes(*r.d));
-      t.block_start = mb;
-      mb += t.d.blocks * t.d.lt;
-      pm.push_back(t);
-      c.B = t.dst;
+      PermDesc pd;
+      make_perm_desc(r.d->bp, r.d->lt, r.d->S, &pd);
+      void* dst = reinterpret_cast<char*>(r.part) + ca_part_bytes(*r.d);
+      add_perm(pd, r.B, dst);
+      c.B = static_cast<const float2*>(dst);
       c.d = ca_identity(*r.d);
     }
     c.scale = r.scale;
@@ -1186,6 +1422,9 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->gemm = reinterpret_cast<const void*>(append(buf, gm, 64));
   lvl->ngemm = (int)gm.size();
   lvl->gemm_tiles = tiles;
+  lvl->gemm_fused = reinterpret_cast<const void*>(append(buf, gf, 64));
+  lvl->ngemm_fused = (int)gf.size();
+  lvl->gemm_fused_tiles = ftiles;
   lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
   lvl->nred = (int)rd.size();
   lvl->red_blocks = rb;
@@ -1205,11 +1444,17 @@ void rebase_level(LevelDev* lvl, const char* base) {
   lvl->gemm = base + reinterpret_cast<uintptr_t>(lvl->gemm);
   lvl->red = base + reinterpret_cast<uintptr_t>(lvl->red);
   lvl->perm = base + reinterpret_cast<uintptr_t>(lvl->perm);
+  lvl->gemm_fused = base + reinterpret_cast<uintptr_t>(lvl->gemm_fused);
   lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
 }
 
 int launch_level(const LevelDev& L, cudaStream_t s) {
   int nk = 0;
+  if (L.nperm > 0) {  // operand reorders of fused GEMMs and correlator partners
+    k_permute_grouped<<<(unsigned)L.perm_blocks, 256, 0, s>>>(
+        static_cast<const PermTask*>(L.perm), L.nperm);
+    ++nk;
+  }
   if (L.npack > 0) {
     if (L.bf16)
       k_pack_grouped<true><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
@@ -1223,17 +1468,21 @@ int launch_level(const LevelDev& L, cudaStream_t s) {
     gp.tasks = static_cast<const GemmTask*>(L.gemm);
     gp.ntasks = L.ngemm;
     gp.total_tiles = L.gemm_tiles;
-    if (launch_gemm(gp, L.bf16, s) < 0) return -1;
+    if (launch_gemm(gp, L.bf16, false, s) < 0) return -1;
+    ++nk;
+  }
+  if (L.ngemm_fused > 0) {
+    GemmParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.tasks = static_cast<const GemmTask*>(L.gemm_fused);
+    gp.ntasks = L.ngemm_fused;
+    gp.total_tiles = L.gemm_fused_tiles;
+    if (launch_gemm(gp, false, true, s) < 0) return -1;
     ++nk;
   }
   if (L.nred > 0) {
     k_reduce_grouped<<<(unsigned)L.red_blocks, 256, 0, s>>>(
         static_cast<const ReduceTask*>(L.red), L.nred);
-    ++nk;
-  }
-  if (L.nperm > 0) {
-    k_permute_grouped<<<(unsigned)L.perm_blocks, 256, 0, s>>>(
-        static_cast<const PermTask*>(L.perm), L.nperm);
     ++nk;
   }
   if (L.nca > 0) {

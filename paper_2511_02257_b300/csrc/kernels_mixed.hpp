@@ -20,17 +20,6 @@ struct PackArgs {
   Group rg, kg;     // row group (free axes) and k group (paired axes)
 };
 
-struct MixedDesc {
-  ContractDesc cd;
-  bool bf16;
-  int64_t kp;               // real k (2K) padded to 16-byte rows
-  int splits, kblocks;      // k splits and k blocks per split
-  int64_t plane_a, plane_b; // bytes of one hi or lo plane
-  int64_t a_off, b_off, part_off, scratch_bytes;
-};
-
-bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d);
-
 // Permuted copy of a complex64 tensor into a contiguous layout:
 // dst[t][i] = src[t][offset of dst index i], the dst axes listed row-major with
 // their source strides.  Rows that stay contiguous in the source are copied
@@ -48,6 +37,24 @@ struct PermDesc {
   long long outer;       // outer index combinations
   long long blocks;      // blocks per slice
 };
+struct MixedDesc {
+  ContractDesc cd;
+  bool bf16;
+  int64_t kp;               // real k (2K) padded to 16-byte rows
+  int splits, kblocks;      // k splits and k blocks per split
+  int64_t plane_a, plane_b; // bytes of one hi or lo plane
+  int64_t a_off, b_off, part_off, scratch_bytes;
+  // fused form (TF32, even K): raw complex64 operands, read in place when
+  // already [rows][K] with K unit-stride, else reordered into scratch
+  bool fused;
+  bool a_direct, b_direct;
+  int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
+  PermDesc a_perm, b_perm;
+};
+bool make_fused_desc(const ContractDesc& cd, MixedDesc* d);
+
+bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d);
+
 // g: dst axes (extent, source stride), row-major order.
 void make_perm_desc(const Group& g, int64_t lt, int64_t src_ts, PermDesc* d);
 int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStream_t s);
@@ -89,6 +96,9 @@ struct LevelDev {
   const void* gemm;
   int ngemm;
   long long gemm_tiles;
+  const void* gemm_fused;
+  int ngemm_fused;
+  long long gemm_fused_tiles;
   const void* red;
   int nred;
   long long red_blocks;

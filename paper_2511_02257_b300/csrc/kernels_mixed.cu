@@ -948,8 +948,13 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
   std::memset(d, 0, sizeof(*d));
   d->bf16 = bf16;
   d->cd = cd;
-  // fused form: TF32 with an even paired extent (16-byte complex64 rows)
-  d->fused = !bf16 && (cd.K % 2 == 0);
+  // fused form: TF32 with an even paired extent (16-byte complex64 rows) and
+  // a narrow right operand (<= 64 complex columns).  There the hi/lo planes
+  // of the plane form cost more HBM traffic than the contraction itself; for
+  // wide operands the plane form is faster (its operand tiles reach shared
+  // memory by TMA alone, while the converter warps add shared-memory traffic
+  // next to the three MMAs per k-step).
+  d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= 64;
   if (d->fused) return make_fused_desc(cd, d);
   const int es = bf16 ? 2 : 4;
   d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA

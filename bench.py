@@ -36,6 +36,18 @@ sys.path.insert(0, HERE)
 # until captured for the current kernel build; see profiles/).
 TRAFFIC_PER_LAUNCH = None
 FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 rate, nominal
+# dense tensor rates relative to BF16 (nominal B300 figures: TF32 1.1 and
+# BF16 2.25 PFLOP/s), applied to the measured BF16 GEMM peak
+TENSOR_RATIO = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, \
+            "fallback"
 
 
 def parse():
@@ -52,6 +64,10 @@ def parse():
                     help="1: replay the whole execute as one CUDA graph")
     ap.add_argument("--window", type=int, default=64,
                     help="grouped-window size of the mixed path (0 = one contraction at a time)")
+    ap.add_argument("--compare", default="tf32x3",
+                    help="with --precision fp64: also time this mixed precision on the same "
+                         "workload (grouped windows, graphs) and report its speedup and "
+                         "error against the FP64 path; 'none' skips it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -133,7 +149,7 @@ def node_flops(od, u):
     K = int(np.prod([L.extents[a] for a in nd.la], dtype=np.int64))
     M = int(np.prod(L.extents, dtype=np.int64)) // K
     N = int(np.prod(R.extents, dtype=np.int64)) // K
-    return 8 * od.lt * M * N * K
+    return 8 * nd.lt * M * N * K
 
 
 def oracle_sample(wl, seconds, rng_seed=0):
@@ -293,6 +309,7 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     info1 = nd.exec_info()
+    corr = nd.read_all_correlators()
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -314,9 +331,8 @@ def main():
     if not args.no_e2e:
         nd.set_option(L.LQC_OPT_TIMING, 0)
         nd.unstage_leaves()
-        out = np.zeros((len(nd.roots()), wl.lt), dtype=np.complex128)
         nd.execute(stream)
-        nd.read_all_correlators(out)
+        out = nd.read_all_correlators()
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -334,6 +350,35 @@ def main():
                "d2h_bytes_per_step": st["d2h_bytes"] + out.nbytes,
                "ms_per_step": 1e3 * t_e2e / args.steps}
 
+    # ---- the precision form on the same workload, against this FP64 run
+    pform = None
+    if args.precision == "fp64" and args.compare != "none":
+        md, _ = L.build_dag(wl, precision=args.compare,
+                            leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+        mplanned = md.schedule(args.policy, args.evict, budget)
+        md.stage_leaves(stream)
+        md.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
+        md.set_option(L.LQC_OPT_WINDOW, args.window)
+        for _ in range(args.warmup):
+            md.execute(stream)
+        torch.cuda.synchronize()
+        e0.record(dev_stream)
+        for _ in range(args.steps):
+            md.execute(stream)
+        e1.record(dev_stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1) / args.steps
+        mv = md.read_all_correlators()
+        err = np.linalg.norm(mv - corr, axis=-1) / np.linalg.norm(corr, axis=-1)
+        mst = md.exec_info()
+        pform = {"precision": args.compare, "window": args.window,
+                 "time_to_solution_s": mms / 1e3, "tflops": flops_step / (mms * 1e-3) / 1e12,
+                 "speedup_vs_fp64": (ms / args.steps) / mms,
+                 "err_vs_fp64_max": float(err.max()), "err_vs_fp64_median": float(np.median(err)),
+                 "kernels_per_step": mst["n_kernels"],
+                 "peak_paper_bytes": mplanned["peak_paper"]}
+        md.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         f, t, nr, nt = oracle_sample(wl, 20.0)
@@ -341,6 +386,30 @@ def main():
                "kind": "oracle",
                "sample": "%d of %d correlator trees (random, seeded) with their descendant "
                          "closures, %.2f GFLOP in %.1f s" % (nr, nt, f / 1e9, t)}
+
+    if args.precision == "fp64":
+        roofline = {"kernel": "k_contract_fp64", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
+                    "peak_source": "nominal B300 FP64 rate (profiling recipe table)",
+                    "fma_probe_tflops": probe,
+                    "frac_of_probe": achieved / probe if achieved else None,
+                    "traffic": TRAFFIC_PER_LAUNCH}
+    else:
+        # split products: 3 real-embedded GEMMs per complex contraction, each
+        # 8 real flops per complex multiply-add (windows time whole levels,
+        # so the kernel time is that of the grouped launches)
+        peaks, src = measured_peaks()
+        peak = peaks["bf16_tflops"] * TENSOR_RATIO[args.precision]
+        ach = 3 * achieved if achieved else None
+        roofline = {"kernel": "k_gemm_split3", "bound": "tensor", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if ach else None,
+                    "peak_source": "%s BF16 GEMM peak x nominal %s/BF16 ratio %.3f"
+                                   % (src, args.precision[:4].upper(),
+                                      TENSOR_RATIO[args.precision]),
+                    "algorithmic_complex_tflops": achieved, "traffic": None}
+    roofline.update({"launches": n_c, "kernel_ms_per_step": ms_c / args.steps,
+                     "contract_all_ms_per_step": ms_a / args.steps})
 
     if rank == 0:
         line = {
@@ -364,16 +433,9 @@ def main():
             "n_evict": planned["n_evict"], "h2d_gb_per_step": planned["h2d_bytes"] / 1e9,
             "d2h_gb_per_step": planned["d2h_bytes"] / 1e9,
             "schedule_ms": 1e3 * t_sched, "dag_build_s": t_build,
-            "roofline": {"kernel": "k_contract_fp64", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
-                         "peak_source": "nominal B300 FP64 rate (profiling recipe table)",
-                         "fma_probe_tflops": probe,
-                         "frac_of_probe": achieved / probe if achieved else None,
-                         "traffic": TRAFFIC_PER_LAUNCH,
-                         "launches": n_c, "kernel_ms_per_step": ms_c / args.steps,
-                         "contract_all_ms_per_step": ms_a / args.steps},
+            "roofline": roofline,
             "kernel_ms_by_shape": breakdown,
+            "precision_form": pform,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -126,10 +126,19 @@ typedef enum {
                              Timing then covers whole windows              */
 } lqc_option;
 
-/* Create an empty DAG.  lt >= 1 time slices; prec selects storage and
+/* Create an empty DAG.  lt >= 1 time slices (the batch extent of the
+ * leaves registered next, see lqc_dag_set_batch); prec selects storage and
  * arithmetic.  *out receives the handle (owned by the caller, released with
  * lqc_dag_destroy). */
 int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec);
+
+/* Batch extent (time slices) of the leaves registered after this call.
+ * Lets one DAG hold several independent problems with different lt (a
+ * batched workload): a contraction's operands must share one batch extent,
+ * which its output inherits; a node's size (Sec. II-C) is lt_node *
+ * prod(extents) * element bytes.  Errors: LQC_ERR_ARG (lt < 1),
+ * LQC_ERR_STATE (after lqc_dag_schedule). */
+int lqc_dag_set_batch(lqc_dag* dag, int64_t lt);
 
 /* Release every host and device resource of the DAG.  Synchronises with any
  * outstanding execution first.  NULL is accepted. */
@@ -137,7 +146,8 @@ int lqc_dag_destroy(lqc_dag* dag);
 
 /* Register a leaf tensor (Sec. II-B: a node with no inputs).
  *  rank in [0, LQC_MAX_RANK], extents[rank] >= 1 (batch axis excluded).
- *  data: lt * prod(extents) complex values as interleaved doubles, or NULL
+ *  data: lt * prod(extents) complex values as interleaved doubles (lt =
+ *  the batch extent current at registration), or NULL
  *  to register the shape only (scheduling/planning without execution; set
  *  the values later with lqc_dag_set_leaf_data).  The values are copied
  *  into the library's pinned host store (mixed precisions store them
@@ -156,7 +166,8 @@ int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
 /* Register a binary contraction (a non-leaf node, Sec. II-B).
  *  left/right: existing node ids (may be equal); npairs in [1, LQC_MAX_RANK];
  *  la[i] (axis of left) is contracted with ra[i] (axis of right), extents
- *  equal, axes distinct on each side.  The output rank is
+ *  equal, axes distinct on each side; both operands have the same batch
+ *  extent (else LQC_ERR_ARG).  The output rank is
  *  rank(left) + rank(right) - 2*npairs and must not exceed LQC_MAX_RANK.
  *  A request identical to an earlier one (same left, right, la, ra) returns
  *  the earlier node's id: identical sub-contractions of different trees are
@@ -219,21 +230,24 @@ int lqc_dag_execute(lqc_dag* dag, void* stream);
 int lqc_dag_wait(lqc_dag* dag, int64_t timeout_ms);
 
 /* Correlator of a rank-0 root: out[2*t], out[2*t+1] = re, im of C_root(t),
- * t in [0, lt).  Waits for the last execute (60 s bound).
+ * t in [0, lt of the root).  Waits for the last execute (60 s bound).
  * Errors: LQC_ERR_ARG (not a rank-0 root), LQC_ERR_STATE (not executed). */
 int lqc_dag_read_correlator(lqc_dag* dag, int64_t root_id, double* out);
 
-/* All rank-0 roots at once, in ascending id: out holds n_roots * 2 * lt
- * doubles (one device-to-host copy).  Same errors as above. */
+/* All rank-0 roots at once, in ascending id, each root's 2 * lt_root
+ * doubles after the previous root's (n_roots * 2 * lt when all share one
+ * batch extent); one device-to-host copy.  Same errors as above, and
+ * LQC_ERR_ARG when cap_doubles is too small. */
 int lqc_dag_read_all_correlators(lqc_dag* dag, double* out, int64_t cap_doubles);
 
 /* Ids of the rank-0 roots in ascending order; same cap / *n convention. */
 int lqc_dag_get_roots(lqc_dag* dag, int64_t* roots, int64_t cap, int64_t* n);
 
-/* Number of nodes and the size in bytes / rank of a node. */
+/* Number of nodes and the size in bytes / rank / leaf flag / batch extent
+ * of a node (each out-pointer nullable). */
 int lqc_dag_num_nodes(lqc_dag* dag, int64_t* n);
 int lqc_dag_node_info(lqc_dag* dag, int64_t id, int64_t* size_bytes, int* rank,
-                      int* is_leaf);
+                      int* is_leaf, int64_t* lt);
 
 /* Figures counted by the last execute (equal to the planned figures by
  * construction of the executor; peak_exec is taken from the plan). */

@@ -29,6 +29,7 @@ class Node:
     ra: Tuple[int, ...] = ()
     parents: List[int] = dataclasses.field(default_factory=list)  # distinct, ascending
     leaf_index: int = -1    # index into the workload's leaf list
+    lt: int = 1             # batch (time-slice) extent, never contracted
 
     @property
     def is_leaf(self) -> bool:
@@ -49,9 +50,11 @@ class Dag:
         self._index: Dict[Tuple, int] = {}
 
     # -- building ---------------------------------------------------------
-    def add_leaf(self, extents, leaf_index: int = -1) -> int:
+    def add_leaf(self, extents, leaf_index: int = -1, lt: Optional[int] = None) -> int:
+        """A leaf with batch extent ``lt`` (default: the DAG's)."""
         nid = len(self.nodes)
-        self.nodes.append(Node(nid, tuple(int(e) for e in extents), leaf_index=leaf_index))
+        self.nodes.append(Node(nid, tuple(int(e) for e in extents), leaf_index=leaf_index,
+                               lt=int(lt if lt is not None else self.lt)))
         return nid
 
     def add_contraction(self, left: int, right: int, la, ra) -> int:
@@ -65,10 +68,12 @@ class Dag:
         for a, b in zip(la, ra):
             if L.extents[a] != R.extents[b]:
                 raise ValueError("paired axes differ in extent")
+        if L.lt != R.lt:
+            raise ValueError("operands differ in the batch extent")
         ext = tuple(e for i, e in enumerate(L.extents) if i not in la) + \
             tuple(e for j, e in enumerate(R.extents) if j not in ra)
         nid = len(self.nodes)
-        self.nodes.append(Node(nid, ext, left, right, la, ra))
+        self.nodes.append(Node(nid, ext, left, right, la, ra, lt=L.lt))
         for c in sorted({left, right}):
             self.nodes[c].parents.append(nid)
         self._index[key] = nid
@@ -76,8 +81,8 @@ class Dag:
 
     # -- queries ----------------------------------------------------------
     def size(self, u: int) -> int:
-        """u.size: bytes of the tensor, batch axis included."""
-        n = self.lt * self.elem_bytes
+        """u.size: bytes of the tensor, its own batch axis included."""
+        n = self.nodes[u].lt * self.elem_bytes
         for e in self.nodes[u].extents:
             n *= e
         return n
@@ -117,7 +122,7 @@ def build_from_workload(wl, elem_bytes: int = 16) -> Tuple[Dag, List[int]]:
     dag = Dag(wl.lt, elem_bytes)
     ids: List[int] = []
     for li, lf in enumerate(wl.leaves):
-        ids.append(dag.add_leaf(lf.extents, leaf_index=li))
+        ids.append(dag.add_leaf(lf.extents, leaf_index=li, lt=wl.leaf_lt(li)))
     for rq in wl.requests:
         ids.append(dag.add_contraction(ids[rq.left], ids[rq.right], rq.la, rq.ra))
     return dag, ids

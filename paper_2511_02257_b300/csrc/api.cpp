@@ -99,6 +99,14 @@ int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
   }
 }
 
+int lqc_dag_set_batch(lqc_dag* h, int64_t lt) {
+  if (!h) return LQC_ERR_ARG;
+  if (h->d.frozen) return fail(h, LQC_ERR_STATE, "DAG is frozen by lqc_dag_schedule");
+  if (lt < 1) return fail(h, LQC_ERR_ARG, "batch extent must be >= 1");
+  h->d.lt = lt;
+  return LQC_OK;
+}
+
 int lqc_dag_destroy(lqc_dag* h) {
   if (!h) return LQC_OK;
   lqc::exec_destroy(h->d);
@@ -117,6 +125,7 @@ int lqc_dag_add_leaf_tensor(lqc_dag* h, int rank, const int64_t* extents, const 
     return fail(h, LQC_ERR_ARG, "bad leaf rank/extents");
   Node n;
   n.rank = rank;
+  n.lt = g.lt;
   n.elems = 1;
   for (int i = 0; i < rank; ++i) {
     if (extents[i] < 1 || extents[i] > (int64_t)1 << 31)
@@ -154,6 +163,7 @@ int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs,
   const Node& R = g.nodes[right];
   if (L.rank == 0 || R.rank == 0)
     return fail(h, LQC_ERR_ARG, "a rank-0 correlator cannot be an operand");
+  if (L.lt != R.lt) return fail(h, LQC_ERR_ARG, "operands differ in the batch extent");
   bool usedL[LQC_MAX_RANK] = {false}, usedR[LQC_MAX_RANK] = {false};
   for (int i = 0; i < npairs; ++i) {
     if (la[i] < 0 || la[i] >= L.rank || ra[i] < 0 || ra[i] >= R.rank)
@@ -179,6 +189,7 @@ int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs,
     n.ra[i] = ra[i];
   }
   n.scale_exp = L.scale_exp + R.scale_exp;
+  n.lt = L.lt;
   n.rank = 0;
   n.elems = 1;
   for (int a = 0; a < L.rank; ++a)
@@ -296,10 +307,12 @@ int lqc_dag_num_nodes(lqc_dag* h, int64_t* n) {
   return LQC_OK;
 }
 
-int lqc_dag_node_info(lqc_dag* h, int64_t id, int64_t* size_bytes, int* rank, int* is_leaf) {
+int lqc_dag_node_info(lqc_dag* h, int64_t id, int64_t* size_bytes, int* rank, int* is_leaf,
+                      int64_t* lt) {
   if (!h) return LQC_ERR_ARG;
   if (id < 0 || id >= (int64_t)h->d.nodes.size()) return fail(h, LQC_ERR_ARG, "id out of range");
   if (size_bytes) *size_bytes = h->d.size_bytes(id);
+  if (lt) *lt = h->d.nodes[id].lt;
   if (rank) *rank = h->d.nodes[id].rank;
   if (is_leaf) *is_leaf = h->d.nodes[id].is_leaf() ? 1 : 0;
   return LQC_OK;
@@ -317,7 +330,7 @@ int lqc_dag_set_leaf_data(lqc_dag* h, int64_t id, const double* data) {
   rc = lqc::host_store_alloc(g, id, &err);
   if (rc != LQC_OK) return fail(h, rc, err);
   Node& n = g.nodes[id];
-  const int64_t cnt = g.lt * n.elems;  // complex values
+  const int64_t cnt = n.lt * n.elems;  // complex values
   if (g.prec == LQC_PREC_FP64) {
     std::memcpy(n.host, data, (size_t)cnt * 16);
   } else {

@@ -151,6 +151,8 @@ struct ExecState {
   int64_t n_results = 0;                  // rank-0 roots
   std::vector<int64_t> root_ids;          // ascending
   std::vector<int32_t> slot_of;           // node -> results slot (-1)
+  std::vector<int64_t> res_off;           // slot -> offset in complex values
+  int64_t n_result_vals = 0;              // sum of the roots' batch extents
   double* scratch = nullptr;
   int64_t scratch_bytes = 0;
   char* host_arena = nullptr;             // pinned write-back copies, placed per plan
@@ -256,6 +258,12 @@ int build_program(Dag& g) {
       x.root_ids.push_back(u);
     }
   x.n_results = (int64_t)x.root_ids.size();
+  x.res_off.assign(x.n_results, 0);
+  x.n_result_vals = 0;
+  for (int64_t k = 0; k < x.n_results; ++k) {
+    x.res_off[k] = x.n_result_vals;
+    x.n_result_vals += g.nodes[x.root_ids[k]].lt;
+  }
   Placer pl;
   int64_t scratch_need = 0, mscratch_need = 0;
   std::vector<Instr>& P = x.prog;
@@ -431,7 +439,7 @@ int build_program(Dag& g) {
         in.kind = I_CONTRACT_ALL;
         in.dst = -1;
         in.root_slot = x.slot_of[u];
-        if (!make_contract_all_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, g.lt,
+        if (!make_contract_all_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, n.lt,
                                     &ad, &err)) {
           g.err = err;
           return LQC_ERR_ARG;
@@ -441,7 +449,7 @@ int build_program(Dag& g) {
                                                   : contract_all_c64_scratch_bytes(ad));
       } else {
         in.kind = I_CONTRACT;
-        if (!make_contract_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, g.lt, &cd,
+        if (!make_contract_desc(L.rank, L.ext, R.rank, R.ext, n.npairs, n.la, n.ra, n.lt, &cd,
                                 &err)) {
           g.err = err;
           return LQC_ERR_ARG;
@@ -571,7 +579,7 @@ int build_program(Dag& g) {
   x.arena_bytes = pl.top;
   if (x.arena_bytes > 0) CK(cudaMalloc((void**)&x.arena, (size_t)x.arena_bytes), "arena cudaMalloc");
   if (x.n_results > 0)
-    CK(cudaMalloc((void**)&x.results, (size_t)(x.n_results * g.lt * 16)), "results cudaMalloc");
+    CK(cudaMalloc((void**)&x.results, (size_t)(x.n_result_vals * 16)), "results cudaMalloc");
   x.scratch_bytes = scratch_need;
   if (scratch_need > 0) CK(cudaMalloc((void**)&x.scratch, (size_t)scratch_need), "scratch cudaMalloc");
   x.mscratch_bytes = mscratch_need;
@@ -608,7 +616,7 @@ int build_program(Dag& g) {
                                    reinterpret_cast<float*>(x.arena + in.dst), x.wscratch + so});
           } else {
             roots.push_back(GroupRoot{
-                &x.adesc[m], operand(in, 0), operand(in, 1), x.results + 2 * g.lt * in.root_slot,
+                &x.adesc[m], operand(in, 0), operand(in, 1), x.results + 2 * x.res_off[in.root_slot],
                 reinterpret_cast<double*>(x.wscratch + so),
                 std::ldexp(1.0, g.nodes[nn.left].scale_exp + g.nodes[nn.right].scale_exp)});
           }
@@ -725,13 +733,13 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
           const ContractAllDesc& d = x.adesc[j];
           if (mixed)
             nk = launch_contract_all_c64(d, (const float*)op[0], (const float*)op[1],
-                                         x.results + 2 * g.lt * in.root_slot, x.scratch,
+                                         x.results + 2 * x.res_off[in.root_slot], x.scratch,
                                          std::ldexp(1.0, g.nodes[n.left].scale_exp +
                                                              g.nodes[n.right].scale_exp),
                                          s);
           else
             nk = launch_contract_all_fp64(d, (const double*)op[0], (const double*)op[1],
-                                          x.results + 2 * g.lt * in.root_slot, x.scratch, s);
+                                          x.results + 2 * x.res_off[in.root_slot], x.scratch, s);
           x.flops += 8 * d.lt * d.S;
         }
         if (nk == -2) {
@@ -769,7 +777,7 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
 int host_store_alloc(Dag& g, int64_t leaf, std::string* err) {
   Node& n = g.nodes[leaf];
   if (n.host) return LQC_OK;
-  const size_t bytes = (size_t)(g.lt * n.elems * g.elem_bytes);
+  const size_t bytes = (size_t)(n.lt * n.elems * g.elem_bytes);
   void* p = nullptr;
   if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) == cudaSuccess) {
     n.host = p;
@@ -990,7 +998,7 @@ int exec_read(Dag& g, int64_t root, double* out) {
   }
   int rc = exec_wait(g, 60000);
   if (rc != LQC_OK) return rc;
-  CK(cudaMemcpy(out, x.results + 2 * g.lt * x.slot_of[root], (size_t)(g.lt * 16),
+  CK(cudaMemcpy(out, x.results + 2 * x.res_off[x.slot_of[root]], (size_t)(g.nodes[root].lt * 16),
                 cudaMemcpyDeviceToHost),
      "read correlator");
   return LQC_OK;
@@ -1002,14 +1010,14 @@ int exec_read_all(Dag& g, double* out, int64_t cap) {
     return LQC_ERR_STATE;
   }
   ExecState& x = *g.ex;
-  if (cap < x.n_results * 2 * g.lt) {
+  if (cap < x.n_result_vals * 2) {
     g.err = "output capacity too small";
     return LQC_ERR_ARG;
   }
   int rc = exec_wait(g, 60000);
   if (rc != LQC_OK) return rc;
   if (x.n_results > 0)
-    CK(cudaMemcpy(out, x.results, (size_t)(x.n_results * g.lt * 16), cudaMemcpyDeviceToHost),
+    CK(cudaMemcpy(out, x.results, (size_t)(x.n_result_vals * 16), cudaMemcpyDeviceToHost),
        "read correlators");
   return LQC_OK;
 }

@@ -18,6 +18,7 @@ struct Node {
   int rank = 0;
   int64_t ext[LQC_MAX_RANK] = {0};
   int64_t elems = 1;            // per time slice
+  int64_t lt = 1;               // batch (time-slice) extent, never contracted
   int64_t left = -1, right = -1;
   int npairs = 0;
   int la[LQC_MAX_RANK] = {0}, ra[LQC_MAX_RANK] = {0};
@@ -50,7 +51,7 @@ struct KeyHash {
 struct ExecState;  // device-side state (exec.cu)
 
 struct Dag {
-  int64_t lt = 1;
+  int64_t lt = 1;               // batch extent given to leaves added next
   lqc_precision prec = LQC_PREC_FP64;
   int elem_bytes = 16;
   std::vector<Node> nodes;
@@ -71,7 +72,7 @@ struct Dag {
   bool executed = false;
   std::string err;
 
-  int64_t size_bytes(int64_t u) const { return lt * nodes[u].elems * elem_bytes; }
+  int64_t size_bytes(int64_t u) const { return nodes[u].lt * nodes[u].elems * elem_bytes; }
   NodeType type(int64_t u) const {
     const Node& n = nodes[u];
     if (n.is_leaf()) return LEAF;

@@ -19,6 +19,15 @@ naive order.
          [--precision tf32x3|bf16x3|fp64] [--reps 20]
 
 times one contraction shape through the single-contraction C ABI.
+
+  python -m paper_2511_02257_b300.experiments batched [--steps 2]
+
+runs the batched workload (50 independent DAGs of uneven N and Lt, ~18k
+contractions) in the mixed-precision grouped form (windows of independent
+contractions per launch, CUDA graphs) and as one launch per contraction in
+FP64, with the leaves resident on the device and from pinned host memory;
+reports times, speedups and the TF32x3 error of every correlator against
+the FP64 path (whose parity with the oracle the test suite establishes).
 """
 from __future__ import annotations
 
@@ -112,9 +121,109 @@ def kernel_bench(argv):
                       "algorithmic_gbs": alg_bytes / ms / 1e6}), flush=True)
 
 
+def _gen_leaves(wl):
+    import synth
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda li: synth.leaf_data(wl, li), range(len(wl.leaves))))
+
+
+def _time_arm(nd, stream, steps, staged):
+    """Best-of-`steps` wall time of execute + read of every correlator."""
+    import torch
+    if staged:
+        nd.stage_leaves(stream)
+    nd.execute(stream)                 # warm-up (graph capture, arena allocation)
+    vals = nd.read_all_correlators()
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        nd.execute(stream)
+        nd.read_all_correlators(vals)
+        times.append(time.perf_counter() - t1)
+    if staged:
+        nd.unstage_leaves()
+    return min(times), vals.copy(), nd.exec_info()
+
+
+def batched_bench(argv):
+    """Mixed grouped form vs one FP64 launch per contraction on the batched
+    workload; see the module docstring."""
+    import torch
+    import paper_2511_02257_b300 as L
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--window", type=int, default=64)
+    ap.add_argument("--policy", default="tree")
+    args = ap.parse_args(argv)
+    wl = synth.make_workload(args.workload)
+    t0 = time.perf_counter()
+    leaves = _gen_leaves(wl)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {}
+    rows = []
+    arms = [("tf32x3", args.window, 1), ("tf32x3", 0, 1), ("tf32x3", 0, 0), ("fp64", 0, 1)]
+    for prec, window, graph in arms:
+        nd, _ = L.build_dag(wl, precision=prec, leaf_data_fn=lambda li: leaves[li])
+        planned = nd.schedule(args.policy, "lru", wl.budget_bytes)
+        nd.set_option(L.LQC_OPT_CUDA_GRAPH, graph)
+        nd.set_option(L.LQC_OPT_WINDOW, window)
+        for staged in (True, False):
+            t, vals, info = _time_arm(nd, stream, args.steps, staged)
+            row = {"workload": args.workload, "precision": prec, "window": window,
+                   "cuda_graph": bool(graph), "leaves": "device" if staged else "pinned host",
+                   "contractions": len(nd.order()), "time_to_solution_s": t,
+                   "tflops": info["flops"] / t / 1e12, "kernels": info["n_kernels"],
+                   "peak_paper_gib": planned["peak_paper"] / 2 ** 30,
+                   "peak_exec_gib": planned["peak_exec"] / 2 ** 30,
+                   "budget_gib": wl.budget_bytes / 2 ** 30, "n_evict": planned["n_evict"],
+                   "h2d_gib": 0.0 if staged else planned["h2d_bytes"] / 2 ** 30}
+            rows.append(row)
+            res[(prec, window, graph, staged)] = (t, vals)
+            print(json.dumps(row), flush=True)
+        nd.close()
+        del nd
+        torch.cuda.empty_cache()
+    nd, _ = L.build_dag(wl, with_data=False)
+    roots = nd.roots()
+    lts = [nd.node_info(r)["lt"] for r in roots]
+    offs = np.concatenate([[0], np.cumsum(lts)])
+    ref64 = res[("fp64", 0, 1, True)][1]
+    mixed = res[("tf32x3", args.window, 1, True)][1]
+
+    def per_root(v, ref):
+        return np.array([np.linalg.norm(v[offs[i]:offs[i + 1]] - ref[offs[i]:offs[i + 1]]) /
+                         np.linalg.norm(ref[offs[i]:offs[i + 1]]) for i in range(len(roots))])
+    e_mixed = per_root(mixed, ref64)
+    same = all(np.array_equal(res[("tf32x3", args.window, 1, s)][1].view(np.float64),
+                              res[("tf32x3", w, g, s2)][1].view(np.float64))
+               for s in (True,) for (w, g, s2) in ((0, 1, True), (0, 0, True),
+                                                   (args.window, 1, False)))
+    t64 = res[("fp64", 0, 1, True)][0]
+    summary = {
+        "summary": args.workload, "roots": len(roots), "leaf_generation_s": t_gen,
+        "speedup_grouped_tf32x3_vs_fp64": t64 / res[("tf32x3", args.window, 1, True)][0],
+        "speedup_grouped_tf32x3_vs_fp64_host_leaves":
+            res[("fp64", 0, 1, False)][0] / res[("tf32x3", args.window, 1, False)][0],
+        "speedup_grouping_vs_single_launches_tf32x3":
+            res[("tf32x3", 0, 1, True)][0] / res[("tf32x3", args.window, 1, True)][0],
+        "speedup_grouping_graph_vs_single_launches_no_graph_tf32x3":
+            res[("tf32x3", 0, 0, True)][0] / res[("tf32x3", args.window, 1, True)][0],
+        "tf32x3_err_vs_fp64_max": float(e_mixed.max()),
+        "tf32x3_err_vs_fp64_median": float(np.median(e_mixed)),
+        "tf32x3_forms_bit_identical": bool(same),
+    }
+    print(json.dumps(summary), flush=True)
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         return kernel_bench(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "batched":
+        return batched_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

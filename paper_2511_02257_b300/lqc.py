@@ -69,6 +69,7 @@ def _sig(name, res, args):
 
 _sig("lqc_dag_create", ctypes.c_int, [ctypes.POINTER(c_vp), c_i64, ctypes.c_int])
 _sig("lqc_dag_destroy", ctypes.c_int, [c_vp])
+_sig("lqc_dag_set_batch", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_add_leaf_tensor", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, P_dbl, P_i64])
 _sig("lqc_dag_set_leaf_data", ctypes.c_int, [c_vp, c_i64, P_dbl])
 _sig("lqc_dag_add_contraction", ctypes.c_int, [c_vp, c_i64, c_i64, ctypes.c_int, P_int, P_int, P_i64])
@@ -87,7 +88,7 @@ _sig("lqc_dag_read_correlator", ctypes.c_int, [c_vp, c_i64, P_dbl])
 _sig("lqc_dag_read_all_correlators", ctypes.c_int, [c_vp, P_dbl, c_i64])
 _sig("lqc_dag_get_roots", ctypes.c_int, [c_vp, P_i64, c_i64, P_i64])
 _sig("lqc_dag_num_nodes", ctypes.c_int, [c_vp, P_i64])
-_sig("lqc_dag_node_info", ctypes.c_int, [c_vp, c_i64, P_i64, P_int, P_int])
+_sig("lqc_dag_node_info", ctypes.c_int, [c_vp, c_i64, P_i64, P_int, P_int, P_i64])
 _sig("lqc_dag_get_stats", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_stats)])
 _sig("lqc_dag_get_exec_info", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_exec_info)])
 _sig("lqc_last_error", ctypes.c_char_p, [c_vp])
@@ -111,7 +112,7 @@ _sig("lqc_contract_all_c64_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c
                                                    ctypes.c_int, P_int, P_int, c_i64])
 
 # re-export the raw entry points under their C names
-for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
+for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
            "lqc_dag_add_contraction", "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
            "lqc_dag_get_plan", "lqc_dag_set_option", "lqc_dag_stage_leaves",
            "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_read_correlator",
@@ -158,8 +159,9 @@ class Dag:
         if rc != LQC_OK:
             raise LqcError(rc, "lqc_dag_create")
         self.h = h
-        self.lt = int(lt)
+        self.lt = int(lt)          # batch extent of the leaves registered next
         self.precision = precision
+        self._root_lts = None      # (num_nodes, roots, their batch extents)
 
     def close(self):
         if getattr(self, "h", None):
@@ -178,7 +180,16 @@ class Dag:
             raise LqcError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
 
     # -- building
-    def add_leaf(self, extents: Sequence[int], data: Optional[np.ndarray] = None) -> int:
+    def set_batch(self, lt: int):
+        """Batch extent of the leaves registered next (independent problems
+        with different time extents in one DAG)."""
+        self._check(_lib.lqc_dag_set_batch(self.h, int(lt)), "set_batch")
+        self.lt = int(lt)
+
+    def add_leaf(self, extents: Sequence[int], data: Optional[np.ndarray] = None,
+                 lt: Optional[int] = None) -> int:
+        if lt is not None and int(lt) != self.lt:
+            self.set_batch(lt)
         ext, pe = _i64arr(list(extents) or [0])
         nid = c_i64()
         pd = None
@@ -264,16 +275,28 @@ class Dag:
                                            ctypes.byref(n)), "get_roots")
         return out[:n.value].tolist()
 
+    def _roots_and_lts(self):
+        nn = self.num_nodes()
+        if self._root_lts is None or self._root_lts[0] != nn:
+            roots = self.roots()
+            self._root_lts = (nn, roots, [self.node_info(r)["lt"] for r in roots])
+        return self._root_lts[1], self._root_lts[2]
+
     def read_correlator(self, root: int) -> np.ndarray:
-        out = np.zeros(2 * self.lt, dtype=np.float64)
+        out = np.zeros(2 * self.node_info(root)["lt"], dtype=np.float64)
         self._check(_lib.lqc_dag_read_correlator(self.h, int(root), out.ctypes.data_as(P_dbl)),
                     "read_correlator")
         return out.view(np.complex128)
 
     def read_all_correlators(self, out: Optional[np.ndarray] = None) -> np.ndarray:
-        nr = len(self.roots())
+        """[n_roots][lt] when all roots share one batch extent, else the
+        roots' correlators concatenated in ascending root id (1-D)."""
+        roots, lts = self._roots_and_lts()
         if out is None:
-            out = np.zeros((nr, self.lt), dtype=np.complex128)
+            if len(set(lts)) <= 1:
+                out = np.zeros((len(roots), lts[0] if lts else self.lt), dtype=np.complex128)
+            else:
+                out = np.zeros(int(sum(lts)), dtype=np.complex128)
         self._check(_lib.lqc_dag_read_all_correlators(self.h, out.view(np.float64).ctypes.data_as(P_dbl),
                                                       out.size * 2), "read_all_correlators")
         return out
@@ -284,10 +307,10 @@ class Dag:
         return n.value
 
     def node_info(self, nid: int):
-        sz, rk, lf = c_i64(), ctypes.c_int(), ctypes.c_int()
+        sz, rk, lf, lt = c_i64(), ctypes.c_int(), ctypes.c_int(), c_i64()
         self._check(_lib.lqc_dag_node_info(self.h, int(nid), ctypes.byref(sz), ctypes.byref(rk),
-                                           ctypes.byref(lf)), "node_info")
-        return {"size": sz.value, "rank": rk.value, "is_leaf": bool(lf.value)}
+                                           ctypes.byref(lf), ctypes.byref(lt)), "node_info")
+        return {"size": sz.value, "rank": rk.value, "is_leaf": bool(lf.value), "lt": lt.value}
 
     def stats(self) -> dict:
         st = lqc_stats()
@@ -322,7 +345,7 @@ def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=
         data = None
         if with_data:
             data = leaf_data_fn(li) if leaf_data_fn else None
-        ids.append(d.add_leaf(lf.extents, data))
+        ids.append(d.add_leaf(lf.extents, data, lt=wl.leaf_lt(li)))
     for rq in wl.requests:
         ids.append(d.add_contraction(ids[rq.left], ids[rq.right], rq.la, rq.ra))
     return d, ids

@@ -8,5 +8,6 @@ anything.  Both the CUDA path (through the C ABI) and the CPU oracle consume
 the same description, each with its own DAG builder.
 """
 from .workloads import (  # noqa: F401
-    Leaf, Request, Workload, CONFIGS, make_workload, leaf_data, ring_requests,
+    Leaf, Request, Workload, CONFIGS, BATCHED, BatchedRecipe, make_workload, leaf_data,
+    ring_requests,
 )

@@ -42,6 +42,8 @@ class Leaf:
     kind: str                 # 'M', 'P' or 'B'
     extents: Tuple[int, ...]  # per-time-slice extents (Lt excluded)
     seed: int                 # data seed (see leaf_data)
+    lt: int = 0               # batch extent; 0 = the workload's Lt
+    nvec: int = 0             # distillation size; 0 = the workload's N
 
 
 @dataclasses.dataclass(frozen=True)
@@ -81,13 +83,21 @@ class Workload:
     def roots(self) -> List[int]:
         return [r for f in self.functions for r in f]
 
+    def leaf_lt(self, li: int) -> int:
+        """Batch extent of leaf ``li`` (independent problems of a batched
+        workload have their own)."""
+        return self.leaves[li].lt or self.lt
+
+    def leaf_nvec(self, li: int) -> int:
+        return self.leaves[li].nvec or self.nvec
+
 
 def leaf_data(wl: Workload, leaf_index: int, dtype=np.complex128) -> np.ndarray:
     """Dense leaf tensor ``[Lt][extents...]`` drawn from its own PCG64 stream."""
     lf = wl.leaves[leaf_index]
     rng = np.random.Generator(np.random.PCG64([wl.seed, 7919, lf.seed]))
-    shape = (wl.lt,) + tuple(lf.extents)
-    sd = np.sqrt(1.0 / (2.0 * wl.nvec))
+    shape = (wl.leaf_lt(leaf_index),) + tuple(lf.extents)
+    sd = np.sqrt(1.0 / (2.0 * wl.leaf_nvec(leaf_index)))
     re = rng.standard_normal(shape)
     im = rng.standard_normal(shape)
     out = np.empty(shape, dtype=np.complex128)
@@ -269,8 +279,64 @@ def _meson_function(rng, rc: Recipe, pools, prefixes):
     return kinds, seq
 
 
+@dataclasses.dataclass(frozen=True)
+class BatchedRecipe:
+    """Many independent correlation-function DAGs of uneven shape in one
+    request stream: each part draws its distillation size N and its batch
+    extent Lt, then follows the multi-meson recipe at that size (propagator
+    leaves only where N <= max_n_spin, which keeps the largest products
+    P x P at N = 64 instead of 4N = 1024 rows per slice)."""
+    name: str = "batched"
+    n_dags: int = 50
+    nvecs: Tuple[int, ...] = (32, 48, 64, 96, 128, 192, 256)
+    lts: Tuple[int, ...] = (16, 32, 64, 128)
+    n_functions: int = 40          # per part: ~400 contractions
+    pool_m: int = 8
+    pool_p: int = 3
+    p_spin: float = 0.25
+    max_n_spin: int = 64
+    budget_bytes: int = 48 * GIB
+
+
+BATCHED = {"batched": BatchedRecipe()}
+
+
+def _make_batched(rc: BatchedRecipe, seed: int) -> Workload:
+    rng = np.random.Generator(np.random.PCG64([seed, 130363]))
+    leaves: List[Leaf] = []
+    parts = []
+    for d in range(rc.n_dags):
+        n = int(rc.nvecs[int(rng.integers(len(rc.nvecs)))])
+        lt = int(rc.lts[int(rng.integers(len(rc.lts)))])
+        spin = n <= rc.max_n_spin
+        sub = make_workload("multi_meson", seed=int(rng.integers(1 << 31)), lt=lt, nvec=n,
+                            n_functions=rc.n_functions, pool_m=rc.pool_m,
+                            pool_p=rc.pool_p if spin else 0, p_spin=rc.p_spin if spin else 0.0,
+                            prefix_pool=rc.n_functions // 3)
+        parts.append((len(leaves), sub))
+        for lf in sub.leaves:
+            leaves.append(Leaf(lf.kind, lf.extents, len(leaves), lt, n))
+    requests: List[Request] = []
+    functions: List[List[int]] = []
+    n_leaves = len(leaves)
+    for loff, sub in parts:
+        roff = n_leaves + len(requests)
+
+        def remap(i, loff=loff, roff=roff, sl=sub.n_leaves):
+            return loff + i if i < sl else roff + (i - sl)
+        for rq in sub.requests:
+            requests.append(Request(remap(rq.left), remap(rq.right), rq.la, rq.ra))
+        functions.extend([[remap(r) for r in f] for f in sub.functions])
+    return Workload(name=rc.name, lt=leaves[0].lt, nvec=max(lf.nvec for lf in leaves),
+                    leaves=leaves, requests=requests, functions=functions,
+                    budget_bytes=rc.budget_bytes, seed=seed)
+
+
 def make_workload(name: str, seed: int = 0, **overrides) -> Workload:
-    """Build the request stream of a named workload (see CONFIGS)."""
+    """Build the request stream of a named workload (see CONFIGS, BATCHED)."""
+    if name in BATCHED:
+        brc = dataclasses.replace(BATCHED[name], **overrides) if overrides else BATCHED[name]
+        return _make_batched(brc, seed)
     rc = dataclasses.replace(CONFIGS[name], **overrides) if overrides else CONFIGS[name]
     rng = np.random.Generator(np.random.PCG64([seed, 104729]))
     n = rc.nvec

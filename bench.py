@@ -19,6 +19,7 @@ host's cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import os
 import statistics
@@ -35,19 +36,6 @@ sys.path.insert(0, HERE)
 # DRAM bytes per launch of the dominant kernel from one ncu capture (None
 # until captured for the current kernel build; see profiles/).
 TRAFFIC_PER_LAUNCH = None
-FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 rate, nominal
-# dense tensor rates relative to BF16 (nominal B300 figures: TF32 1.1 and
-# BF16 2.25 PFLOP/s), applied to the measured BF16 GEMM peak
-TENSOR_RATIO = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}
-
-
-def measured_peaks():
-    try:
-        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except (OSError, ValueError):
-        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, \
-            "fallback"
 
 
 def parse():
@@ -135,10 +123,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _blas_all_cores():
+    """Context in which the oracle's BLAS pool spans every host core
+    (threadpoolctl where installed; otherwise the BLAS default, which is
+    one thread per core unless the environment limits it)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(limits=os.cpu_count(), user_api="blas")
+    except ImportError:
+        return contextlib.nullcontext()
+
+
 def blas_threads():
-    """Threads of the BLAS pool the oracle runs on (all host cores)."""
-    from threadpoolctl import threadpool_info, threadpool_limits
-    with threadpool_limits(limits=os.cpu_count(), user_api="blas"):
+    """Threads of the BLAS pool the oracle runs on."""
+    try:
+        from threadpoolctl import threadpool_info
+    except ImportError:
+        env = [os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")]
+        env = [int(v) for v in env if v and v.isdigit()]
+        return env[0] if env else len(os.sched_getaffinity(0))
+    with _blas_all_cores():
         n = [p.get("num_threads", 0) for p in threadpool_info() if p.get("user_api") == "blas"]
     return max(n) if n else 1
 
@@ -156,8 +160,7 @@ def oracle_sample(wl, seconds, rng_seed=0):
     """Time the CPU oracle on a random subset of correlation functions
     (their descendant closures), sized to about ``seconds`` of work, with
     the BLAS thread pool spanning every host core."""
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(limits=os.cpu_count(), user_api="blas"):
+    with _blas_all_cores():
         return _oracle_sample(wl, seconds, rng_seed)
 
 
@@ -387,6 +390,12 @@ def main():
                "sample": "%d of %d correlator trees (random, seeded) with their descendant "
                          "closures, %.2f GFLOP in %.1f s" % (nr, nt, f / 1e9, t)}
 
+    from paper_2511_02257_b300.roofline import (FP64_NOMINAL_TFLOPS, TENSOR_RATIO,
+                                                 dag_roofline_for, measured_peaks)
+    droof = dag_roofline_for(wl, ids, args.precision, ms / args.steps / 1e3)
+    if pform:
+        pform["dag_roofline"] = dag_roofline_for(wl, ids, args.compare,
+                                                 pform["time_to_solution_s"])
     if args.precision == "fp64":
         roofline = {"kernel": "k_contract_fp64", "bound": "alu", "achieved": achieved,
                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -435,6 +444,7 @@ def main():
             "schedule_ms": 1e3 * t_sched, "dag_build_s": t_build,
             "roofline": roofline,
             "kernel_ms_by_shape": breakdown,
+            "dag_roofline": droof,
             "precision_form": pform,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -166,8 +166,9 @@ def batched_bench(argv):
     res = {}
     rows = []
     arms = [("tf32x3", args.window, 1), ("tf32x3", 0, 1), ("tf32x3", 0, 0), ("fp64", 0, 1)]
+    from paper_2511_02257_b300.roofline import dag_roofline_for
     for prec, window, graph in arms:
-        nd, _ = L.build_dag(wl, precision=prec, leaf_data_fn=lambda li: leaves[li])
+        nd, ids = L.build_dag(wl, precision=prec, leaf_data_fn=lambda li: leaves[li])
         planned = nd.schedule(args.policy, "lru", wl.budget_bytes)
         nd.set_option(L.LQC_OPT_CUDA_GRAPH, graph)
         nd.set_option(L.LQC_OPT_WINDOW, window)
@@ -180,7 +181,8 @@ def batched_bench(argv):
                    "peak_paper_gib": planned["peak_paper"] / 2 ** 30,
                    "peak_exec_gib": planned["peak_exec"] / 2 ** 30,
                    "budget_gib": wl.budget_bytes / 2 ** 30, "n_evict": planned["n_evict"],
-                   "h2d_gib": 0.0 if staged else planned["h2d_bytes"] / 2 ** 30}
+                   "h2d_gib": 0.0 if staged else planned["h2d_bytes"] / 2 ** 30,
+                   "dag_roofline": dag_roofline_for(wl, ids, prec, t) if staged else None}
             rows.append(row)
             res[(prec, window, graph, staged)] = (t, vals)
             print(json.dumps(row), flush=True)

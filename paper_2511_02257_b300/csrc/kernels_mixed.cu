@@ -650,27 +650,127 @@ __device__ __forceinline__ void df_acc_prod(float& sh, float& sl, float a, float
   sh = t;
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
-// partial sum of block c of slice t of one correlator (fixed reduction order)
+// ------------------------------------------------------------ permute
+// A PermDesc maps every element e of a destination order (row-major over its
+// axes) to a source offset.  Two block shapes move it with coalesced reads
+// and writes, and serve both the reorder copies and the correlator sums
+// (which multiply instead of storing, so a partner is never copied):
+//  * runs (mode 0): the destination's innermost axis X is unit-stride in the
+//    source too.  A block takes kPermElems consecutive destination elements;
+//    the source offsets of the runs it touches are computed once into
+//    shared memory (32-bit index arithmetic: slices below 2^31 elements).
+//  * tiles (mode 1): the source's unit-stride axis Y is another axis.  A
+//    block takes kPermTiles 32x32 tiles (X by Y) of one outer index, all
+//    loaded along Y before one barrier, then used along X.
+constexpr int kPermElems = 2048;
+constexpr int kPermTiles = 4;
+constexpr int kPermSmem = kPermTiles * 32 * 33 * 8;  // >= (kPermElems + 1) * 4
+
+// source and destination offsets of outer index o (row-major digits)
+__device__ __forceinline__ unsigned perm_outer(const PermDesc& d, unsigned o, unsigned* dso) {
+  unsigned so = 0, ds = 0;
+#pragma unroll
+  for (int a = LQC_MAX_RANK - 1; a >= 0; --a) {
+    if (a < d.nout) {
+      const unsigned e = (unsigned)d.oext[a];
+      const unsigned q = o / e;
+      const unsigned r = o - q * e;
+      so += r * (unsigned)d.osrc[a];
+      ds += r * (unsigned)d.odst[a];
+      o = q;
+    }
+  }
+  *dso = ds;
+  return so;
+}
+
+// calls op(e, src value) for the elements of block b (one slice)
+template <typename Op>
+__device__ __forceinline__ void perm_visit(const PermDesc& d, const float2* __restrict__ src,
+                                           unsigned b, unsigned char* smem, Op op) {
+  if (d.mode == 0) {
+    unsigned* so_tab = reinterpret_cast<unsigned*>(smem);
+    const unsigned X = (unsigned)d.X;
+    const unsigned e0 = b * kPermElems;
+    const unsigned e1 = min(e0 + (unsigned)kPermElems, (unsigned)d.n);
+    const unsigned r0 = e0 / X, r1 = (e1 - 1) / X;
+    unsigned dummy;
+    for (unsigned r = r0 + threadIdx.x; r <= r1; r += blockDim.x)
+      so_tab[r - r0] = perm_outer(d, r, &dummy);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPermElems / 256; ++j) {
+      const unsigned e = e0 + j * 256 + threadIdx.x;
+      if (e < e1) {
+        const unsigned r = e / X;
+        op(e, src[so_tab[r - r0] + (e - r * X)]);
+      }
+    }
+    return;
+  }
+  float2 (*tile)[32][33] = reinterpret_cast<float2 (*)[32][33]>(smem);
+  const unsigned xb = ((unsigned)d.X + 31) / 32;
+  const unsigned ygb = (((unsigned)d.Y + 31) / 32 + kPermTiles - 1) / kPermTiles;
+  const unsigned o = b / (xb * ygb), rem = b - o * (xb * ygb);
+  const unsigned x0 = (rem % xb) * 32, yg = rem / xb;
+  unsigned dso;
+  const unsigned so = perm_outer(d, o, &dso);
+  const unsigned tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const unsigned sX = (unsigned)d.sX, dY = (unsigned)d.dY;
+#pragma unroll
+  for (int q = 0; q < kPermTiles; ++q) {  // along the source's unit-stride axis Y
+    const unsigned y = (yg * kPermTiles + q) * 32 + tx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned x = x0 + ty + 8 * j;
+      if (y < (unsigned)d.Y && x < (unsigned)d.X) tile[q][ty + 8 * j][tx] = src[so + y + x * sX];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kPermTiles; ++q) {  // along the destination's unit-stride axis X
+    const unsigned x = x0 + tx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned y = (yg * kPermTiles + q) * 32 + ty + 8 * j;
+      if (y < (unsigned)d.Y && x < (unsigned)d.X) op(dso + y * dY + x, tile[q][tx][ty + 8 * j]);
+    }
+  }
+}
+
+__device__ __forceinline__ void permute_block(const PermDesc& d, const float2* __restrict__ src,
+                                              float2* __restrict__ dst, int t, long long b) {
+  __shared__ __align__(16) unsigned char smem[kPermSmem];
+  src += (long long)t * d.src_ts;
+  dst += (long long)t * d.n;
+  perm_visit(d, src, (unsigned)b, smem, [&](unsigned e, float2 v) { dst[e] = v; });
+}
+
+__global__ void __launch_bounds__(256)
+k_permute_c64(const float2* __restrict__ src, float2* __restrict__ dst, const PermDesc d) {
+  permute_block(d, src, dst, blockIdx.y, blockIdx.x);
+}
+
+// partial sum of block b of slice t of one correlator, r(t) = sum_e A[e] *
+// B[src(e)] with the destination order of `d` = the left operand's order;
+// fixed reduction order, so every launch form gives the same bits
 __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
                                                  const float2* __restrict__ B,
-                                                 double2* __restrict__ part,
-                                                 const ContractAllDesc& p, long long t, int c) {
-  const unsigned S = (unsigned)p.S;
-  const unsigned lo = (unsigned)(((unsigned long long)S * c) / p.chunks);
-  const unsigned hi = (unsigned)(((unsigned long long)S * (c + 1)) / p.chunks);
-  A += t * p.S;
-  B += t * p.S;
+                                                 double2* __restrict__ part, const PermDesc& d,
+                                                 long long t, unsigned b) {
+  __shared__ __align__(16) unsigned char smem[kPermSmem];
+  A += t * d.n;
+  B += t * d.src_ts;
   // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
   // ~44 significant bits) at FP32 throughput; across threads and blocks: FP64
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  for (unsigned i = lo + threadIdx.x; i < hi; i += 256) {
-    const float2 a = A[i];
-    const float2 b = B[goff(p.bp, i)];
-    df_acc_prod(rh, rl, a.x, b.x);
-    df_acc_prod(rh, rl, -a.y, b.y);
-    df_acc_prod(ih, il, a.x, b.y);
-    df_acc_prod(ih, il, a.y, b.x);
-  }
+  perm_visit(d, B, b, smem, [&](unsigned e, float2 bv) {
+    const float2 a = A[e];
+    df_acc_prod(rh, rl, a.x, bv.x);
+    df_acc_prod(rh, rl, -a.y, bv.y);
+    df_acc_prod(ih, il, a.x, bv.y);
+    df_acc_prod(ih, il, a.y, bv.x);
+  });
   double re = (double)rh + (double)rl, im = (double)ih + (double)il;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -683,14 +783,14 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
   if (threadIdx.x == 0) {
     double2 s = w[0];
     for (int k = 1; k < 8; ++k) { s.x += w[k].x; s.y += w[k].y; }
-    part[t * p.chunks + c] = s;
+    part[t * d.blocks + b] = s;
   }
 }
 
 __global__ void __launch_bounds__(256)
 k_contract_all_c64(const float2* __restrict__ A, const float2* __restrict__ B,
-                   double2* __restrict__ part, const ContractAllDesc p) {
-  ca_partial_block(A, B, part, p, blockIdx.y, blockIdx.x);
+                   double2* __restrict__ part, const PermDesc d) {
+  ca_partial_block(A, B, part, d, blockIdx.y, blockIdx.x);
 }
 
 __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
@@ -705,64 +805,6 @@ __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
     s.y += v.y;
   }
   C[t] = make_double2(s.x * scale, s.y * scale);
-}
-
-// ------------------------------------------------------------ permute
-// outer offsets of outer index o (row-major digits)
-__device__ __forceinline__ void perm_outer(const PermDesc& d, long long o, long long& so,
-                                           long long& dso) {
-  so = 0;
-  dso = 0;
-#pragma unroll
-  for (int a = LQC_MAX_RANK - 1; a >= 0; --a) {
-    if (a < d.nout) {
-      const long long e = d.oext[a];
-      const long long q = o / e;
-      const long long r = o - q * e;
-      so += r * d.osrc[a];
-      dso += r * d.odst[a];
-      o = q;
-    }
-  }
-}
-
-// block b of slice t
-__device__ __forceinline__ void permute_block(const PermDesc& d, const float2* __restrict__ src,
-                                              float2* __restrict__ dst, int t, long long b) {
-  src += (long long)t * d.src_ts;
-  dst += (long long)t * d.n;
-  if (d.mode == 0) {
-    const int xb = (d.X + 255) / 256;
-    const long long o = b / xb;
-    const int x = (int)(b % xb) * 256 + threadIdx.x;
-    long long so, dso;
-    perm_outer(d, o, so, dso);
-    if (x < d.X) dst[dso + x] = src[so + x];
-    return;
-  }
-  __shared__ float2 tile[32][33];
-  const int xb = (d.X + 31) / 32, yb = (d.Y + 31) / 32;
-  const long long o = b / ((long long)xb * yb);
-  const int x0 = (int)(b % xb) * 32, y0 = (int)((b / xb) % yb) * 32;
-  long long so, dso;
-  perm_outer(d, o, so, dso);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {  // read along the source's unit-stride axis Y
-    const int y = y0 + tx, x = x0 + ty + 8 * j;
-    if (y < d.Y && x < d.X) tile[ty + 8 * j][tx] = src[so + y + (long long)x * d.sX];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {  // write along the destination's unit-stride axis X
-    const int x = x0 + tx, y = y0 + ty + 8 * j;
-    if (y < d.Y && x < d.X) dst[dso + (long long)y * d.dY + x] = tile[tx][ty + 8 * j];
-  }
-}
-
-__global__ void __launch_bounds__(256)
-k_permute_c64(const float2* __restrict__ src, float2* __restrict__ dst, const PermDesc d) {
-  permute_block(d, src, dst, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------ grouped
@@ -781,10 +823,10 @@ struct PackTask {
 
 struct CATask {
   const float2* A;
-  const float2* B;       // the (reordered, if needed) right operand
+  const float2* B;
   double2* out;
   double2* part;
-  ContractAllDesc d;
+  PermDesc d;            // B in A's order; d.blocks partial sums per slice
   double scale;
   long long block_start, t_start;
 };
@@ -844,7 +886,8 @@ __global__ void __launch_bounds__(256)
 k_contract_all_grouped(const CATask* __restrict__ tasks, int n) {
   const CATask& tk = tasks[find_task(tasks, n, blockIdx.x)];
   const long long local = blockIdx.x - tk.block_start;
-  ca_partial_block(tk.A, tk.B, tk.part, tk.d, local / tk.d.chunks, (int)(local % tk.d.chunks));
+  ca_partial_block(tk.A, tk.B, tk.part, tk.d, local / tk.d.blocks,
+                   (unsigned)(local % tk.d.blocks));
 }
 
 __global__ void k_contract_all_final_grouped(const CATask* __restrict__ tasks, int n,
@@ -860,8 +903,8 @@ __global__ void k_contract_all_final_grouped(const CATask* __restrict__ tasks, i
   const CATask& tk = tasks[lo];
   const long long t = g - tk.t_start;
   double2 s = make_double2(0.0, 0.0);
-  for (int c = 0; c < tk.d.chunks; ++c) {
-    const double2 v = tk.part[t * tk.d.chunks + c];
+  for (long long c = 0; c < tk.d.blocks; ++c) {
+    const double2 v = tk.part[t * tk.d.blocks + c];
     s.x += v.x;
     s.y += v.y;
   }
@@ -955,7 +998,8 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
   // memory by TMA alone, while the converter warps add shared-memory traffic
   // next to the three MMAs per k-step).
   d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= 64;
-  if (d->fused) return make_fused_desc(cd, d);
+  if (d->fused && make_fused_desc(cd, d)) return true;
+  d->fused = false;
   const int es = bf16 ? 2 : 4;
   d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA
   const int64_t bk = 128 / es;                  // elements per k block
@@ -1028,11 +1072,13 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d) {
   d->a_off = off;
   if (!d->a_direct) {
     make_perm_desc(concat_groups(cd.am, cd.ak), cd.lt, cd.a_ts, &d->a_perm);
+    if (!perm_fits(d->a_perm)) return false;
     off = round_up(off + cd.lt * cd.M * cd.K * 8, 256);
   }
   d->b_off = off;
   if (!d->b_direct) {
     make_perm_desc(concat_groups(cd.bn, cd.bk), cd.lt, cd.b_ts, &d->b_perm);
+    if (!perm_fits(d->b_perm)) return false;
     off = round_up(off + cd.lt * cd.N * cd.K * 8, 256);
   }
   d->part_off = off;
@@ -1250,12 +1296,18 @@ void make_perm_desc(const Group& g0, int64_t lt, int64_t src_ts, PermDesc* d) {
     d->outer *= g.ext[last];
     d->X = 1;
   }
-  d->blocks = d->mode == 0 ? d->outer * ((d->X + 255) / 256)
-                           : d->outer * ((d->X + 31) / 32) * ((d->Y + 31) / 32);
+  d->blocks = d->mode == 0
+                  ? (d->n + kPermElems - 1) / kPermElems
+                  : d->outer * ((d->X + 31) / 32) *
+                        (((d->Y + 31) / 32 + kPermTiles - 1) / kPermTiles);
+}
+
+bool perm_fits(const PermDesc& d) {  // the block functions use 32-bit offsets
+  return d.n < (1ll << 31) && d.src_ts < (1ll << 31) && d.blocks > 0 && d.blocks < (1ll << 31);
 }
 
 int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStream_t s) {
-  if (d.lt > 65535 || d.blocks <= 0 || d.blocks >= (1ll << 31)) return -1;
+  if (d.lt > 65535 || !perm_fits(d)) return -1;
   dim3 grid((unsigned)d.blocks, (unsigned)d.lt);
   k_permute_c64<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(src),
                                      reinterpret_cast<float2*>(dst), d);
@@ -1263,44 +1315,32 @@ int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStre
 }
 
 namespace {
-bool ca_needs_copy(const ContractAllDesc& d) {
-  return !(d.bp.n == 1 && d.bp.stride[0] == 1);
+// correlator plan: B visited in the left operand's order (no copy)
+PermDesc ca_perm(const ContractAllDesc& d) {
+  PermDesc pd;
+  make_perm_desc(d.bp, d.lt, d.S, &pd);
+  return pd;
 }
-int64_t ca_part_bytes(const ContractAllDesc& d) { return (d.lt * (int64_t)d.chunks * 16 + 255) & ~int64_t(255); }
-ContractAllDesc ca_identity(const ContractAllDesc& d) {
-  ContractAllDesc e = d;
-  e.bp.n = 1;
-  e.bp.ext[0] = (int)d.S;
-  e.bp.stride[0] = 1;
-  return e;
+int64_t ca_part_bytes(const PermDesc& pd) {
+  return (pd.lt * (int64_t)pd.blocks * 16 + 255) & ~int64_t(255);
 }
 }  // namespace
 
 int64_t contract_all_c64_scratch_bytes(const ContractAllDesc& d) {
-  return ca_part_bytes(d) + (ca_needs_copy(d) ? d.lt * d.S * 8 : 0);
+  return ca_part_bytes(ca_perm(d));
 }
 
 int launch_contract_all_c64(const ContractAllDesc& d0, const float* A, const float* B, double* C,
                             double* scratch, double scale, cudaStream_t s) {
-  if (d0.lt > 65535) return -1;
-  int nk = 0;
-  ContractAllDesc d = d0;
-  if (ca_needs_copy(d0)) {  // right operand into the left operand's order, coalesced
-    PermDesc pd;
-    make_perm_desc(d0.bp, d0.lt, d0.S, &pd);
-    float* copy = reinterpret_cast<float*>(reinterpret_cast<char*>(scratch) + ca_part_bytes(d0));
-    if (launch_permute_c64(pd, B, copy, s) < 0) return -1;
-    ++nk;
-    B = copy;
-    d = ca_identity(d0);
-  }
-  dim3 grid((unsigned)d.chunks, (unsigned)d.lt);
+  const PermDesc pd = ca_perm(d0);
+  if (pd.lt > 65535 || !perm_fits(pd) || pd.blocks > (1 << 20)) return -1;
+  dim3 grid((unsigned)pd.blocks, (unsigned)pd.lt);
   double2* part = reinterpret_cast<double2*>(scratch);
   k_contract_all_c64<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(A),
-                                          reinterpret_cast<const float2*>(B), part, d);
-  k_contract_all_final_scaled<<<(unsigned)((d.lt + 127) / 128), 128, 0, s>>>(
-      part, reinterpret_cast<double2*>(C), d.lt, d.chunks, scale);
-  return cudaPeekAtLastError() == cudaSuccess ? nk + 2 : -1;
+                                          reinterpret_cast<const float2*>(B), part, pd);
+  k_contract_all_final_scaled<<<(unsigned)((pd.lt + 127) / 128), 128, 0, s>>>(
+      part, reinterpret_cast<double2*>(C), pd.lt, (int)pd.blocks, scale);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int mixed_error_status(bool reset) {
@@ -1405,19 +1445,12 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     c.B = reinterpret_cast<const float2*>(r.B);
     c.out = reinterpret_cast<double2*>(r.C);
     c.part = reinterpret_cast<double2*>(r.part);
-    c.d = *r.d;
-    if (ca_needs_copy(*r.d)) {
-      PermDesc pd;
-      make_perm_desc(r.d->bp, r.d->lt, r.d->S, &pd);
-      void* dst = reinterpret_cast<char*>(r.part) + ca_part_bytes(*r.d);
-      add_perm(pd, r.B, dst);
-      c.B = static_cast<const float2*>(dst);
-      c.d = ca_identity(*r.d);
-    }
+    c.d = ca_perm(*r.d);
+    if (!perm_fits(c.d)) return false;
     c.scale = r.scale;
     c.block_start = cb;
     c.t_start = ct;
-    cb += (long long)c.d.chunks * c.d.lt;
+    cb += c.d.blocks * c.d.lt;
     ct += c.d.lt;
     ca.push_back(c);
   }

@@ -57,6 +57,8 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d);
 
 // g: dst axes (extent, source stride), row-major order.
 void make_perm_desc(const Group& g, int64_t lt, int64_t src_ts, PermDesc* d);
+// true when the permute / correlator blocks can index the slices (32-bit)
+bool perm_fits(const PermDesc& d);
 int launch_permute_c64(const PermDesc& d, const float* src, float* dst, cudaStream_t s);
 // bytes of scratch the complex64 contract-all needs (partials + a reordered
 // copy of the right operand when its pairing is not contiguous)
@@ -79,7 +81,7 @@ struct GroupExt {
   char* scratch;
 };
 // one correlator of a level: its scratch region `part` of
-// contract_all_c64_scratch_bytes (partials, then the reordered right operand)
+// contract_all_c64_scratch_bytes (the per-block FP64 partial sums)
 struct GroupRoot {
   const ContractAllDesc* d;
   const float* A;

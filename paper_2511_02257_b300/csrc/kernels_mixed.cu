@@ -848,12 +848,14 @@ struct ReduceTask {
 
 constexpr int kReduceElems = 2048;  // elements per block of the grouped reduction
 
-template <typename T>
-__device__ __forceinline__ int find_task(const T* tasks, int n, long long b) {
+// task owning block b: binary search over the contiguous first-block array
+// (a few cache lines, shared by every block of the launch)
+__device__ __forceinline__ int find_task(const long long* __restrict__ starts, int n,
+                                         long long b) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (tasks[mid].block_start <= b) lo = mid;
+    if (__ldg(starts + mid) <= b) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -861,9 +863,10 @@ __device__ __forceinline__ int find_task(const T* tasks, int n, long long b) {
 
 template <bool BF16>
 __global__ void __launch_bounds__(256)
-k_pack_grouped(const PackTask* __restrict__ tasks, int n) {
+k_pack_grouped(const PackTask* __restrict__ tasks, const long long* __restrict__ starts,
+               int n) {
   typedef typename Split<BF16>::T T;
-  const PackTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+  const PackTask& tk = tasks[find_task(starts, n, blockIdx.x)];
   const long long local = blockIdx.x - tk.block_start;
   const int bx = (int)(local % tk.kblk), by = (int)((local / tk.kblk) % tk.rblk);
   const int bz = (int)(local / ((long long)tk.kblk * tk.rblk));
@@ -876,15 +879,17 @@ k_pack_grouped(const PackTask* __restrict__ tasks, int n) {
 }
 
 __global__ void __launch_bounds__(256)
-k_permute_grouped(const PermTask* __restrict__ tasks, int n) {
-  const PermTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+k_permute_grouped(const PermTask* __restrict__ tasks, const long long* __restrict__ starts,
+                  int n) {
+  const PermTask& tk = tasks[find_task(starts, n, blockIdx.x)];
   const long long local = blockIdx.x - tk.block_start;
   permute_block(tk.d, tk.src, tk.dst, (int)(local / tk.d.blocks), local % tk.d.blocks);
 }
 
 __global__ void __launch_bounds__(256)
-k_contract_all_grouped(const CATask* __restrict__ tasks, int n) {
-  const CATask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+k_contract_all_grouped(const CATask* __restrict__ tasks, const long long* __restrict__ starts,
+                       int n) {
+  const CATask& tk = tasks[find_task(starts, n, blockIdx.x)];
   const long long local = blockIdx.x - tk.block_start;
   ca_partial_block(tk.A, tk.B, tk.part, tk.d, local / tk.d.blocks,
                    (unsigned)(local % tk.d.blocks));
@@ -912,8 +917,9 @@ __global__ void k_contract_all_final_grouped(const CATask* __restrict__ tasks, i
 }
 
 __global__ void __launch_bounds__(256)
-k_reduce_grouped(const ReduceTask* __restrict__ tasks, int n) {
-  const ReduceTask& tk = tasks[find_task(tasks, n, blockIdx.x)];
+k_reduce_grouped(const ReduceTask* __restrict__ tasks, const long long* __restrict__ starts,
+                 int n) {
+  const ReduceTask& tk = tasks[find_task(starts, n, blockIdx.x)];
   const long long base = (blockIdx.x - tk.block_start) * (long long)kReduceElems;
   for (int e = threadIdx.x; e < kReduceElems; e += 256) {
     const long long i = base + e;
@@ -1454,6 +1460,15 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     ct += c.d.lt;
     ca.push_back(c);
   }
+  auto starts = [&](const auto& v) {
+    std::vector<long long> st;
+    for (const auto& t : v) st.push_back(t.block_start);
+    return reinterpret_cast<const long long*>(append(buf, st, 64));
+  };
+  lvl->pack_starts = starts(pk);
+  lvl->red_starts = starts(rd);
+  lvl->perm_starts = starts(pm);
+  lvl->ca_starts = starts(ca);
   lvl->pack = reinterpret_cast<const void*>(append(buf, pk, 64));
   lvl->npack = (int)pk.size();
   lvl->pack_blocks = pb;
@@ -1484,22 +1499,29 @@ void rebase_level(LevelDev* lvl, const char* base) {
   lvl->perm = base + reinterpret_cast<uintptr_t>(lvl->perm);
   lvl->gemm_fused = base + reinterpret_cast<uintptr_t>(lvl->gemm_fused);
   lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
+  auto rb = [&](const long long*& p) {
+    p = reinterpret_cast<const long long*>(base + reinterpret_cast<uintptr_t>(p));
+  };
+  rb(lvl->pack_starts);
+  rb(lvl->red_starts);
+  rb(lvl->perm_starts);
+  rb(lvl->ca_starts);
 }
 
 int launch_level(const LevelDev& L, cudaStream_t s) {
   int nk = 0;
   if (L.nperm > 0) {  // operand reorders of fused GEMMs and correlator partners
     k_permute_grouped<<<(unsigned)L.perm_blocks, 256, 0, s>>>(
-        static_cast<const PermTask*>(L.perm), L.nperm);
+        static_cast<const PermTask*>(L.perm), L.perm_starts, L.nperm);
     ++nk;
   }
   if (L.npack > 0) {
     if (L.bf16)
       k_pack_grouped<true><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
-          static_cast<const PackTask*>(L.pack), L.npack);
+          static_cast<const PackTask*>(L.pack), L.pack_starts, L.npack);
     else
       k_pack_grouped<false><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
-          static_cast<const PackTask*>(L.pack), L.npack);
+          static_cast<const PackTask*>(L.pack), L.pack_starts, L.npack);
     ++nk;
     GemmParams gp;
     std::memset(&gp, 0, sizeof(gp));
@@ -1520,12 +1542,12 @@ int launch_level(const LevelDev& L, cudaStream_t s) {
   }
   if (L.nred > 0) {
     k_reduce_grouped<<<(unsigned)L.red_blocks, 256, 0, s>>>(
-        static_cast<const ReduceTask*>(L.red), L.nred);
+        static_cast<const ReduceTask*>(L.red), L.red_starts, L.nred);
     ++nk;
   }
   if (L.nca > 0) {
     k_contract_all_grouped<<<(unsigned)L.ca_blocks, 256, 0, s>>>(
-        static_cast<const CATask*>(L.ca), L.nca);
+        static_cast<const CATask*>(L.ca), L.ca_starts, L.nca);
     k_contract_all_final_grouped<<<(unsigned)((L.ca_threads + 127) / 128), 128, 0, s>>>(
         static_cast<const CATask*>(L.ca), L.nca, L.ca_threads);
     nk += 2;

@@ -91,8 +91,11 @@ struct GroupRoot {
   double scale;
 };
 // task tables of one level (device pointers after rebase_level)
+// (each *_starts array: the tasks' first block indices, ascending, for the
+// block -> task search of the grouped kernels)
 struct LevelDev {
   const void* pack;
+  const long long* pack_starts;
   int npack;
   long long pack_blocks;
   const void* gemm;
@@ -102,12 +105,15 @@ struct LevelDev {
   int ngemm_fused;
   long long gemm_fused_tiles;
   const void* red;
+  const long long* red_starts;
   int nred;
   long long red_blocks;
   const void* perm;
+  const long long* perm_starts;
   int nperm;
   long long perm_blocks;
   const void* ca;
+  const long long* ca_starts;
   int nca;
   long long ca_blocks, ca_threads;
   bool bf16;

@@ -684,26 +684,35 @@ __device__ __forceinline__ unsigned perm_outer(const PermDesc& d, unsigned o, un
   return so;
 }
 
-// calls op(e, src value) for the elements of block b (one slice)
-template <typename Op>
+// calls op(e, src value, pre(e)) for the elements of block b (one slice);
+// pre(e) is issued for every element before the block's barrier, so its
+// loads overlap the source loads (a correlator's left operand)
+template <typename Pre, typename Op>
 __device__ __forceinline__ void perm_visit(const PermDesc& d, const float2* __restrict__ src,
-                                           unsigned b, unsigned char* smem, Op op) {
+                                           unsigned b, unsigned char* smem, Pre pre, Op op) {
   if (d.mode == 0) {
+    constexpr int J = kPermElems / 256;
     unsigned* so_tab = reinterpret_cast<unsigned*>(smem);
     const unsigned X = (unsigned)d.X;
     const unsigned e0 = b * kPermElems;
     const unsigned e1 = min(e0 + (unsigned)kPermElems, (unsigned)d.n);
     const unsigned r0 = e0 / X, r1 = (e1 - 1) / X;
+    float2 pv[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const unsigned e = e0 + j * 256 + threadIdx.x;
+      pv[j] = e < e1 ? pre(e) : make_float2(0.f, 0.f);
+    }
     unsigned dummy;
     for (unsigned r = r0 + threadIdx.x; r <= r1; r += blockDim.x)
       so_tab[r - r0] = perm_outer(d, r, &dummy);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kPermElems / 256; ++j) {
+    for (int j = 0; j < J; ++j) {
       const unsigned e = e0 + j * 256 + threadIdx.x;
       if (e < e1) {
         const unsigned r = e / X;
-        op(e, src[so_tab[r - r0] + (e - r * X)]);
+        op(e, src[so_tab[r - r0] + (e - r * X)], pv[j]);
       }
     }
     return;
@@ -717,13 +726,23 @@ __device__ __forceinline__ void perm_visit(const PermDesc& d, const float2* __re
   const unsigned so = perm_outer(d, o, &dso);
   const unsigned tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const unsigned sX = (unsigned)d.sX, dY = (unsigned)d.dY;
+  const unsigned X = (unsigned)d.X, Y = (unsigned)d.Y;
+  float2 pv[kPermTiles][4];
 #pragma unroll
-  for (int q = 0; q < kPermTiles; ++q) {  // along the source's unit-stride axis Y
+  for (int q = 0; q < kPermTiles; ++q) {  // destination-order operand, along X
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned x = x0 + tx, y = (yg * kPermTiles + q) * 32 + ty + 8 * j;
+      pv[q][j] = (y < Y && x < X) ? pre(dso + y * dY + x) : make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPermTiles; ++q) {  // source, along its unit-stride axis Y
     const unsigned y = (yg * kPermTiles + q) * 32 + tx;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const unsigned x = x0 + ty + 8 * j;
-      if (y < (unsigned)d.Y && x < (unsigned)d.X) tile[q][ty + 8 * j][tx] = src[so + y + x * sX];
+      if (y < Y && x < X) tile[q][ty + 8 * j][tx] = src[so + y + x * sX];
     }
   }
   __syncthreads();
@@ -733,7 +752,7 @@ __device__ __forceinline__ void perm_visit(const PermDesc& d, const float2* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const unsigned y = (yg * kPermTiles + q) * 32 + ty + 8 * j;
-      if (y < (unsigned)d.Y && x < (unsigned)d.X) op(dso + y * dY + x, tile[q][tx][ty + 8 * j]);
+      if (y < Y && x < X) op(dso + y * dY + x, tile[q][tx][ty + 8 * j], pv[q][j]);
     }
   }
 }
@@ -743,7 +762,9 @@ __device__ __forceinline__ void permute_block(const PermDesc& d, const float2* _
   __shared__ __align__(16) unsigned char smem[kPermSmem];
   src += (long long)t * d.src_ts;
   dst += (long long)t * d.n;
-  perm_visit(d, src, (unsigned)b, smem, [&](unsigned e, float2 v) { dst[e] = v; });
+  perm_visit(
+      d, src, (unsigned)b, smem, [](unsigned) { return make_float2(0.f, 0.f); },
+      [&](unsigned e, float2 v, float2) { dst[e] = v; });
 }
 
 __global__ void __launch_bounds__(256)
@@ -764,8 +785,7 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
   // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
   // ~44 significant bits) at FP32 throughput; across threads and blocks: FP64
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  perm_visit(d, B, b, smem, [&](unsigned e, float2 bv) {
-    const float2 a = A[e];
+  perm_visit(d, B, b, smem, [&](unsigned e) { return A[e]; }, [&](unsigned, float2 bv, float2 a) {
     df_acc_prod(rh, rl, a.x, bv.x);
     df_acc_prod(rh, rl, -a.y, bv.y);
     df_acc_prod(ih, il, a.x, bv.y);

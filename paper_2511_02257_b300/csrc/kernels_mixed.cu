@@ -774,23 +774,57 @@ k_permute_c64(const float2* __restrict__ src, float2* __restrict__ dst, const Pe
 
 // partial sum of block b of slice t of one correlator, r(t) = sum_e A[e] *
 // B[src(e)] with the destination order of `d` = the left operand's order;
-// fixed reduction order, so every launch form gives the same bits
+// fixed reduction order, so every launch form gives the same bits.  Runs
+// (mode 0) go through perm_visit; transposed pairs (mode 1) without shared
+// memory: each warp sums one 32x32 tile, A read along X (coalesced), B
+// along its unit-stride axis Y per lane (each lane's lines stay in L1
+// across the tile's 32 rows), kCaWarpTiles tiles per block.
+constexpr int kCaWarpTiles = 8;
+
+__device__ __forceinline__ void ca_acc(float& rh, float& rl, float& ih, float& il, float2 a,
+                                       float2 bv) {
+  df_acc_prod(rh, rl, a.x, bv.x);
+  df_acc_prod(rh, rl, -a.y, bv.y);
+  df_acc_prod(ih, il, a.x, bv.y);
+  df_acc_prod(ih, il, a.y, bv.x);
+}
+
 __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
                                                  const float2* __restrict__ B,
                                                  double2* __restrict__ part, const PermDesc& d,
                                                  long long t, unsigned b) {
-  __shared__ __align__(16) unsigned char smem[kPermSmem];
+  __shared__ __align__(16) unsigned char smem[(kPermElems + 1) * 4];
   A += t * d.n;
   B += t * d.src_ts;
   // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
   // ~44 significant bits) at FP32 throughput; across threads and blocks: FP64
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  perm_visit(d, B, b, smem, [&](unsigned e) { return A[e]; }, [&](unsigned, float2 bv, float2 a) {
-    df_acc_prod(rh, rl, a.x, bv.x);
-    df_acc_prod(rh, rl, -a.y, bv.y);
-    df_acc_prod(ih, il, a.x, bv.y);
-    df_acc_prod(ih, il, a.y, bv.x);
-  });
+  if (d.mode == 0) {
+    perm_visit(d, B, b, smem, [&](unsigned e) { return A[e]; },
+               [&](unsigned, float2 bv, float2 a) { ca_acc(rh, rl, ih, il, a, bv); });
+  } else {
+    const unsigned X = (unsigned)d.X, Y = (unsigned)d.Y;
+    const unsigned xb = (X + 31) / 32, yb = (Y + 31) / 32;
+    const unsigned tile = b * kCaWarpTiles + (threadIdx.x >> 5);
+    const unsigned lane = threadIdx.x & 31;
+    if (tile < (unsigned)d.outer * xb * yb) {
+      const unsigned o = tile / (xb * yb), rem = tile - o * (xb * yb);
+      const unsigned x = (rem % xb) * 32 + lane, y0 = (rem / xb) * 32;
+      unsigned dso;
+      const unsigned so = perm_outer(d, o, &dso);
+      if (x < X) {
+        const float2* a = A + dso + x;
+        const float2* bp = B + so + x * (unsigned)d.sX;
+        const unsigned dY = (unsigned)d.dY;
+        const unsigned ny = min(32u, Y - y0);
+#pragma unroll 8
+        for (unsigned yy = 0; yy < ny; ++yy) {
+          const unsigned y = y0 + yy;
+          ca_acc(rh, rl, ih, il, a[y * dY], bp[y]);
+        }
+      }
+    }
+  }
   double re = (double)rh + (double)rl, im = (double)ih + (double)il;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1345,6 +1379,9 @@ namespace {
 PermDesc ca_perm(const ContractAllDesc& d) {
   PermDesc pd;
   make_perm_desc(d.bp, d.lt, d.S, &pd);
+  if (pd.mode == 1)  // warp tiles of 32x32, kCaWarpTiles per block
+    pd.blocks = (pd.outer * ((pd.X + 31) / 32) * ((pd.Y + 31) / 32) + kCaWarpTiles - 1) /
+                kCaWarpTiles;
   return pd;
 }
 int64_t ca_part_bytes(const PermDesc& pd) {

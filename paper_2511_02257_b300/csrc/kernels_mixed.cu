@@ -32,6 +32,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "kernels.hpp"
 #include "kernels_mixed.hpp"
@@ -866,12 +867,12 @@ __global__ void k_contract_all_final_scaled(const double2* __restrict__ part,
 // handful of launches per level instead of a few per contraction.  Every
 // launch walks a task table in global memory; a block finds its task by
 // binary search over the tasks' first block index.
-struct PackTask {
-  PackArgs op[2];
-  const float2* X[2];
-  void* hi[2];
-  void* lo[2];
-  int lt, kblk, rblk;
+struct PackTask {  // one operand; identical operands of a level are packed once
+  PackArgs op;
+  const float2* X;
+  void* hi;
+  void* lo;
+  int kblk, rblk;
   long long block_start;
 };
 
@@ -923,13 +924,9 @@ k_pack_grouped(const PackTask* __restrict__ tasks, const long long* __restrict__
   const PackTask& tk = tasks[find_task(starts, n, blockIdx.x)];
   const long long local = blockIdx.x - tk.block_start;
   const int bx = (int)(local % tk.kblk), by = (int)((local / tk.kblk) % tk.rblk);
-  const int bz = (int)(local / ((long long)tk.kblk * tk.rblk));
-  const int which = bz >= tk.lt ? 1 : 0;
-  const int t = bz - which * tk.lt;
-  const unsigned r0 = by * 32, k0 = bx * 32;
-  if (r0 >= (unsigned)tk.op[which].rows) return;
-  pack_block<BF16>(tk.op[which], tk.X[which], static_cast<T*>(tk.hi[which]),
-                   static_cast<T*>(tk.lo[which]), t, r0, k0);
+  const int t = (int)(local / ((long long)tk.kblk * tk.rblk));
+  pack_block<BF16>(tk.op, tk.X, static_cast<T*>(tk.hi), static_cast<T*>(tk.lo), t, by * 32,
+                   bx * 32);
 }
 
 __global__ void __launch_bounds__(256)
@@ -1169,23 +1166,28 @@ static PackArgs pack_args(const ContractDesc& cd, int which, int64_t kp) {
 }
 
 // task of one contraction whose planes / partials live in `scratch`
+// a_stage / b_stage: where the operand's planes (plane form) or reordered
+// copy (fused form) are, when another contraction of the level produced them;
+// nullptr = in this contraction's own scratch
 bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* scratch, float* C,
-                    GemmTask* t) {
+                    GemmTask* t, const char* a_stage, const char* b_stage) {
   const ContractDesc& cd = d.cd;
   char* sc = static_cast<char*>(scratch);
+  const char* as = a_stage ? a_stage : sc + d.a_off;
+  const char* bs = b_stage ? b_stage : sc + d.b_off;
   std::memset(t, 0, sizeof(*t));
   if (d.fused) {
-    const void* a = d.a_direct ? (const void*)A : (const void*)(sc + d.a_off);
-    const void* b = d.b_direct ? (const void*)B : (const void*)(sc + d.b_off);
+    const void* a = d.a_direct ? (const void*)A : (const void*)as;
+    const void* b = d.b_direct ? (const void*)B : (const void*)bs;
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
     if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM) ||
         !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts, kBN / 2))
       return false;
-  } else if (!make_map(&t->map[0], sc + d.a_off, d.bf16, d.kp, cd.M, cd.lt) ||
-      !make_map(&t->map[1], sc + d.a_off + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
-      !make_map(&t->map[2], sc + d.b_off, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
-      !make_map(&t->map[3], sc + d.b_off + d.plane_b, d.bf16, d.kp, 2 * cd.N, cd.lt))
+  } else if (!make_map(&t->map[0], as, d.bf16, d.kp, cd.M, cd.lt) ||
+             !make_map(&t->map[1], as + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
+             !make_map(&t->map[2], bs, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
+             !make_map(&t->map[3], bs + d.plane_b, d.bf16, d.kp, 2 * cd.N, cd.lt))
     return false;
   t->M = (int)cd.M;
   t->Nr = (int)(2 * cd.N);
@@ -1240,7 +1242,7 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
     if (nk < 0) return -1;
     GemmParams gp;
     std::memset(&gp, 0, sizeof(gp));
-    if (!fill_gemm_task(d, A, B, scratch, C, &gp.single)) return -2;
+    if (!fill_gemm_task(d, A, B, scratch, C, &gp.single, nullptr, nullptr)) return -2;
     gp.total_tiles = gp.single.tiles;
     if (launch_gemm(gp, false, true, s) < 0) return -1;
     ++nk;
@@ -1291,7 +1293,7 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
   }
   GemmParams gp;
   std::memset(&gp, 0, sizeof(gp));
-  if (!fill_gemm_task(d, A, B, scratch, C, &gp.single)) return -2;
+  if (!fill_gemm_task(d, A, B, scratch, C, &gp.single, nullptr, nullptr)) return -2;
   gp.total_tiles = gp.single.tiles;
   if (launch_gemm(gp, d.bf16, false, s) < 0) return -1;
   ++nk;
@@ -1462,40 +1464,69 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     rb += (r.per + kReduceElems - 1) / kReduceElems;
     rd.push_back(r);
   };
+  // an operand staged (reordered, or split into planes) for one contraction
+  // of the level serves every contraction of the level that stages the same
+  // tensor the same way: key = source address + the staging descriptor
+  std::unordered_map<std::string, const char*> staged;
+  auto key_of = [](const void* src, const void* desc, size_t n, int64_t lt) {
+    std::string k(reinterpret_cast<const char*>(&src), sizeof(src));
+    k.append(reinterpret_cast<const char*>(desc), n);
+    k.append(reinterpret_cast<const char*>(&lt), sizeof(lt));
+    return k;
+  };
+  // returns the staged data of (src, desc): existing, or `dst` after
+  // registering it (then *fresh = true and the caller adds the task)
+  auto stage = [&](const std::string& key, const char* dst, bool* fresh) {
+    auto it = staged.find(key);
+    *fresh = it == staged.end();
+    if (*fresh) staged.emplace(key, dst);
+    return *fresh ? dst : it->second;
+  };
   for (const GroupExt& e : ext) {
     const MixedDesc& d = *e.d;
     const ContractDesc& cd = d.cd;
     char* sc = e.scratch;
+    const char* as = nullptr;
+    const char* bs = nullptr;
+    bool fresh = false;
     if (d.fused) {
-      if (!d.a_direct) add_perm(d.a_perm, e.A, sc + d.a_off);
-      if (!d.b_direct) add_perm(d.b_perm, e.B, sc + d.b_off);
+      if (!d.a_direct) {
+        as = stage(key_of(e.A, &d.a_perm, sizeof(PermDesc), 0), sc + d.a_off, &fresh);
+        if (fresh) add_perm(d.a_perm, e.A, sc + d.a_off);
+      }
+      if (!d.b_direct) {
+        bs = stage(key_of(e.B, &d.b_perm, sizeof(PermDesc), 0), sc + d.b_off, &fresh);
+        if (fresh) add_perm(d.b_perm, e.B, sc + d.b_off);
+      }
       GemmTask g;
-      if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g)) return false;
+      if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g, as, bs)) return false;
       g.tile_start = ftiles;
       ftiles += g.tiles;
       gf.push_back(g);
       if (d.splits > 1) add_reduce(d, g, e.C);
       continue;
     }
-    PackTask p;
-    std::memset(&p, 0, sizeof(p));
-    p.op[0] = pack_args(cd, 0, d.kp);
-    p.op[1] = pack_args(cd, 1, d.kp);
-    p.X[0] = reinterpret_cast<const float2*>(e.A);
-    p.X[1] = reinterpret_cast<const float2*>(e.B);
-    p.hi[0] = sc + d.a_off;
-    p.lo[0] = sc + d.a_off + d.plane_a;
-    p.hi[1] = sc + d.b_off;
-    p.lo[1] = sc + d.b_off + d.plane_b;
-    p.lt = (int)cd.lt;
     const int64_t kc = std::max<int64_t>(cd.K, d.kp / 2);
-    p.kblk = (int)((kc + 31) / 32);
-    p.rblk = (int)((std::max<int64_t>(cd.M, cd.N) + 31) / 32);
-    p.block_start = pb;
-    pb += (long long)p.kblk * p.rblk * 2 * p.lt;
-    pk.push_back(p);
+    for (int which = 0; which < 2; ++which) {
+      PackTask p;
+      std::memset(&p, 0, sizeof(p));
+      p.op = pack_args(cd, which, d.kp);
+      p.X = reinterpret_cast<const float2*>(which ? e.B : e.A);
+      char* dst = sc + (which ? d.b_off : d.a_off);
+      const char* got = stage(key_of(p.X, &p.op, sizeof(PackArgs), cd.lt),
+                              dst, &fresh);
+      (which ? bs : as) = got;
+      if (!fresh) continue;
+      p.hi = dst;
+      p.lo = dst + (which ? d.plane_b : d.plane_a);
+      p.kblk = (int)((kc + 31) / 32);
+      p.rblk = (int)((p.op.rows + 31) / 32);
+      p.block_start = pb;
+      pb += (long long)p.kblk * p.rblk * cd.lt;
+      pk.push_back(p);
+    }
     GemmTask g;
-    if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g)) return false;
+    if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g, as, bs)) return false;
     g.tile_start = tiles;
     tiles += g.tiles;
     gm.push_back(g);

@@ -20,10 +20,11 @@ naive order.
 
 times one contraction shape through the single-contraction C ABI.
 
-  python -m paper_2511_02257_b300.experiments batched [--steps 2]
+  python -m paper_2511_02257_b300.experiments batched [--workload batched|baryon|...]
+         [--steps 2] [--window 64]
 
-runs the batched workload (50 independent DAGs of uneven N and Lt, ~18k
-contractions) in the mixed-precision grouped form (windows of independent
+runs a workload (default: the batched one, 50 independent DAGs of uneven N
+and Lt, ~18k contractions) in the mixed-precision grouped form (windows of independent
 contractions per launch, CUDA graphs) and as one launch per contraction in
 FP64, with the leaves resident on the device and from pinned host memory;
 reports times, speedups and the TF32x3 error of every correlator against

@@ -56,6 +56,9 @@ def parse():
                     help="with --precision fp64: also time this mixed precision on the same "
                          "workload (grouped windows, graphs) and report its speedup and "
                          "error against the FP64 path; 'none' skips it")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="mixed precisions: pick window / fused-form limit / split policy by "
+                         "timing every candidate on this DAG before the timed steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -236,6 +239,14 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def autotune(nd, stream):
+    """Run the library's autotuner on a staged DAG; summary for the line."""
+    t0 = time.perf_counter()
+    entries = nd.autotune(stream, reps=2)
+    return {"best": entries[0], "worst_ms": entries[-1]["ms"], "candidates": len(entries),
+            "tune_s": time.perf_counter() - t0}
+
+
 def shape_breakdown(wl, ids, times, n_exec):
     """Kernel ms per execution grouped by contraction shape (M, N, K per slice;
     K alone for a correlator), largest first."""
@@ -292,9 +303,12 @@ def main():
 
     # ---- device-resident leaves: the kernel-level metric
     nd.stage_leaves(stream)
-    nd.set_option(L.LQC_OPT_TIMING, 1)
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
     nd.set_option(L.LQC_OPT_WINDOW, args.window)
+    tuned = None
+    if args.precision != "fp64" and args.autotune:
+        tuned = autotune(nd, stream)
+    nd.set_option(L.LQC_OPT_TIMING, 1)
     for _ in range(args.warmup):
         nd.execute(stream)
     nd.wait()
@@ -362,6 +376,7 @@ def main():
         md.stage_leaves(stream)
         md.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
         md.set_option(L.LQC_OPT_WINDOW, args.window)
+        mtuned = autotune(md, stream) if args.autotune else None
         for _ in range(args.warmup):
             md.execute(stream)
         torch.cuda.synchronize()
@@ -374,7 +389,7 @@ def main():
         mv = md.read_all_correlators()
         err = np.linalg.norm(mv - corr, axis=-1) / np.linalg.norm(corr, axis=-1)
         mst = md.exec_info()
-        pform = {"precision": args.compare, "window": args.window,
+        pform = {"precision": args.compare, "autotune": mtuned,
                  "time_to_solution_s": mms / 1e3, "tflops": flops_step / (mms * 1e-3) / 1e12,
                  "speedup_vs_fp64": (ms / args.steps) / mms,
                  "err_vs_fp64_max": float(err.max()), "err_vs_fp64_median": float(np.median(err)),
@@ -431,7 +446,9 @@ def main():
                        "functions": len(wl.functions), "contractions": len(nd.order()),
                        "policy": args.policy, "evict": args.evict, "budget_bytes": budget,
                        "precision": args.precision, "cuda_graph": bool(args.graph),
-                       "window": args.window if args.precision != "fp64" else 0,
+                       "window": (tuned["best"]["window"] if tuned else args.window)
+                                 if args.precision != "fp64" else 0,
+                       "autotune": tuned,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
                              % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,

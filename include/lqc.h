@@ -118,13 +118,30 @@ typedef enum {
   LQC_OPT_TIMING = 3,     /* 1: bracket every contraction kernel with CUDA
                              events on the compute stream; lqc_dag_get_exec_info
                              then reports summed per-kind kernel time        */
-  LQC_OPT_WINDOW = 4      /* mixed precisions, plans without evictions: run up
+  LQC_OPT_WINDOW = 4,     /* mixed precisions, plans without evictions: run up
                              to this many consecutive contractions of the order
                              as one grouped window (frees deferred to its end;
                              each dependency level a few grouped launches).
                              0 or 1 = one contraction at a time; default 64.
                              Timing then covers whole windows              */
+  LQC_OPT_FUSED_MAX_N = 5, /* TF32X3: right operands of at most this many
+                             complex columns (and an even paired extent) are
+                             read as raw complex64 and split inside the GEMM;
+                             wider ones are split into hi/lo planes first.
+                             Default 64; 0 = never fused                    */
+  LQC_OPT_SPLIT_POLICY = 6 /* mixed GEMM k splits: 0 (default) while the
+                             output tiles cannot fill the GPU and for the
+                             FP32 chunk bound (1024 real k), 1 for the chunk
+                             bound only                                     */
 } lqc_option;
+
+/* One autotuner candidate and its measured time per execute. */
+typedef struct {
+  int64_t window;        /* LQC_OPT_WINDOW */
+  int64_t fused_max_n;   /* LQC_OPT_FUSED_MAX_N */
+  int64_t split_policy;  /* LQC_OPT_SPLIT_POLICY */
+  double ms;             /* device time per execute (CUDA events) */
+} lqc_tune_entry;
 
 /* Create an empty DAG.  lt >= 1 time slices (the batch extent of the
  * leaves registered next, see lqc_dag_set_batch); prec selects storage and
@@ -223,6 +240,22 @@ int lqc_dag_unstage_leaves(lqc_dag* dag);
  * arena (sized by the plan) and the results buffer; later calls reuse them.
  * Errors: LQC_ERR_STATE (not scheduled, leaf without data), LQC_ERR_CUDA. */
 int lqc_dag_execute(lqc_dag* dag, void* stream);
+
+/* Autotuner of the mixed precisions (no counterpart in the paper: the
+ * batching form's tile and grouping choices).  After lqc_dag_schedule, with
+ * leaf data given (or staged): for every candidate of LQC_OPT_WINDOW in
+ * {0, 64, 256} (windows only when the plan evicts nothing) x
+ * LQC_OPT_FUSED_MAX_N in {0, 64, 2^30} (TF32X3 only) x LQC_OPT_SPLIT_POLICY
+ * in {0, 1}, runs one execute that builds the program, then times `reps`
+ * executes on `stream` with CUDA events; sets the three options to the
+ * fastest candidate.  entries (nullable; capacity cap) receive every
+ * candidate with its time, *n their count (at most 18).  Correlators of
+ * every candidate agree within the mixed tolerance; the chosen options stay
+ * in effect for later executes.  Errors: LQC_ERR_STATE (not scheduled, leaf
+ * without data), LQC_ERR_ARG (FP64 DAG, reps outside [1, 1000], cap too
+ * small), LQC_ERR_CUDA; on error the previous options are restored. */
+int lqc_dag_autotune(lqc_dag* dag, void* stream, int reps, lqc_tune_entry* entries,
+                     int64_t cap, int64_t* n);
 
 /* Wait (bounded by timeout_ms; <= 0 means 60000) for the last execute to
  * finish.  LQC_ERR_TIMEOUT if it did not finish in time (the DAG stays

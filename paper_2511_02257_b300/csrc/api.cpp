@@ -285,6 +285,14 @@ int lqc_dag_set_option(lqc_dag* h, int option, int64_t value) {
       if (value < 0 || value > 4096) return fail(h, LQC_ERR_ARG, "window size out of range");
       h->d.opt_window = value;
       break;
+    case LQC_OPT_FUSED_MAX_N:
+      if (value < 0) return fail(h, LQC_ERR_ARG, "fused-form limit must be >= 0");
+      h->d.opt_fused_max_n = value;
+      break;
+    case LQC_OPT_SPLIT_POLICY:
+      if (value != 0 && value != 1) return fail(h, LQC_ERR_ARG, "split policy must be 0 or 1");
+      h->d.opt_split_policy = value;
+      break;
     default: return fail(h, LQC_ERR_ARG, "unknown option");
   }
   lqc::exec_invalidate_plan(h->d);
@@ -373,6 +381,18 @@ int lqc_dag_execute(lqc_dag* h, void* stream) {
   LQC_GUARD_BEGIN
   if (!h->d.scheduled) return fail(h, LQC_ERR_STATE, "execute before schedule");
   return lqc::exec_run(h->d, stream);
+  LQC_GUARD_END(h)
+}
+
+int lqc_dag_autotune(lqc_dag* h, void* stream, int reps, lqc_tune_entry* entries, int64_t cap,
+                     int64_t* n) {
+  if (!h || !n) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  if (!h->d.scheduled) return fail(h, LQC_ERR_STATE, "autotune before schedule");
+  if (h->d.prec == LQC_PREC_FP64)
+    return fail(h, LQC_ERR_ARG, "autotune applies to the mixed precisions");
+  if (reps < 1 || reps > 1000) return fail(h, LQC_ERR_ARG, "reps out of range");
+  return lqc::exec_autotune(h->d, stream, reps, entries, cap, n);
   LQC_GUARD_END(h)
 }
 

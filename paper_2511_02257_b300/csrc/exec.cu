@@ -462,7 +462,10 @@ int build_program(Dag& g) {
       }
       MixedDesc md{};
       if (g.prec != LQC_PREC_FP64 && in.kind == I_CONTRACT) {
-        if (!make_mixed_desc(cd, g.prec == LQC_PREC_BF16X3, &md)) {
+        MixedTune tune;
+        tune.fused_max_n = g.opt_fused_max_n;
+        tune.split_policy = (int)g.opt_split_policy;
+        if (!make_mixed_desc(cd, g.prec == LQC_PREC_BF16X3, &md, tune)) {
           g.err = "contraction too large for the mixed-precision kernels";
           return LQC_ERR_ARG;
         }
@@ -806,6 +809,70 @@ void exec_invalidate_plan(Dag& g) {
   if (!g.ex) return;
   exec_wait(g, 60000);
   free_program(*g.ex);
+}
+
+// Times whole executions of the scheduled DAG (as it stands: staged or host
+// leaves, graph or not) for every candidate of window x fused-form limit x
+// split policy, `reps` executes each after one that builds the program; the
+// fastest is kept.  Windows only where the plan evicts nothing.
+int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64_t cap,
+                  int64_t* n) {
+  std::vector<lqc_tune_entry> cand;
+  const bool windows_ok = g.planned.n_evict == 0;
+  for (int64_t w : {int64_t(0), int64_t(64), int64_t(256)}) {
+    if (w && !windows_ok) continue;
+    for (int64_t f : {int64_t(0), int64_t(64), int64_t(1) << 30}) {
+      if (g.prec == LQC_PREC_BF16X3 && f) continue;  // no fused form for BF16
+      for (int64_t sp : {int64_t(0), int64_t(1)}) cand.push_back(lqc_tune_entry{w, f, sp, 0.0});
+    }
+  }
+  if (cap < (int64_t)cand.size() && entries) {
+    g.err = "tune entry capacity too small";
+    return LQC_ERR_ARG;
+  }
+  const int64_t save[3] = {g.opt_window, g.opt_fused_max_n, g.opt_split_policy};
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0), "tune event");
+  CK(cudaEventCreate(&e1), "tune event");
+  int rc = LQC_OK;
+  size_t best = 0;
+  for (size_t c = 0; c < cand.size() && rc == LQC_OK; ++c) {
+    g.opt_window = cand[c].window;
+    g.opt_fused_max_n = cand[c].fused_max_n;
+    g.opt_split_policy = cand[c].split_policy;
+    exec_invalidate_plan(g);
+    rc = exec_run(g, stream);  // builds the program (and the graph)
+    if (rc != LQC_OK) break;
+    cudaEventRecord(e0, cs);
+    for (int r = 0; r < reps && rc == LQC_OK; ++r) rc = exec_run(g, stream);
+    cudaEventRecord(e1, cs);
+    if (rc != LQC_OK) break;
+    rc = exec_wait(g, 600000);
+    if (rc != LQC_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) rc = cuda_fail(g, e, "tune timing");
+    cand[c].ms = ms / reps;
+    if (cand[c].ms < cand[best].ms) best = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LQC_OK) {
+    g.opt_window = save[0];
+    g.opt_fused_max_n = save[1];
+    g.opt_split_policy = save[2];
+    exec_invalidate_plan(g);
+    return rc;
+  }
+  g.opt_window = cand[best].window;
+  g.opt_fused_max_n = cand[best].fused_max_n;
+  g.opt_split_policy = cand[best].split_policy;
+  exec_invalidate_plan(g);
+  *n = (int64_t)cand.size();
+  if (entries) std::copy(cand.begin(), cand.end(), entries);
+  return LQC_OK;
 }
 
 namespace {

@@ -67,6 +67,7 @@ struct Dag {
   // execution
   ExecState* ex = nullptr;
   int64_t opt_graph = 0, opt_poison = 0, opt_timing = 0, opt_window = 64;
+  int64_t opt_fused_max_n = 64, opt_split_policy = 0;  // mixed GEMM choices
   lqc_stats measured{};
   lqc_exec_info info{};
   bool executed = false;
@@ -92,6 +93,8 @@ int64_t model_peak(const Dag& g, const std::vector<int64_t>& order);
 
 // ---- executor (exec.cu) ----
 int exec_run(Dag& g, void* stream);
+int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64_t cap,
+                  int64_t* n);
 int exec_wait(Dag& g, int64_t timeout_ms);
 int exec_collect_timing(Dag& g);
 int exec_kernel_times(Dag& g, int64_t* node, double* ms, int64_t cap, int64_t* n);

@@ -1044,30 +1044,38 @@ int num_sms() {  // SMs of the current device (one persistent CTA each)
 
 }  // namespace
 
-bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
+namespace {
+// split count: (policy 0) k splits while the output tiles alone cannot fill
+// the GPU, keeping >= 4 k blocks per split; always FP32 chunks of <=
+// kMaxChunk real k (error control)
+int64_t choose_splits(const ContractDesc& cd, int64_t kblocks, int64_t bk, int policy) {
+  const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
+  int64_t splits = 1;
+  if (policy == 0)
+    while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
+  while ((kblocks + splits - 1) / splits * bk > kMaxChunk && splits < 64) splits *= 2;
+  return splits;
+}
+}  // namespace
+
+bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const MixedTune& tune) {
   std::memset(d, 0, sizeof(*d));
   d->bf16 = bf16;
   d->cd = cd;
   // fused form: TF32 with an even paired extent (16-byte complex64 rows) and
-  // a narrow right operand (<= 64 complex columns).  There the hi/lo planes
+  // a narrow right operand (by default <= 64 complex columns).  There the hi/lo planes
   // of the plane form cost more HBM traffic than the contraction itself; for
   // wide operands the plane form is faster (its operand tiles reach shared
   // memory by TMA alone, while the converter warps add shared-memory traffic
   // next to the three MMAs per k-step).
-  d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= 64;
-  if (d->fused && make_fused_desc(cd, d)) return true;
+  d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= tune.fused_max_n;
+  if (d->fused && make_fused_desc(cd, d, tune.split_policy)) return true;
   d->fused = false;
   const int es = bf16 ? 2 : 4;
   d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA
   const int64_t bk = 128 / es;                  // elements per k block
   const int64_t kblocks = (d->kp + bk - 1) / bk;
-  // split k when the output tiles alone cannot fill the GPU, keeping at
-  // least 4 k blocks per split
-  const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
-  int64_t splits = 1;
-  while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
-  // and keep FP32 accumulation chunks to <= kMaxChunk real k (error control)
-  while ((kblocks + splits - 1) / splits * bk > kMaxChunk && splits < 64) splits *= 2;
+  const int64_t splits = choose_splits(cd, kblocks, bk, tune.split_policy);
   d->splits = (int)splits;
   d->kblocks = (int)((kblocks + splits - 1) / splits);
   const int64_t plane_a = cd.lt * cd.M * d->kp * es;
@@ -1082,15 +1090,6 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d) {
 }
 
 namespace {
-// split count: k splits when the output tiles alone cannot fill the GPU
-// (keeping >= 4 k blocks per split), and FP32 chunks of <= kMaxChunk real k
-int64_t choose_splits(const ContractDesc& cd, int64_t kblocks, int64_t bk) {
-  const int64_t tiles = ((2 * cd.N + kBN - 1) / kBN) * ((cd.M + kBM - 1) / kBM) * cd.lt;
-  int64_t splits = 1;
-  while (tiles * splits * 2 <= 2 * 148 && kblocks / (splits * 2) >= 4) splits *= 2;
-  while ((kblocks + splits - 1) / splits * bk > kMaxChunk && splits < 64) splits *= 2;
-  return splits;
-}
 // dst axes (rows group, then k group) with the operand's strides
 Group concat_groups(const Group& rows, const Group& ks) {
   Group g;
@@ -1107,11 +1106,11 @@ Group concat_groups(const Group& rows, const Group& ks) {
 }
 }  // namespace
 
-bool make_fused_desc(const ContractDesc& cd, MixedDesc* d) {
+bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
   d->kp = 2 * cd.K;                              // real k of a complex64 row
   const int64_t bk = 32;                         // fp32 elements per 128-byte k block
   const int64_t kblocks = (d->kp + bk - 1) / bk;
-  const int64_t splits = choose_splits(cd, kblocks, bk);
+  const int64_t splits = choose_splits(cd, kblocks, bk, split_policy);
   d->splits = (int)splits;
   d->kblocks = (int)((kblocks + splits - 1) / splits);
   // an operand whose paired axes form its unit-stride axis and whose free

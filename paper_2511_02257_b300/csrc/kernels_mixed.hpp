@@ -51,9 +51,18 @@ struct MixedDesc {
   int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
   PermDesc a_perm, b_perm;
 };
-bool make_fused_desc(const ContractDesc& cd, MixedDesc* d);
+bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 
-bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d);
+// Choices the autotuner makes per DAG: right operands of at most
+// fused_max_n complex columns take the fused form (TF32, even K); split
+// policy 0 splits k while the output tiles cannot fill the GPU (and for the
+// FP32 chunk bound), 1 only for the FP32 chunk bound.
+struct MixedTune {
+  int64_t fused_max_n = 64;
+  int split_policy = 0;
+};
+bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d,
+                     const MixedTune& tune = MixedTune());
 
 // g: dst axes (extent, source stride), row-major order.
 void make_perm_desc(const Group& g, int64_t lt, int64_t src_ts, PermDesc* d);

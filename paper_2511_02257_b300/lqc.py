@@ -33,6 +33,7 @@ LQC_SCHED_NAIVE_TOPO, LQC_SCHED_TREE, LQC_SCHED_SIBLING = 0, 1, 2
 LQC_EVICT_LRU, LQC_EVICT_NEXT_USE = 0, 1
 LQC_PREC_FP64, LQC_PREC_TF32X3, LQC_PREC_BF16X3 = 0, 1, 2
 LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING, LQC_OPT_WINDOW = 1, 2, 3, 4
+LQC_OPT_FUSED_MAX_N, LQC_OPT_SPLIT_POLICY = 5, 6
 OP_NAMES = {0: "LOAD", 1: "EVICT", 2: "CONTRACT", 3: "FREE"}
 POLICIES = {"naive": LQC_SCHED_NAIVE_TOPO, "tree": LQC_SCHED_TREE, "sibling": LQC_SCHED_SIBLING}
 EVICTS = {"lru": LQC_EVICT_LRU, "next_use": LQC_EVICT_NEXT_USE}
@@ -55,6 +56,14 @@ class lqc_exec_info(ctypes.Structure):
                                      "copied_d2h", "n_ops", "n_contract", "n_contract_all")] + \
         [("ms_contract", ctypes.c_double), ("ms_contract_all", ctypes.c_double),
          ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class lqc_tune_entry(ctypes.Structure):
+    _fields_ = [("window", c_i64), ("fused_max_n", c_i64), ("split_policy", c_i64),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -84,6 +93,8 @@ _sig("lqc_dag_stage_leaves", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_unstage_leaves", ctypes.c_int, [c_vp])
 _sig("lqc_dag_execute", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_wait", ctypes.c_int, [c_vp, c_i64])
+_sig("lqc_dag_autotune", ctypes.c_int, [c_vp, c_vp, ctypes.c_int, ctypes.POINTER(lqc_tune_entry),
+                                        c_i64, P_i64])
 _sig("lqc_dag_read_correlator", ctypes.c_int, [c_vp, c_i64, P_dbl])
 _sig("lqc_dag_read_all_correlators", ctypes.c_int, [c_vp, P_dbl, c_i64])
 _sig("lqc_dag_get_roots", ctypes.c_int, [c_vp, P_i64, c_i64, P_i64])
@@ -115,7 +126,8 @@ _sig("lqc_contract_all_c64_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c
 for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
            "lqc_dag_add_contraction", "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
            "lqc_dag_get_plan", "lqc_dag_set_option", "lqc_dag_stage_leaves",
-           "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_read_correlator",
+           "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_autotune",
+           "lqc_dag_read_correlator",
            "lqc_dag_read_all_correlators", "lqc_dag_get_roots", "lqc_dag_num_nodes",
            "lqc_dag_node_info", "lqc_dag_get_stats", "lqc_dag_get_exec_info", "lqc_last_error",
            "lqc_dag_get_kernel_times",
@@ -263,6 +275,16 @@ class Dag:
 
     def execute(self, stream: int = 0):
         self._check(_lib.lqc_dag_execute(self.h, c_vp(stream)), "execute")
+
+    def autotune(self, stream: int = 0, reps: int = 3):
+        """Time every candidate of (window, fused-form limit, split policy)
+        on this DAG and keep the fastest; returns the candidates with their
+        ms per execute, fastest first."""
+        entries = (lqc_tune_entry * 32)()
+        n = c_i64()
+        self._check(_lib.lqc_dag_autotune(self.h, c_vp(stream), int(reps), entries, 32,
+                                          ctypes.byref(n)), "autotune")
+        return sorted((entries[i].as_dict() for i in range(n.value)), key=lambda e: e["ms"])
 
     def wait(self, timeout_ms: int = 60000):
         self._check(_lib.lqc_dag_wait(self.h, int(timeout_ms)), "wait")

@@ -279,3 +279,19 @@ def test_multi_meson_full_size_all_roots():
     errs = [rel_err(vals[r], ref[r]) for r in ref]
     assert max(errs) < TOL, max(errs)
     assert nd.stats() == planned
+
+
+def test_baryon_fp64_sampled_roots():
+    """Baryon-like DAG (B_64 leaves contracted over one or two legs, with
+    meson insertions): a seeded sample of correlators against the oracle."""
+    wl = synth.make_workload("baryon")
+    od, _ = D.build_from_workload(wl)
+    rng = np.random.default_rng(5)
+    roots = [int(r) for r in rng.choice(od.roots(), size=16, replace=False)]
+    _, ref = _oracle(wl, roots)
+    nd, _ = _native(wl)
+    planned = nd.schedule("tree")
+    nd.execute(torch.cuda.current_stream().cuda_stream)
+    errs = [rel_err(nd.read_correlator(r), ref[r]) for r in roots]
+    assert max(errs) < TOL, max(errs)
+    assert nd.stats() == planned

@@ -16,9 +16,12 @@ Prints one JSON line per policy, then a summary line with ratios to the
 naive order.
 
   python -m paper_2511_02257_b300.experiments kernel --shape pxp --n 64 --lt 64
-         [--precision tf32x3|bf16x3|fp64] [--reps 20]
+         [--precision tf32x3|bf16x3|fp64] [--reps 20] [--fused-max-n F]
 
-times one contraction shape through the single-contraction C ABI.
+times one contraction shape through the single-contraction C ABI, or, with
+--fused-max-n, as a one-contraction DAG (leaves staged on the device, the
+executor's options set; F = 0 forces the plane form, a large F the fused
+form of TF32X3).
 
   python -m paper_2511_02257_b300.experiments batched [--workload batched|baryon|...]
          [--steps 2] [--window 64]
@@ -65,9 +68,12 @@ def kernel_bench(argv):
     ap.add_argument("--lt", type=int, default=64)
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--fused-max-n", type=int, default=None)
     args = ap.parse_args(argv)
     sa, sb, la, ra = SHAPES[args.shape](args.n)
     lt = args.lt
+    if args.fused_max_n is not None:
+        return kernel_bench_dag(args, sa, sb, la, ra)
     P64 = ctypes.POINTER(ctypes.c_int64)
     PI = ctypes.POINTER(ctypes.c_int)
     ea = np.asarray(sa, np.int64)
@@ -120,6 +126,42 @@ def kernel_bench(argv):
                       "complex_tflops": flops / ms / 1e9,
                       "tensor_tflops": (3 if prec != L.LQC_PREC_FP64 else 1) * flops / ms / 1e9,
                       "algorithmic_gbs": alg_bytes / ms / 1e6}), flush=True)
+
+
+def kernel_bench_dag(args, sa, sb, la, ra):
+    """One contraction as a DAG (two staged leaves, one root of rank > 0)."""
+    import torch
+    import paper_2511_02257_b300 as L
+    lt = args.lt
+    rng = np.random.default_rng(1)
+    d = L.Dag(lt, args.precision)
+    a = d.add_leaf(sa, (rng.standard_normal((lt,) + sa) + 1j * rng.standard_normal((lt,) + sa)))
+    b = d.add_leaf(sb, (rng.standard_normal((lt,) + sb) + 1j * rng.standard_normal((lt,) + sb)))
+    d.add_contraction(a, b, la, ra)
+    d.schedule("tree")
+    stream = torch.cuda.current_stream().cuda_stream
+    d.set_option(L.LQC_OPT_WINDOW, 0)
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, args.fused_max_n)
+    d.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
+    d.stage_leaves(stream)
+    for _ in range(3):
+        d.execute(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        d.execute(stream)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    K = int(np.prod([sa[i] for i in la]))
+    M = int(np.prod(sa)) // K
+    N = int(np.prod(sb)) // K
+    flops = 8.0 * lt * M * N * K
+    print(json.dumps({"shape": args.shape, "n": args.n, "lt": lt, "M": M, "N": N, "K": K,
+                      "precision": args.precision, "fused_max_n": args.fused_max_n,
+                      "ms_per_contraction": ms, "complex_tflops": flops / ms / 1e9,
+                      "kernels": d.exec_info()["n_kernels"]}), flush=True)
 
 
 def _gen_leaves(wl):

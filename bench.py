@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--autotune", type=int, default=1,
                     help="mixed precisions: pick window / fused-form limit / split policy by "
                          "timing every candidate on this DAG before the timed steps")
+    ap.add_argument("--fused-max-n", type=int, default=64,
+                    help="with --autotune 0: LQC_OPT_FUSED_MAX_N of the mixed path")
+    ap.add_argument("--split-policy", type=int, default=0,
+                    help="with --autotune 0: LQC_OPT_SPLIT_POLICY of the mixed path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -305,6 +309,8 @@ def main():
     nd.stage_leaves(stream)
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
     nd.set_option(L.LQC_OPT_WINDOW, args.window)
+    nd.set_option(L.LQC_OPT_FUSED_MAX_N, args.fused_max_n)
+    nd.set_option(L.LQC_OPT_SPLIT_POLICY, args.split_policy)
     tuned = None
     if args.precision != "fp64" and args.autotune:
         tuned = autotune(nd, stream)
@@ -376,6 +382,8 @@ def main():
         md.stage_leaves(stream)
         md.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
         md.set_option(L.LQC_OPT_WINDOW, args.window)
+        md.set_option(L.LQC_OPT_FUSED_MAX_N, args.fused_max_n)
+        md.set_option(L.LQC_OPT_SPLIT_POLICY, args.split_policy)
         mtuned = autotune(md, stream) if args.autotune else None
         for _ in range(args.warmup):
             md.execute(stream)
@@ -449,6 +457,9 @@ def main():
                        "window": (tuned["best"]["window"] if tuned else args.window)
                                  if args.precision != "fp64" else 0,
                        "autotune": tuned,
+                       "fused_max_n": (tuned["best"]["fused_max_n"] if tuned else args.fused_max_n),
+                       "split_policy": (tuned["best"]["split_policy"] if tuned
+                                        else args.split_policy),
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
                              % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,

@@ -47,7 +47,7 @@ constexpr int kStages = 3;
 constexpr int kTmemCols = 4 * kBN;  // 2 buffers x (main + correction accumulator)
 constexpr int64_t kMaxChunk = 1024;  // real k summed in FP32 registers before an FP64 sum
 constexpr int kDrainWarps = 8;  // two per TMEM lane quarter, one per column half
-constexpr int kConvWarps = 4;   // fused form: raw complex64 tiles -> hi/lo operand tiles
+constexpr int kConvWarps = 6;   // fused form: raw complex64 tiles -> hi/lo operand tiles
 constexpr int kGemmThreads = 64 + 32 * kDrainWarps;
 constexpr int kChunkBlocks = 2;     // k-blocks per TMEM accumulation before a drain
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s

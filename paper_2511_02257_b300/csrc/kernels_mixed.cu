@@ -191,6 +191,7 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   CUtensorMap map[4];   // Ahi, Alo, Bhi, Blo
   float* out;           // splits == 1: D' [lt][M][Nr]; else partials [splits][lt][M][Nr]
   int M, Nr, kblocks, splits, lt, ntn, ntm, tiles;
+  int b_mn;             // fused form: B stored [k][n] (n unit-stride), transposed by the converters
   long long tile_start;
 };
 
@@ -327,7 +328,10 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
             tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
-            tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], k0, n0 / 2, t);
+            if (tk->b_mn)  // [16 complex k rows][kBN/2 complex n], unswizzled
+              tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], n0, k0 / 2, t);
+            else
+              tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], k0, n0 / 2, t);
           } else {
             uint8_t* sp = smem + st * C::kStageBytes;
             mbar_expect_tx(&rf[st], C::kStageBytes);
@@ -484,12 +488,9 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           *reinterpret_cast<float4*>(sp + C::kATile + 16 * c) = make_float4(l0, l1, l2, l3);
         }
         // B: complex row n -> B' rows 2n (re, -im) and 2n+1 (im, re); 16-byte
-        // chunk c of row r sits at chunk c ^ (r & 7) (128-byte swizzle)
-#pragma unroll 2
-        for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
-          const int n = it >> 3, c = it & 7;
-          const float4 v =
-              *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 + 16 * (c ^ (n & 7)));
+        // chunk c (complex k 2c, 2c+1) of row r sits at chunk c ^ (r & 7)
+        // (128-byte swizzle).  v = (re, im) at k = 2c, then at 2c + 1.
+        auto emit = [&](int n, int c, float4 v) {
           const int r0 = 2 * n, r1 = 2 * n + 1;
           const int o0 = r0 * 128 + 16 * (c ^ (r0 & 7)), o1 = r1 * 128 + 16 * (c ^ (r1 & 7));
           float h[4], l[4];
@@ -504,6 +505,25 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           // row 2n+1 = (im, re): the same split parts, re-paired
           *reinterpret_cast<float4*>(bh + o1) = make_float4(-h[1], h[0], -h[3], h[2]);
           *reinterpret_cast<float4*>(bl + o1) = make_float4(-l[1], l[0], -l[3], l[2]);
+        };
+        if (tk->b_mn) {
+          // raw tile [16 k][kBN/2 n] complex: consecutive threads take
+          // consecutive n (conflict-free reads), the transpose happens in the
+          // writes to the K-major operand rows
+          const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
+#pragma unroll 2
+          for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
+            const int n = it % (kBN / 2), c = it / (kBN / 2);
+            const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
+            emit(n, c, make_float4(v0.x, v0.y, v1.x, v1.y));
+          }
+        } else {
+#pragma unroll 2
+          for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
+            const int n = it >> 3, c = it & 7;
+            emit(n, c, *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 +
+                                                         16 * (c ^ (n & 7))));
+          }
         }
         // generic-proxy writes -> visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1016,6 +1036,23 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // 3-D fp32 map over raw complex64 rows: dims (2K floats, rows, lt), strides
 // in complex elements, box (32 floats = 128 bytes, box_rows, 1)
+// [lt][K rows][n2 floats] (n unit-stride), boxes of kBN floats (kBN/2
+// complex n) x 16 rows (complex k), unswizzled: the raw tile of a right
+// operand stored [k][n]
+bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows, int64_t lt,
+                     int64_t row_stride, int64_t slice_stride) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)n2, (cuuint64_t)krows, (cuuint64_t)lt};
+  cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 8), (cuuint64_t)(slice_stride * 8)};
+  cuuint32_t box[3] = {(cuuint32_t)kBN, 16u, 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool make_raw_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t lt,
                   int64_t row_stride, int64_t slice_stride, int box_rows) {
   auto fn = encode_fn();
@@ -1124,6 +1161,14 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
   d->b_direct = direct(cd.bn, cd.bk, cd.b_kfast) && cd.b_ts % 2 == 0;
   d->a_rowstride = d->a_direct ? (cd.am.n ? cd.am.stride[0] : cd.K) : cd.K;
   d->b_rowstride = d->b_direct ? (cd.bn.n ? cd.bn.stride[0] : cd.K) : cd.K;
+  // B stored [k][n] with n unit-stride (a matrix product's right operand):
+  // read in place, k rows of 16-byte multiples, transposed by the converters
+  d->b_mn = !d->b_direct && !cd.b_kfast && cd.bn.n == 1 && cd.bn.stride[0] == 1 &&
+            cd.bk.n == 1 && cd.bk.stride[0] % 2 == 0 && cd.b_ts % 2 == 0;
+  if (d->b_mn) {
+    d->b_direct = true;
+    d->b_rowstride = cd.bk.stride[0];
+  }
   int64_t off = 0;
   d->a_off = off;
   if (!d->a_direct) {
@@ -1180,9 +1225,11 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const void* b = d.b_direct ? (const void*)B : (const void*)bs;
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
-    if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM) ||
-        !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts, kBN / 2))
+    if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) return false;
+    if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
+               : !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts, kBN / 2))
       return false;
+    t->b_mn = d.b_mn ? 1 : 0;
   } else if (!make_map(&t->map[0], as, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[1], as + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[2], bs, d.bf16, d.kp, 2 * cd.N, cd.lt) ||

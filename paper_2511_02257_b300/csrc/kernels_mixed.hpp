@@ -48,6 +48,7 @@ struct MixedDesc {
   // already [rows][K] with K unit-stride, else reordered into scratch
   bool fused;
   bool a_direct, b_direct;
+  bool b_mn;                // B read in place as [k][n]; the GEMM's converters transpose it
   int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
   PermDesc a_perm, b_perm;
 };

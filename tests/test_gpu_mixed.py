@@ -233,3 +233,29 @@ def test_contract_all_c64_vs_oracle(case, lt):
     torch.cuda.synchronize()
     # products of float inputs are exact in the double-float sums: FP64-level agreement
     assert rel_err(dC.cpu().numpy(), 2.0 * ref) < 1e-12
+
+
+@pytest.mark.parametrize("mkn", [(64, 64, 64), (100, 48, 130), (33, 70, 200), (256, 192, 256),
+                                 (128, 1100, 96)])
+@pytest.mark.parametrize("fused", [0, 1 << 30])
+@pytest.mark.parametrize("window", [0, 64])
+def test_matrix_product_forms_vs_oracle(mkn, fused, window):
+    """C = A.B with B stored [k][n] (read in place and transposed inside the
+    fused GEMM when n is even), then Tr(C.D): every form against the oracle."""
+    M, K, N = mkn
+    lt = 3
+    rng = np.random.default_rng(M * 7 + K * 3 + N)
+
+    def rnd(*s):
+        return (rng.standard_normal((lt,) + s) + 1j * rng.standard_normal((lt,) + s)) / np.sqrt(K)
+    A, B, Dm = rnd(M, K), rnd(K, N), rnd(N, M)
+    ref = C.contract_pair(C.contract_pair(A, B, (1,), (0,)), Dm, (0, 1), (1, 0))
+    d = L.Dag(lt, "tf32x3")
+    a, b, dd = d.add_leaf((M, K), A), d.add_leaf((K, N), B), d.add_leaf((N, M), Dm)
+    c = d.add_contraction(a, b, [1], [0])
+    r = d.add_contraction(c, dd, [0, 1], [1, 0])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, fused)
+    d.set_option(L.LQC_OPT_WINDOW, window)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3

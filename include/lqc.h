@@ -352,7 +352,8 @@ int lqc_contract_all_fp64_noalloc(const double* A, int rank_a, const int64_t* ex
  * accumulated in FP32 on the tensor cores (tcgen05), and long contractions are
  * split over the paired indices into FP32 partials summed in FP64.
  * `scratch` (caller-owned device memory, contents ignored) must hold
- * lqc_contract_mixed_scratch_bytes(...) bytes.  Errors: LQC_ERR_ARG,
+ * lqc_contract_mixed_scratch_bytes(...) bytes (at least 256; that call returns 0
+ * for shapes or a precision it rejects).  Errors: LQC_ERR_ARG,
  * LQC_ERR_CUDA.  A kernel that gives up on a bounded internal wait records it
  * in a device error word read by lqc_mixed_error. */
 int lqc_contract_mixed(const float* A, int rank_a, const int64_t* ext_a,

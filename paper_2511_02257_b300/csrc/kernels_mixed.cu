@@ -1705,7 +1705,7 @@ int64_t lqc_contract_mixed_scratch_bytes(int rank_a, const int64_t* ext_a, int r
   if (!lqc::make_contract_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &cd, &err))
     return 0;
   if (!lqc::make_mixed_desc(cd, prec == LQC_PREC_BF16X3, &md)) return 0;
-  return md.scratch_bytes;
+  return std::max<int64_t>(md.scratch_bytes, 256);  // 0 is reserved for errors
 }
 
 int lqc_contract_mixed(const float* A, int rank_a, const int64_t* ext_a, const float* B,

@@ -1,5 +1,8 @@
 """Contraction orders: a naive topological baseline, the sibling scheduler
-(Sec. III-A, Alg. 1-3) and the tree scheduler (Sec. III-B, Alg. 4-8).
+(Sec. III-A, Alg. 1-3), the tree scheduler (Sec. III-B, Alg. 4-8), and two
+schedulers the paper only names: a node-based gain scheduler (its stated
+future work, Sec. VI) and the similarity ordering of trees it attributes to
+Redstar (RS-GS, Sec. II-A).
 
 Each scheduler returns the order of the non-leaf nodes (the contractions).
 Leaves "brought to memory" inside a scheduler have no effect on the order;
@@ -19,6 +22,19 @@ Readings where the paper leaves a choice open (all deterministic):
   x.outAv - u; "INMMEM" is INMEM; PROCESS-CTREE visits the nodes of T by a
   post-order walk from the root (left operand first, each node once) and
   skips nodes an earlier tree already processed (their sub-trees too).
+* node (one sentence in Sec. VI: a node-based scheduler using the tree
+  scheduler's gain concept): at every step, among the contractions whose
+  non-leaf inputs are computed, take the one whose processing lowers the
+  resident memory of the model (Sec. II-C) the most -- gain = bytes of the
+  inputs it releases (it is their last pending consumer) - bytes of the
+  leaves it loads - its output bytes (none for a root, released at once);
+  ties to the smallest id.
+* rsgs (Sec. II-A: trees sorted by similarity, trees sharing contractions
+  processed one after the other): start with the first tree (smallest root
+  id); next, the unprocessed tree sharing the most contractions (non-leaf
+  nodes) with the tree processed last, ties to the smallest index; each
+  tree's not yet processed nodes are emitted by the same post-order walk as
+  the tree scheduler's.
 """
 from __future__ import annotations
 
@@ -258,4 +274,95 @@ def tree(dag: Dag, check: Optional[Callable[[TreeState, List[int]], None]] = Non
     return order
 
 
-SCHEDULERS = {"naive": naive, "sibling": sibling, "tree": tree}
+# --------------------------------------------------------------------------
+# Node-based gain scheduler (Sec. VI, future work; reading in the header)
+# --------------------------------------------------------------------------
+def node_gain(dag: Dag, u: int, resident, pending) -> int:
+    """Bytes by which processing u lowers the resident memory of the model:
+    released inputs - loaded leaves - the output (kept unless u is a root)."""
+    nd = dag.nodes[u]
+    g = 0
+    for x in nd.children:
+        if dag.nodes[x].is_leaf and x not in resident:
+            g -= dag.size(x)
+        if pending[x] == 1:          # u is x's last pending consumer
+            g += dag.size(x)
+    if nd.parents:
+        g -= dag.size(u)
+    return g
+
+
+def node(dag: Dag, check: Optional[Callable[[List[int], List[int]], None]] = None) -> List[int]:
+    """Greedy by gain over the available contractions, recomputed from the
+    definition at every step.  ``check(order_so_far, available)`` runs before
+    every selection (test hook)."""
+    nodes = dag.nodes
+    pending = [len(nd.parents) for nd in nodes]
+    resident = set()
+    done = [False] * len(nodes)
+
+    def ready(u):
+        return all(nodes[c].is_leaf or done[c] for c in nodes[u].children)
+    avail = {u for u in dag.non_leaf() if ready(u)}
+    order: List[int] = []
+    while avail:
+        if check is not None:
+            check(list(order), sorted(avail))
+        best = min(avail, key=lambda u: (-node_gain(dag, u, resident, pending), u))
+        avail.discard(best)
+        order.append(best)
+        done[best] = True
+        for x in nodes[best].children:
+            if nodes[x].is_leaf:
+                resident.add(x)
+            pending[x] -= 1
+            if pending[x] == 0:
+                resident.discard(x)
+        if nodes[best].parents:
+            resident.add(best)
+        for p in nodes[best].parents:
+            if not done[p] and ready(p):
+                avail.add(p)
+    return order
+
+
+# --------------------------------------------------------------------------
+# RS-GS: trees ordered by similarity (Sec. II-A; reading in the header)
+# --------------------------------------------------------------------------
+def _post_order(dag: Dag, root: int, done, out: List[int]) -> None:
+    stack = [(root, False)]
+    while stack:
+        u, expanded = stack.pop()
+        nd = dag.nodes[u]
+        if nd.is_leaf or done[u]:
+            continue
+        if expanded:
+            done[u] = True
+            out.append(u)
+            continue
+        stack.append((u, True))
+        for c in reversed(nd.children):   # left operand first
+            stack.append((c, False))
+
+
+def rsgs(dag: Dag) -> List[int]:
+    roots = dag.roots()
+    contr = [set(u for u in dag.tree(r) if not dag.nodes[u].is_leaf) for r in roots]
+    done = [False] * len(dag.nodes)
+    used = [False] * len(roots)
+    order: List[int] = []
+    cur = 0 if roots else -1
+    while cur >= 0:
+        used[cur] = True
+        _post_order(dag, roots[cur], done, order)
+        best, best_shared = -1, -1
+        for j in range(len(roots)):
+            if not used[j]:
+                shared = len(contr[cur] & contr[j])
+                if shared > best_shared:
+                    best, best_shared = j, shared
+        cur = best
+    return order
+
+
+SCHEDULERS = {"naive": naive, "sibling": sibling, "tree": tree, "node": node, "rsgs": rsgs}

@@ -8,6 +8,13 @@
   the sibling scheduler processes every node exactly once (Sec. III-A).
 * Peaks are never below the exhaustive optimum; on tiny DAGs the tree
   scheduler's peak is compared with that optimum.
+* Node-based gain scheduler: hand trace on the Table 1 DAG; before every
+  selection, the chosen node is the available one whose step lowers the
+  memory model's M the most, with M recomputed by the model itself
+  (oracle.memory.model_trace on the prefix plus the candidate); a planted
+  sign mistake in the gain is caught.
+* Similarity order of trees (RS-GS): hand trace on the Table 1 DAG and a
+  constructed DAG whose tree sequence is fixed by inspection.
 """
 import json
 import os
@@ -72,7 +79,7 @@ def test_tree_gains_match_from_scratch_workloads(name):
 
 
 @pytest.mark.parametrize("seed", range(40))
-@pytest.mark.parametrize("sched", ["naive", "sibling", "tree"])
+@pytest.mark.parametrize("sched", ["naive", "sibling", "tree", "node", "rsgs"])
 def test_orders_valid_and_not_below_optimum(seed, sched):
     lt, leaves, contr = random_spec(1000 + seed, n_leaves=4, n_contr=7)
     dag = D.from_spec(lt, leaves, contr)
@@ -93,7 +100,7 @@ def test_sibling_processes_each_node_once():
 def test_workload_orders_valid(name):
     wl = synth.make_workload(name)
     dag, _ = D.build_from_workload(wl)
-    for s in ("naive", "sibling", "tree"):
+    for s in ("naive", "sibling", "tree", "node", "rsgs"):
         assert D.validate_order(dag, S.SCHEDULERS[s](dag)) is None
 
 
@@ -143,3 +150,64 @@ def test_planted_gain_mistake_caught():
         assert caught
     finally:
         S.TreeState.process_child = orig
+
+
+def test_node_and_rsgs_hand_traces():
+    g = json.load(open(os.path.join(GOLD, "table1.json")))
+    h = json.load(open(os.path.join(GOLD, "hand_traces.json")))
+    dag, idx, names = _named_dag(g)
+    order = S.node(dag)
+    assert [names[u] for u in order] == h["node"]["order"]
+    sizes, _ = M.model_trace(dag, order)
+    assert [x // UNIT for x in sizes] == h["node"]["sizes"]
+    assert [names[u] for u in S.rsgs(dag)] == h["rsgs"]["order"]
+    ex = json.load(open(os.path.join(GOLD, "rsgs_example.json")))
+    dag2 = D.from_spec(1, [(1, 1)] * ex["leaves"],
+                       [(l, r, tuple(la), tuple(ra)) for (l, r, la, ra) in ex["contractions"]])
+    assert S.rsgs(dag2) == ex["rsgs_order"]
+
+
+def _node_check_via_model(dag, expected):
+    """Independent of node_gain: the step that lowers M the most, M taken
+    from the memory model's own trace."""
+    def check(prefix, avail):
+        base = M.model_trace(dag, prefix)[0][-1] if prefix else 0
+        delta = {v: M.model_trace(dag, prefix + [v])[0][-1] - base for v in avail}
+        expected.append(min(avail, key=lambda v: (delta[v], v)))
+    return check
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_node_choice_lowers_model_memory_most(seed):
+    lt, leaves, contr = random_spec(3000 + seed, n_leaves=6, n_contr=14, share=0.6)
+    dag = D.from_spec(lt, leaves, contr)
+    expected = []
+    order = S.node(dag, check=_node_check_via_model(dag, expected))
+    assert order == expected
+    assert D.validate_order(dag, order) is None
+
+
+def test_node_choice_on_workload_prefix():
+    wl = synth.make_workload("tiny", seed=1)
+    dag, _ = D.build_from_workload(wl)
+    expected = []
+    assert S.node(dag, check=_node_check_via_model(dag, expected)) == expected
+
+
+def test_planted_node_gain_mistake_caught(monkeypatch):
+    """Plant a plausible bug (the output size counted with the wrong sign)
+    and check that the model-based pin catches it."""
+    orig = S.node_gain
+
+    def buggy(dag, u, resident, pending):
+        g = orig(dag, u, resident, pending)
+        return g + 2 * dag.size(u) if dag.nodes[u].parents else g
+    monkeypatch.setattr(S, "node_gain", buggy)
+    caught = 0
+    for seed in range(10):
+        lt, leaves, contr = random_spec(3000 + seed, n_leaves=6, n_contr=14, share=0.6)
+        dag = D.from_spec(lt, leaves, contr)
+        expected = []
+        if S.node(dag, check=_node_check_via_model(dag, expected)) != expected:
+            caught += 1
+    assert caught > 0

@@ -61,7 +61,18 @@ typedef enum {
 typedef enum {
   LQC_SCHED_NAIVE_TOPO = 0, /* non-leaf nodes in ascending id             */
   LQC_SCHED_TREE = 1,       /* tree scheduler, Alg. 4-8 (Sec. III-B)      */
-  LQC_SCHED_SIBLING = 2     /* sibling scheduler, Alg. 1-3 (Sec. III-A)   */
+  LQC_SCHED_SIBLING = 2,    /* sibling scheduler, Alg. 1-3 (Sec. III-A)   */
+  LQC_SCHED_NODE = 3,       /* node-based gain scheduler (Sec. VI names it
+                               as future work): each step the available
+                               contraction whose processing lowers the
+                               resident memory of Sec. II-C the most
+                               (released inputs - loaded leaves - output,
+                               no output for a root); ties to smallest id */
+  LQC_SCHED_RSGS = 4        /* trees ordered by similarity (Sec. II-A,
+                               Redstar): first tree, then the unprocessed
+                               tree sharing the most contractions with the
+                               last one (ties to the smallest index); each
+                               tree's new contractions in post-order       */
 } lqc_policy;
 
 typedef enum {

@@ -219,6 +219,8 @@ int lqc_dag_schedule(lqc_dag* h, lqc_policy policy, lqc_evict evict, uint64_t bu
     case LQC_SCHED_NAIVE_TOPO: order = lqc::schedule_naive(g); break;
     case LQC_SCHED_TREE: order = lqc::schedule_tree(g); break;
     case LQC_SCHED_SIBLING: order = lqc::schedule_sibling(g); break;
+    case LQC_SCHED_NODE: order = lqc::schedule_node(g); break;
+    case LQC_SCHED_RSGS: order = lqc::schedule_rsgs(g); break;
     default: return fail(h, LQC_ERR_ARG, "unknown scheduling policy");
   }
   return finish_schedule(h, std::move(order), evict, budget_bytes, planned);

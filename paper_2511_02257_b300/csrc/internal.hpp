@@ -85,6 +85,8 @@ struct Dag {
 std::vector<int64_t> schedule_naive(const Dag& g);
 std::vector<int64_t> schedule_sibling(const Dag& g);
 std::vector<int64_t> schedule_tree(const Dag& g);
+std::vector<int64_t> schedule_node(const Dag& g);
+std::vector<int64_t> schedule_rsgs(const Dag& g);
 
 // ---- planner (plan.cpp): returns false and sets g.err on a budget error ----
 bool plan_replay(const Dag& g, const std::vector<int64_t>& order, uint64_t budget,

@@ -15,6 +15,18 @@
 //    nodes of a tree are visited by a post-order walk from its root, left
 //    operand first, skipping nodes (and their sub-trees) that an earlier
 //    tree already processed.
+// Two schedulers the paper only names, with these readings:
+//  * node (Sec. VI, future work: a node-based scheduler using the tree
+//    scheduler's gain concept): each step takes, among the contractions whose
+//    non-leaf inputs are computed, the one whose processing lowers the
+//    resident memory of the model (Sec. II-C) the most: gain = bytes of the
+//    inputs it releases (their last pending consumer) - bytes of the leaves
+//    it loads - its output bytes (none for a root); ties to the smallest id.
+//  * rsgs (Sec. II-A, Redstar's trees sorted by similarity): the first tree
+//    (smallest root id), then repeatedly the unprocessed tree sharing the
+//    most contractions with the tree processed last (ties to the smallest
+//    index); each tree's not yet processed contractions in the same
+//    post-order walk as the tree scheduler's.
 #include <pthread.h>
 
 #include <algorithm>
@@ -361,6 +373,127 @@ struct TreeSched {
 };
 
 }  // namespace
+
+// ------------------------------------------------------------------- node
+std::vector<int64_t> schedule_node(const Dag& g) {
+  const int64_t N = (int64_t)g.nodes.size();
+  std::vector<int64_t> pending(N), missing(N, 0), version(N, 0), order;
+  std::vector<uint8_t> resident(N, 0), done(N, 0);
+  for (int64_t u = 0; u < N; ++u) {
+    const Node& n = g.nodes[u];
+    pending[u] = (int64_t)n.parents.size();
+    for (int k = 0; k < n.n_children(); ++k)
+      if (!g.nodes[n.child(k)].is_leaf()) ++missing[u];
+  }
+  auto gain = [&](int64_t u) {
+    const Node& n = g.nodes[u];
+    int64_t v = 0;
+    for (int k = 0; k < n.n_children(); ++k) {
+      const int64_t x = n.child(k);
+      if (g.nodes[x].is_leaf() && !resident[x]) v -= g.size_bytes(x);
+      if (pending[x] == 1) v += g.size_bytes(x);
+    }
+    if (!n.parents.empty()) v -= g.size_bytes(u);
+    return v;
+  };
+  struct Ent {
+    int64_t gain, id, ver;
+    bool operator<(const Ent& o) const {  // max gain first, then smallest id
+      return gain != o.gain ? gain < o.gain : id > o.id;
+    }
+  };
+  std::priority_queue<Ent> heap;
+  auto push = [&](int64_t u) { heap.push(Ent{gain(u), u, ++version[u]}); };
+  for (int64_t u = 0; u < N; ++u)
+    if (!g.nodes[u].is_leaf() && missing[u] == 0) push(u);
+  // a node's gain changes only when one of its children changes residency
+  // or reaches one pending consumer: re-key the available parents
+  auto rekey_parents = [&](int64_t x) {
+    for (int64_t p : g.nodes[x].parents)
+      if (!done[p] && missing[p] == 0) push(p);
+  };
+  while (!heap.empty()) {
+    const Ent e = heap.top();
+    heap.pop();
+    if (done[e.id] || e.ver != version[e.id]) continue;  // stale entry
+    const int64_t u = e.id;
+    const Node& n = g.nodes[u];
+    done[u] = 1;
+    order.push_back(u);
+    for (int k = 0; k < n.n_children(); ++k) {
+      const int64_t x = n.child(k);
+      const bool was_resident = resident[x];
+      if (g.nodes[x].is_leaf()) resident[x] = 1;
+      if (--pending[x] == 0) resident[x] = 0;
+      if ((g.nodes[x].is_leaf() && !was_resident) || pending[x] == 1) rekey_parents(x);
+    }
+    if (!n.parents.empty()) resident[u] = 1;
+    for (int64_t p : n.parents)
+      if (--missing[p] == 0 && !done[p]) push(p);
+  }
+  return order;
+}
+
+// ------------------------------------------------------------------- rsgs
+std::vector<int64_t> schedule_rsgs(const Dag& g) {
+  const int64_t N = (int64_t)g.nodes.size();
+  std::vector<int64_t> roots;
+  for (int64_t u = 0; u < N; ++u)
+    if (!g.nodes[u].is_leaf() && g.nodes[u].parents.empty()) roots.push_back(u);
+  const int64_t K = (int64_t)roots.size();
+  // trees containing each contraction (descendant closures of the roots)
+  std::vector<std::vector<int32_t>> trees_of(N);
+  std::vector<int64_t> stamp(N, -1), stack;
+  for (int64_t i = 0; i < K; ++i) {
+    stack.assign(1, roots[i]);
+    while (!stack.empty()) {
+      const int64_t u = stack.back();
+      stack.pop_back();
+      if (stamp[u] == i || g.nodes[u].is_leaf()) continue;
+      stamp[u] = i;
+      trees_of[u].push_back((int32_t)i);
+      for (int k = 0; k < g.nodes[u].n_children(); ++k) stack.push_back(g.nodes[u].child(k));
+    }
+  }
+  std::vector<uint8_t> done(N, 0), used(K, 0);
+  std::vector<int64_t> order, shared(K, 0);
+  std::vector<std::pair<int64_t, bool>> walk;
+  int64_t cur = K ? 0 : -1;
+  while (cur >= 0) {
+    used[cur] = 1;
+    walk.assign(1, {roots[cur], false});  // post-order, left operand first
+    while (!walk.empty()) {
+      auto [u, expanded] = walk.back();
+      walk.pop_back();
+      const Node& n = g.nodes[u];
+      if (n.is_leaf() || done[u]) continue;
+      if (expanded) {
+        done[u] = 1;
+        order.push_back(u);
+        continue;
+      }
+      walk.push_back({u, true});
+      for (int k = n.n_children() - 1; k >= 0; --k) walk.push_back({n.child(k), false});
+    }
+    // contractions shared by the tree just processed and every other tree
+    std::fill(shared.begin(), shared.end(), 0);
+    std::fill(stamp.begin(), stamp.end(), -1);
+    stack.assign(1, roots[cur]);
+    while (!stack.empty()) {
+      const int64_t u = stack.back();
+      stack.pop_back();
+      if (stamp[u] == cur || g.nodes[u].is_leaf()) continue;
+      stamp[u] = cur;
+      for (int32_t j : trees_of[u]) ++shared[j];
+      for (int k = 0; k < g.nodes[u].n_children(); ++k) stack.push_back(g.nodes[u].child(k));
+    }
+    int64_t best = -1;
+    for (int64_t j = 0; j < K; ++j)
+      if (!used[j] && (best < 0 || shared[j] > shared[best])) best = j;
+    cur = best;
+  }
+  return order;
+}
 
 std::vector<int64_t> schedule_tree(const Dag& g) {
   TreeSched t(g);

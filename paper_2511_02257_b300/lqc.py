@@ -30,12 +30,14 @@ c_vp = ctypes.c_void_p
 LQC_OK, LQC_ERR_ARG, LQC_ERR_BUDGET, LQC_ERR_CUDA = 0, -1, -2, -3
 LQC_ERR_HOST_MEM, LQC_ERR_STATE, LQC_ERR_TIMEOUT = -4, -5, -6
 LQC_SCHED_NAIVE_TOPO, LQC_SCHED_TREE, LQC_SCHED_SIBLING = 0, 1, 2
+LQC_SCHED_NODE, LQC_SCHED_RSGS = 3, 4
 LQC_EVICT_LRU, LQC_EVICT_NEXT_USE = 0, 1
 LQC_PREC_FP64, LQC_PREC_TF32X3, LQC_PREC_BF16X3 = 0, 1, 2
 LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING, LQC_OPT_WINDOW = 1, 2, 3, 4
 LQC_OPT_FUSED_MAX_N, LQC_OPT_SPLIT_POLICY = 5, 6
 OP_NAMES = {0: "LOAD", 1: "EVICT", 2: "CONTRACT", 3: "FREE"}
-POLICIES = {"naive": LQC_SCHED_NAIVE_TOPO, "tree": LQC_SCHED_TREE, "sibling": LQC_SCHED_SIBLING}
+POLICIES = {"naive": LQC_SCHED_NAIVE_TOPO, "tree": LQC_SCHED_TREE, "sibling": LQC_SCHED_SIBLING,
+            "node": LQC_SCHED_NODE, "rsgs": LQC_SCHED_RSGS}
 EVICTS = {"lru": LQC_EVICT_LRU, "next_use": LQC_EVICT_NEXT_USE}
 PRECISIONS = {"fp64": LQC_PREC_FP64, "tf32x3": LQC_PREC_TF32X3, "bf16x3": LQC_PREC_BF16X3}
 

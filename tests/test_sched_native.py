@@ -20,7 +20,7 @@ from tests.dagutil import random_spec
 
 L = pytest.importorskip("paper_2511_02257_b300")
 
-POL = {"naive": "naive", "sibling": "sibling", "tree": "tree"}
+POL = {"naive": "naive", "sibling": "sibling", "tree": "tree", "node": "node", "rsgs": "rsgs"}
 EV = {M.LRU: "lru", M.NEXT_USE: "next_use"}
 STAT_KEYS = ("peak_paper", "peak_exec", "n_evict", "n_h2d", "n_d2h", "h2d_bytes", "d2h_bytes")
 
@@ -65,7 +65,7 @@ def test_dedup_ids_match_oracle(seed):
 
 
 @pytest.mark.parametrize("seed", range(40))
-@pytest.mark.parametrize("sched", ["naive", "sibling", "tree"])
+@pytest.mark.parametrize("sched", ["naive", "sibling", "tree", "node", "rsgs"])
 def test_orders_bit_exact_random(seed, sched):
     lt, leaves, contr = random_spec(500 + seed, n_leaves=6, n_contr=16, share=0.7)
     od = D.from_spec(lt, leaves, contr)
@@ -81,7 +81,7 @@ def test_orders_and_plans_bit_exact_workloads(name):
     nd, ids = L.build_dag(wl, with_data=False)
     assert nd.num_nodes() == len(od.nodes)
     budget = wl.budget_bytes or None
-    for sched in ("naive", "sibling", "tree"):
+    for sched in ("naive", "sibling", "tree", "node", "rsgs"):
         order = S.SCHEDULERS[sched](od)
         for pol in (M.LRU, M.NEXT_USE):
             st = nd.schedule(POL[sched], EV[pol], budget or 0)
@@ -137,6 +137,9 @@ def test_table1_schedules_native():
     assert [names[u] for u in nd.order()] == h["sibling"]["order"]
     nd.schedule("tree")
     assert [names[u] for u in nd.order()] == h["tree"]["order"]
+    for sched in ("node", "rsgs"):
+        nd.schedule(sched)
+        assert [names[u] for u in nd.order()] == h[sched]["order"]
 
 
 def test_argument_errors():

@@ -507,13 +507,16 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           *reinterpret_cast<float4*>(bl + o1) = make_float4(-l[1], l[0], -l[3], l[2]);
         };
         if (tk->b_mn) {
-          // raw tile [16 k][kBN/2 n] complex: consecutive threads take
-          // consecutive n (conflict-free reads), the transpose happens in the
-          // writes to the K-major operand rows
+          // raw tile [16 k][kBN/2 n] complex.  A warp takes 16 consecutive n
+          // at two chunks c, c ^ 1: each half-warp reads 128 contiguous bytes,
+          // and the B' rows' swizzled writes cover all 8 chunk positions
+          // (bank-conflict-free); unit bits: n = [3:0] + 16*[6:5], c = 2*[8:7]
+          // + [4]
+          static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
           const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
 #pragma unroll 2
           for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
-            const int n = it % (kBN / 2), c = it / (kBN / 2);
+            const int n = (it & 15) + 16 * ((it >> 5) & 3), c = 2 * (it >> 7) + ((it >> 4) & 1);
             const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
             emit(n, c, make_float4(v0.x, v0.y, v1.x, v1.y));
           }

@@ -33,9 +33,15 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture (None
-# until captured for the current kernel build; see profiles/).
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of the dominant FP64 kernel from one
+# ncu capture of the default workload: 300 launches of k_contract_fp64<1,1>,
+# the 64x64x64 x Lt 64 contraction that makes 86 % of its launches (reads
+# its two 4.2 MB inputs once; the output stays in L2).  Algorithmic bytes of
+# that launch: 12.58 MB.
+TRAFFIC_PER_LAUNCH = 8.34e6
+TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of 300 launches of "
+                "k_contract_fp64<1,1> (64x64x64 x Lt 64, 86 % of the launches); algorithmic "
+                "12.58 MB per such launch")
 
 
 def parse():
@@ -426,7 +432,7 @@ def main():
                     "peak_source": "nominal B300 FP64 rate (profiling recipe table)",
                     "fma_probe_tflops": probe,
                     "frac_of_probe": achieved / probe if achieved else None,
-                    "traffic": TRAFFIC_PER_LAUNCH}
+                    "traffic": TRAFFIC_PER_LAUNCH, "traffic_note": TRAFFIC_NOTE}
     else:
         # split products: 3 real-embedded GEMMs per complex contraction, each
         # 8 real flops per complex multiply-add (windows time whole levels,

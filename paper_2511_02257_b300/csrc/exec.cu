@@ -267,9 +267,24 @@ int build_program(Dag& g) {
   Placer pl;
   int64_t scratch_need = 0, mscratch_need = 0;
   std::vector<Instr>& P = x.prog;
-  // grouped windows: mixed precisions, plans without evictions
   bool evicts = false;
   for (const Op& op : g.ops) evicts = evicts || op.kind == OP_EVICT;
+  // leaf region: when the plan evicts nothing and the budget has room, each
+  // leaf gets bytes of its own at the bottom of the arena that no other
+  // tensor reuses, so its H2D load waits for no kernel and the copy stream
+  // runs ahead of the compute stream (loads keep their first-use order)
+  std::vector<int64_t> leaf_slot(N, -1);
+  if (!staged && !evicts) {
+    int64_t total = 0;
+    for (const Op& op : g.ops)
+      if (op.kind == OP_LOAD && g.nodes[op.node].is_leaf() && leaf_slot[op.node] < 0) {
+        leaf_slot[op.node] = total;
+        total += (g.size_bytes(op.node) + 255) & ~int64_t(255);
+      }
+    if (g.budget == 0 || g.planned.peak_exec + total <= (int64_t)g.budget) pl.top = total;
+    else std::fill(leaf_slot.begin(), leaf_slot.end(), -1);
+  }
+  // grouped windows: mixed precisions, plans without evictions
   const int W = (g.prec != LQC_PREC_FP64 && g.opt_window > 1 && !evicts) ? (int)g.opt_window : 0;
   std::vector<int32_t> win;            // open window: member instructions
   std::vector<int64_t> win_free;       // frees deferred to the window's end
@@ -302,7 +317,7 @@ int build_program(Dag& g) {
       x.mdesc.emplace_back();
       dep[S_COMPUTE] = (int32_t)P.size() - 1;
     }
-    pl.release(off[u], g.size_bytes(u), dep);
+    if (leaf_slot[u] < 0) pl.release(off[u], g.size_bytes(u), dep);
     off[u] = -1;
   };
   auto member_need = [&](int32_t j) -> int64_t {
@@ -364,9 +379,13 @@ int build_program(Dag& g) {
       in.bytes = g.size_bytes(u);
       in.src[0] = in.src[1] = -1;
       int32_t dep[3];
-      in.dst = pl.alloc(in.bytes, dep);
-      add_wait(in, dep[S_COMPUTE]);
-      add_wait(in, dep[S_D2H]);
+      if (leaf_slot[u] >= 0) {
+        in.dst = leaf_slot[u];  // own bytes: nothing to wait for
+      } else {
+        in.dst = pl.alloc(in.bytes, dep);
+        add_wait(in, dep[S_COMPUTE]);
+        add_wait(in, dep[S_D2H]);
+      }
       if (!n.is_leaf()) {
         add_wait(in, wb_instr[u]);  // reload after the write-back landed
         in.src[0] = hoff[u];        // host offset of the copy

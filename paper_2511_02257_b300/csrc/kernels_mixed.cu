@@ -799,10 +799,11 @@ k_permute_c64(const float2* __restrict__ src, float2* __restrict__ dst, const Pe
 // partial sum of block b of slice t of one correlator, r(t) = sum_e A[e] *
 // B[src(e)] with the destination order of `d` = the left operand's order;
 // fixed reduction order, so every launch form gives the same bits.  Runs
-// (mode 0) go through perm_visit; transposed pairs (mode 1) take kCaTiles
-// 32x32 tiles per block, both operands' tiles staged through shared memory
-// with coalesced reads (A along X, B along its unit-stride axis Y).
-constexpr int kCaTiles = 4;
+// (mode 0) go through perm_visit; transposed pairs (mode 1) without shared
+// memory: each warp sums one 32x32 tile, A read along X (coalesced), B
+// along its unit-stride axis Y per lane (each lane's lines stay in L1
+// across the tile's 32 rows), kCaWarpTiles tiles per block.
+constexpr int kCaWarpTiles = 8;
 
 __device__ __forceinline__ void ca_acc(float& rh, float& rl, float& ih, float& il, float2 a,
                                        float2 bv) {
@@ -816,7 +817,7 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
                                                  const float2* __restrict__ B,
                                                  double2* __restrict__ part, const PermDesc& d,
                                                  long long t, unsigned b) {
-  __shared__ __align__(16) unsigned char smem[2 * 32 * 33 * 8];  // >= (kPermElems + 1) * 4
+  __shared__ __align__(16) unsigned char smem[(kPermElems + 1) * 4];
   A += t * d.n;
   B += t * d.src_ts;
   // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
@@ -826,35 +827,26 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
     perm_visit(d, B, b, smem, [&](unsigned e) { return A[e]; },
                [&](unsigned, float2 bv, float2 a) { ca_acc(rh, rl, ih, il, a, bv); });
   } else {
-    float2 (*sa)[33] = reinterpret_cast<float2 (*)[33]>(smem);            // [y][x]
-    float2 (*sb)[33] = reinterpret_cast<float2 (*)[33]>(smem + 32 * 33 * 8);  // [x][y]
     const unsigned X = (unsigned)d.X, Y = (unsigned)d.Y;
     const unsigned xb = (X + 31) / 32, yb = (Y + 31) / 32;
-    const unsigned ntile = (unsigned)d.outer * xb * yb;
-    const unsigned tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const unsigned sX = (unsigned)d.sX, dY = (unsigned)d.dY;
-    for (int q = 0; q < kCaTiles; ++q) {
-      const unsigned tile = b * kCaTiles + q;
-      if (tile >= ntile) break;  // uniform across the block
+    const unsigned tile = b * kCaWarpTiles + (threadIdx.x >> 5);
+    const unsigned lane = threadIdx.x & 31;
+    if (tile < (unsigned)d.outer * xb * yb) {
       const unsigned o = tile / (xb * yb), rem = tile - o * (xb * yb);
-      const unsigned x0 = (rem % xb) * 32, y0 = (rem / xb) * 32;
+      const unsigned x = (rem % xb) * 32 + lane, y0 = (rem / xb) * 32;
       unsigned dso;
       const unsigned so = perm_outer(d, o, &dso);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const unsigned r = ty + 8 * j;
-        const unsigned xa = x0 + tx, ya = y0 + r;  // A along X
-        sa[r][tx] = (xa < X && ya < Y) ? A[dso + ya * dY + xa] : make_float2(0.f, 0.f);
-        const unsigned yb_ = y0 + tx, xb_ = x0 + r;  // B along Y
-        sb[r][tx] = (xb_ < X && yb_ < Y) ? B[so + yb_ + xb_ * sX] : make_float2(0.f, 0.f);
+      if (x < X) {
+        const float2* a = A + dso + x;
+        const float2* bp = B + so + x * (unsigned)d.sX;
+        const unsigned dY = (unsigned)d.dY;
+        const unsigned ny = min(32u, Y - y0);
+#pragma unroll 8
+        for (unsigned yy = 0; yy < ny; ++yy) {
+          const unsigned y = y0 + yy;
+          ca_acc(rh, rl, ih, il, a[y * dY], bp[y]);
+        }
       }
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const unsigned r = ty + 8 * j;  // element (x = x0 + tx, y = y0 + r)
-        ca_acc(rh, rl, ih, il, sa[r][tx], sb[tx][r]);
-      }
-      __syncthreads();
     }
   }
   double re = (double)rh + (double)rl, im = (double)ih + (double)il;
@@ -1438,8 +1430,9 @@ namespace {
 PermDesc ca_perm(const ContractAllDesc& d) {
   PermDesc pd;
   make_perm_desc(d.bp, d.lt, d.S, &pd);
-  if (pd.mode == 1)  // 32x32 tile pairs, kCaTiles per block
-    pd.blocks = (pd.outer * ((pd.X + 31) / 32) * ((pd.Y + 31) / 32) + kCaTiles - 1) / kCaTiles;
+  if (pd.mode == 1)  // warp tiles of 32x32, kCaWarpTiles per block
+    pd.blocks = (pd.outer * ((pd.X + 31) / 32) * ((pd.Y + 31) / 32) + kCaWarpTiles - 1) /
+                kCaWarpTiles;
   return pd;
 }
 int64_t ca_part_bytes(const PermDesc& pd) {

@@ -132,7 +132,9 @@ typedef enum {
   LQC_OPT_WINDOW = 4,     /* mixed precisions, plans without evictions: run up
                              to this many consecutive contractions of the order
                              as one grouped window (frees deferred to its end;
-                             each dependency level a few grouped launches).
+                             each dependency level a few grouped launches; a
+                             window also closes before its deferred frees
+                             would take the arena past the budget).
                              0 or 1 = one contraction at a time; default 64.
                              Timing then covers whole windows              */
   LQC_OPT_FUSED_MAX_N = 5, /* TF32X3: right operands of at most this many
@@ -255,12 +257,12 @@ int lqc_dag_execute(lqc_dag* dag, void* stream);
 /* Autotuner of the mixed precisions (no counterpart in the paper: the
  * batching form's tile and grouping choices).  After lqc_dag_schedule, with
  * leaf data given (or staged): for every candidate of LQC_OPT_WINDOW in
- * {0, 64, 256} (windows only when the plan evicts nothing) x
+ * {0, 64, 512, 4096} (windows only when the plan evicts nothing) x
  * LQC_OPT_FUSED_MAX_N in {0, 64, 2^30} (TF32X3 only) x LQC_OPT_SPLIT_POLICY
  * in {0, 1}, runs one execute that builds the program, then times `reps`
  * executes on `stream` with CUDA events; sets the three options to the
  * fastest candidate.  entries (nullable; capacity cap) receive every
- * candidate with its time, *n their count (at most 18).  Correlators of
+ * candidate with its time, *n their count (at most 24).  Correlators of
  * every candidate agree within the mixed tolerance; the chosen options stay
  * in effect for later executes.  Errors: LQC_ERR_STATE (not scheduled, leaf
  * without data), LQC_ERR_ARG (FP64 DAG, reps outside [1, 1000], cap too

@@ -432,6 +432,13 @@ int build_program(Dag& g) {
       }
       release(u);
     } else {  // CONTRACT
+      // a window holds at most W contractions, and closes (releasing its
+      // deferred frees) before its arena would outgrow the budget
+      if (W > 0 && !win.empty() &&
+          ((int64_t)win.size() >= W ||
+           (g.budget > 0 && n.rank != 0 &&
+            pl.top + ((g.size_bytes(u) + 255) & ~int64_t(255)) > (int64_t)g.budget)))
+        flush();
       Instr in{};
       in.stream = S_COMPUTE;
       in.node = u;
@@ -838,7 +845,7 @@ int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64
                   int64_t* n) {
   std::vector<lqc_tune_entry> cand;
   const bool windows_ok = g.planned.n_evict == 0;
-  for (int64_t w : {int64_t(0), int64_t(64), int64_t(256)}) {
+  for (int64_t w : {int64_t(0), int64_t(64), int64_t(512), int64_t(4096)}) {
     if (w && !windows_ok) continue;
     for (int64_t f : {int64_t(0), int64_t(64), int64_t(1) << 30}) {
       if (g.prec == LQC_PREC_BF16X3 && f) continue;  // no fused form for BF16

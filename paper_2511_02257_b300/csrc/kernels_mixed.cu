@@ -455,7 +455,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         }
       }
     }
-  } else if (FUSED) {
+  } else if constexpr (FUSED) {
     // ---- converter warps: raw complex64 tiles -> hi/lo operand tiles
     const int ct = threadIdx.x - 32 * (2 + kDrainWarps);  // 0 .. 32*kConvWarps-1
     constexpr int kCT = 32 * kConvWarps;

@@ -200,6 +200,7 @@ def test_grouped_windows_bit_identical_to_single_launches(precision):
     for w in (64, 7):
         assert np.array_equal(out[w].view(np.float64), out[0].view(np.float64)), w
     assert kernels[64] * 4 < kernels[0]
+    assert kernels[64] < kernels[7] < kernels[0]     # windows hold at most W contractions
 
 
 @pytest.mark.parametrize("case", [((16, 16), (16, 16), (0, 1), (1, 0)),

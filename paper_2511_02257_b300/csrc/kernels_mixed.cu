@@ -475,10 +475,55 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         if (!ok) break;
         const uint8_t* rp = raw + r * C::kRawBytes;
         uint8_t* sp = smem + st * C::kStageBytes;
+        // Every raw load of this thread's units is issued first (A: 16-byte
+        // chunks, B: one complex k pair of one column each), then the splits
+        // and stores: the loads overlap instead of one unit's round trip after
+        // another.
+        constexpr int kUA = (C::kRawA / 16 + kCT - 1) / kCT;  // A units per thread
+        constexpr int kUB = ((kBN / 2) * 8 + kCT - 1) / kCT;  // B units per thread
+        static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
+        float4 va[kUA], vb[kUB];
+#pragma unroll
+        for (int j = 0; j < kUA; ++j) {
+          const int c = ct + j * kCT;
+          if (c < C::kRawA / 16) va[j] = *reinterpret_cast<const float4*>(rp + 16 * c);
+        }
+        // B unit it -> (column n, chunk c).  [k][n] tiles: a warp takes 16
+        // consecutive n at two chunks c, c ^ 1 (each half-warp reads 128
+        // contiguous bytes; the B' rows' swizzled writes cover all 8 chunk
+        // positions): n = [3:0] + 16*[6:5], c = 2*[8:7] + [4].  K-major tiles:
+        // n = it / 8, c = it % 8.
+        const bool bmn = tk->b_mn != 0;
+        const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
+        auto unit = [&](int it, int& n, int& c) {
+          if (bmn) {
+            n = (it & 15) + 16 * ((it >> 5) & 3);
+            c = 2 * (it >> 7) + ((it >> 4) & 1);
+          } else {
+            n = it >> 3;
+            c = it & 7;
+          }
+        };
+#pragma unroll
+        for (int j = 0; j < kUB; ++j) {
+          const int it = ct + j * kCT;
+          if (it < (kBN / 2) * 8) {
+            int n, c;
+            unit(it, n, c);
+            if (bmn) {  // complex (k, n) at k = 2c and 2c + 1
+              const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
+              vb[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
+            } else {
+              vb[j] = *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 + 16 * (c ^ (n & 7)));
+            }
+          }
+        }
         // A: same 128-byte-swizzled layout in and out, element by element
-#pragma unroll 4
-        for (int c = ct; c < C::kRawA / 16; c += kCT) {
-          const float4 v = *reinterpret_cast<const float4*>(rp + 16 * c);
+#pragma unroll
+        for (int j = 0; j < kUA; ++j) {
+          const int c = ct + j * kCT;
+          if (c >= C::kRawA / 16) continue;
+          const float4 v = va[j];
           float h0, l0, h1, l1, h2, l2, h3, l3;
           Split<false>::split(v.x, h0, l0);
           Split<false>::split(v.y, h1, l1);
@@ -487,10 +532,16 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           *reinterpret_cast<float4*>(sp + 16 * c) = make_float4(h0, h1, h2, h3);
           *reinterpret_cast<float4*>(sp + C::kATile + 16 * c) = make_float4(l0, l1, l2, l3);
         }
-        // B: complex row n -> B' rows 2n (re, -im) and 2n+1 (im, re); 16-byte
-        // chunk c (complex k 2c, 2c+1) of row r sits at chunk c ^ (r & 7)
-        // (128-byte swizzle).  v = (re, im) at k = 2c, then at 2c + 1.
-        auto emit = [&](int n, int c, float4 v) {
+        // B: complex column n -> B' rows 2n (re, -im) and 2n+1 (im, re); the
+        // 16-byte chunk c (complex k 2c, 2c+1) of row r sits at chunk
+        // c ^ (r & 7) (128-byte swizzle)
+#pragma unroll
+        for (int j = 0; j < kUB; ++j) {
+          const int it = ct + j * kCT;
+          if (it >= (kBN / 2) * 8) continue;
+          int n, c;
+          unit(it, n, c);
+          const float4 v = vb[j];
           const int r0 = 2 * n, r1 = 2 * n + 1;
           const int o0 = r0 * 128 + 16 * (c ^ (r0 & 7)), o1 = r1 * 128 + 16 * (c ^ (r1 & 7));
           float h[4], l[4];
@@ -505,28 +556,6 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           // row 2n+1 = (im, re): the same split parts, re-paired
           *reinterpret_cast<float4*>(bh + o1) = make_float4(-h[1], h[0], -h[3], h[2]);
           *reinterpret_cast<float4*>(bl + o1) = make_float4(-l[1], l[0], -l[3], l[2]);
-        };
-        if (tk->b_mn) {
-          // raw tile [16 k][kBN/2 n] complex.  A warp takes 16 consecutive n
-          // at two chunks c, c ^ 1: each half-warp reads 128 contiguous bytes,
-          // and the B' rows' swizzled writes cover all 8 chunk positions
-          // (bank-conflict-free); unit bits: n = [3:0] + 16*[6:5], c = 2*[8:7]
-          // + [4]
-          static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
-          const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
-#pragma unroll 2
-          for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
-            const int n = (it & 15) + 16 * ((it >> 5) & 3), c = 2 * (it >> 7) + ((it >> 4) & 1);
-            const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
-            emit(n, c, make_float4(v0.x, v0.y, v1.x, v1.y));
-          }
-        } else {
-#pragma unroll 2
-          for (int it = ct; it < (kBN / 2) * 8; it += kCT) {
-            const int n = it >> 3, c = it & 7;
-            emit(n, c, *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 +
-                                                         16 * (c ^ (n & 7))));
-          }
         }
         // generic-proxy writes -> visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

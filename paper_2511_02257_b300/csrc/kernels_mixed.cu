@@ -464,9 +464,9 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
       const GemmTask* tk = tile_task(gp, tile, k, local);
       for (int i = 0; i < tk->kblocks; ++i, ++g) {
         const int r = g % R, st = g % S;
+        // the raw tile first: its loads overlap the wait for a free operand stage
         if (lane == 0) {
-          if (!mbar_wait(&rfull[r], (uint32_t)(g / R) & 1u) ||
-              !mbar_wait(&empty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
+          if (!mbar_wait(&rfull[r], (uint32_t)(g / R) & 1u) || *abort_flag) {
             *abort_flag = 1;
             ok = 0;
           }
@@ -518,6 +518,14 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             }
           }
         }
+        if (lane == 0) {
+          if (!mbar_wait(&empty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
         // A: same 128-byte-swizzled layout in and out, element by element
 #pragma unroll
         for (int j = 0; j < kUA; ++j) {

@@ -233,8 +233,11 @@ struct GemmCfg {
   static constexpr int kRawA = kBM * 128, kRawB = (kBN / 2) * 128;
   static constexpr int kRawBytes = kRawA + kRawB;
   static constexpr int kThreads = kGemmThreads + (FUSED ? 32 * kConvWarps : 0);
+  // epilogue staging: per drain warp 32 rows x 16 columns, pitch 20 floats
+  static constexpr int kStgPitch = 20;
+  static constexpr int kStgBytes = kDrainWarps * 32 * kStgPitch * 4;
   static constexpr int kSmem = kOpStages * kStageBytes + kRawStages * kRawBytes +
-                               1024 /* align */ + 256 /* barriers */;
+                               1024 /* align */ + 256 /* barriers */ + kStgBytes;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -270,6 +273,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
   uint64_t* rempty = rfull + R;        // FUSED [R] raw stage converted
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* stage_out = reinterpret_cast<float*>(raw + R * C::kRawBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -440,18 +444,41 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      if (ok && row < M) {
-        float* dst = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr + (size_t)row * Nr;
-        const int col = tn * kBN + c0;
-        if (col + kHalf <= Nr && (Nr & 3) == 0) {
-          float4* d4 = reinterpret_cast<float4*>(dst + col);
+      if (ok) {  // warp-uniform: the staging below is collective
+        // each thread holds one row of the tile; 16 columns at a time go
+        // through this warp's shared-memory pitch so that a store covers 8 rows
+        // x 64 contiguous bytes instead of 32 rows x 16 bytes
+        float* stg = stage_out + (warp - 2) * (32 * C::kStgPitch);
+        float* base = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr;
+        const int row0 = tm * kBM + q * 32, col0 = tn * kBN + c0;
+        const bool vec = (Nr & 3) == 0;
+        (void)row;
 #pragma unroll
-          for (int u = 0; u < kHalf / 4; ++u)
-            d4[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
-        } else {
+        for (int j = 0; j < kHalf; j += 16) {
+          float4* w = reinterpret_cast<float4*>(stg + lane * C::kStgPitch);
 #pragma unroll
-          for (int u = 0; u < kHalf; ++u)
-            if (col + u < Nr) dst[col + u] = acc[u];
+          for (int u = 0; u < 4; ++u)
+            w[u] = make_float4(acc[j + 4 * u], acc[j + 4 * u + 1], acc[j + 4 * u + 2],
+                               acc[j + 4 * u + 3]);
+          __syncwarp();
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int rr = (lane >> 2) + 8 * p, cc = (lane & 3) * 4;
+            const float4 v = *reinterpret_cast<const float4*>(stg + rr * C::kStgPitch + cc);
+            const int orow = row0 + rr, col = col0 + j + cc;
+            if (orow < M) {
+              float* d = base + (size_t)orow * Nr + col;
+              if (vec && col + 4 <= Nr) {
+                *reinterpret_cast<float4*>(d) = v;
+              } else {
+                if (col < Nr) d[0] = v.x;
+                if (col + 1 < Nr) d[1] = v.y;
+                if (col + 2 < Nr) d[2] = v.z;
+                if (col + 3 < Nr) d[3] = v.w;
+              }
+            }
+          }
+          __syncwarp();
         }
       }
     }

@@ -905,10 +905,22 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
         const float2* bp = B + so + x * (unsigned)d.sX;
         const unsigned dY = (unsigned)d.dY;
         const unsigned ny = min(32u, Y - y0);
+        if (((so | (unsigned)d.sX) & 1u) == 0 && (ny & 1u) == 0) {
+          // B 16-byte aligned along y (y0 is a multiple of 32): two complex
+          // values per load, the same summation order
+#pragma unroll 4
+          for (unsigned yy = 0; yy < ny; yy += 2) {
+            const unsigned y = y0 + yy;
+            const float4 b2 = *reinterpret_cast<const float4*>(bp + y);
+            ca_acc(rh, rl, ih, il, a[y * dY], make_float2(b2.x, b2.y));
+            ca_acc(rh, rl, ih, il, a[(y + 1) * dY], make_float2(b2.z, b2.w));
+          }
+        } else {
 #pragma unroll 8
-        for (unsigned yy = 0; yy < ny; ++yy) {
-          const unsigned y = y0 + yy;
-          ca_acc(rh, rl, ih, il, a[y * dY], bp[y]);
+          for (unsigned yy = 0; yy < ny; ++yy) {
+            const unsigned y = y0 + yy;
+            ca_acc(rh, rl, ih, il, a[y * dY], bp[y]);
+          }
         }
       }
     }

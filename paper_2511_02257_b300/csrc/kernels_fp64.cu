@@ -288,24 +288,20 @@ bool make_contract_desc(int rank_a, const int64_t* ext_a, int rank_b, const int6
       d->bn.stride[d->bn.n++] = sb[b];
       d->N *= ext_b[b];
     }
-  // paired axes: merge neighbours only where both sides are contiguous
-  int w = 0;
+  // paired axes in pair order (k runs row-major over the pairs); each side
+  // merges the neighbours that are contiguous on that side, so one operand
+  // can be a single k group while the other is not (both still enumerate k
+  // in the same order)
+  d->ak.n = d->bk.n = npairs;
   for (int j = 0; j < npairs; ++j) {
     const int e = (int)ext_a[la[j]];
-    if (w > 0 && d->ak.stride[w - 1] == sa[la[j]] * e && d->bk.stride[w - 1] == sb[ra[j]] * e) {
-      d->ak.ext[w - 1] *= e;
-      d->bk.ext[w - 1] *= e;
-      d->ak.stride[w - 1] = sa[la[j]];
-      d->bk.stride[w - 1] = sb[ra[j]];
-    } else {
-      d->ak.ext[w] = d->bk.ext[w] = e;
-      d->ak.stride[w] = sa[la[j]];
-      d->bk.stride[w] = sb[ra[j]];
-      ++w;
-    }
+    d->ak.ext[j] = d->bk.ext[j] = e;
+    d->ak.stride[j] = sa[la[j]];
+    d->bk.stride[j] = sb[ra[j]];
     d->K *= e;
   }
-  d->ak.n = d->bk.n = w;
+  merge_group(&d->ak);
+  merge_group(&d->bk);
   merge_group(&d->am);
   merge_group(&d->bn);
   d->a_kfast = pa[rank_a - 1] ? 1 : 0;

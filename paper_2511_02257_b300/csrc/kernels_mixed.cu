@@ -98,6 +98,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
 // K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of
 // 1024 B (stride-dimension offset), descriptor version 1, layout SWIZZLE_128B.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -191,7 +199,9 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   CUtensorMap map[4];   // Ahi, Alo, Bhi, Blo
   float* out;           // splits == 1: D' [lt][M][Nr]; else partials [splits][lt][M][Nr]
   int M, Nr, kblocks, splits, lt, ntn, ntm, tiles;
-  int b_mn;             // fused form: B stored [k][n] (n unit-stride), transposed by the converters
+  int b_mn;             // fused form: B stored [k][n] (n unit-stride), transposed by the converters;
+                        // 2: n split into blocks of b_ni columns (an outer free axis)
+  int b_ni;
   long long tile_start;
 };
 
@@ -332,7 +342,10 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
             tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
-            if (tk->b_mn)  // [16 complex k rows][kBN/2 complex n], unswizzled
+            if (tk->b_mn == 2)  // the same tile inside one block of the outer n axis
+              tma_load_4d(rp + C::kRawA, &tk->map[2], &rf[st], n0 % (2 * tk->b_ni), k0 / 2,
+                          n0 / (2 * tk->b_ni), t);
+            else if (tk->b_mn)  // [16 complex k rows][kBN/2 complex n], unswizzled
               tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], n0, k0 / 2, t);
             else
               tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], k0, n0 / 2, t);
@@ -520,7 +533,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         // contiguous bytes; the B' rows' swizzled writes cover all 8 chunk
         // positions): n = [3:0] + 16*[6:5], c = 2*[8:7] + [4].  K-major tiles:
         // n = it / 8, c = it % 8.
-        const bool bmn = tk->b_mn != 0;
+        const bool bmn = tk->b_mn != 0;  // [k][n] raw tile (3-d or 4-d map alike)
         const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
         auto unit = [&](int it, int& n, int& c) {
           if (bmn) {
@@ -1132,6 +1145,24 @@ bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows
   return r == CUDA_SUCCESS;
 }
 
+// [lt][outer][K rows][n2 floats] with the outer n axis of stride outer_stride:
+// boxes of kBN floats x 16 rows inside one outer block
+bool make_raw_map_mn4(CUtensorMap* m, const void* base, int64_t n2, int64_t krows,
+                      int64_t outer, int64_t lt, int64_t row_stride, int64_t outer_stride,
+                      int64_t slice_stride) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)n2, (cuuint64_t)krows, (cuuint64_t)outer, (cuuint64_t)lt};
+  cuuint64_t strides[3] = {(cuuint64_t)(row_stride * 8), (cuuint64_t)(outer_stride * 8),
+                           (cuuint64_t)(slice_stride * 8)};
+  cuuint32_t box[4] = {(cuuint32_t)kBN, 16u, 1u, 1u};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool make_raw_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t lt,
                   int64_t row_stride, int64_t slice_stride, int box_rows) {
   auto fn = encode_fn();
@@ -1244,7 +1275,13 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
   // read in place, k rows of 16-byte multiples, transposed by the converters
   d->b_mn = !d->b_direct && !cd.b_kfast && cd.bn.n == 1 && cd.bn.stride[0] == 1 &&
             cd.bk.n == 1 && cd.bk.stride[0] % 2 == 0 && cd.b_ts % 2 == 0;
-  if (d->b_mn) {
+  // or [k][outer n][inner n] blocks (a propagator contracted over one
+  // distillation axis): one TMA box per tile when the inner n extent is a
+  // multiple of the tile's 64 complex columns
+  d->b_mn2 = !d->b_direct && !d->b_mn && !cd.b_kfast && cd.bn.n == 2 && cd.bn.stride[1] == 1 &&
+             cd.bn.ext[1] % (kBN / 2) == 0 && cd.bn.stride[0] % 2 == 0 && cd.bk.n == 1 &&
+             cd.bk.stride[0] % 2 == 0 && cd.b_ts % 2 == 0;
+  if (d->b_mn || d->b_mn2) {
     d->b_direct = true;
     d->b_rowstride = cd.bk.stride[0];
   }
@@ -1305,10 +1342,17 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
     if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) return false;
-    if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
-               : !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts, kBN / 2))
+    if (d.b_mn2) {
+      if (!make_raw_map_mn4(&t->map[2], b, 2 * cd.bn.ext[1], cd.K, cd.bn.ext[0], cd.lt,
+                            d.b_rowstride, cd.bn.stride[0], bts))
+        return false;
+    } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
+                      : !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts,
+                                      kBN / 2)) {
       return false;
-    t->b_mn = d.b_mn ? 1 : 0;
+    }
+    t->b_mn = d.b_mn2 ? 2 : (d.b_mn ? 1 : 0);
+    t->b_ni = d.b_mn2 ? cd.bn.ext[1] : 0;
   } else if (!make_map(&t->map[0], as, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[1], as + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[2], bs, d.bf16, d.kp, 2 * cd.N, cd.lt) ||

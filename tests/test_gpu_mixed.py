@@ -260,3 +260,27 @@ def test_matrix_product_forms_vs_oracle(mkn, fused, window):
     d.set_option(L.LQC_OPT_WINDOW, window)
     d.execute(torch.cuda.current_stream().cuda_stream)
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
+
+
+@pytest.mark.parametrize("n", [64, 128])
+@pytest.mark.parametrize("window", [0, 64])
+def test_propagator_right_operand_in_place_vs_oracle(n, window):
+    """M . P over P's first distillation axis: P is read in place as [k][spin
+    block][n] by the fused GEMM (one 4-d TMA box per tile), then a correlator
+    of the result; against the oracle."""
+    lt = 2
+    rng = np.random.default_rng(n + window)
+
+    def rnd(*s):
+        return (rng.standard_normal((lt,) + s) + 1j * rng.standard_normal((lt,) + s)) / np.sqrt(n)
+    Mm, Pp, Dd = rnd(n, n), rnd(4, 4, n, n), rnd(n, 4, 4, n)
+    ref = C.contract_pair(C.contract_pair(Mm, Pp, (1,), (2,)), Dd, (0, 1, 2, 3), (0, 1, 2, 3))
+    d = L.Dag(lt, "tf32x3")
+    a, b, dd = d.add_leaf((n, n), Mm), d.add_leaf((4, 4, n, n), Pp), d.add_leaf((n, 4, 4, n), Dd)
+    c = d.add_contraction(a, b, [1], [2])
+    r = d.add_contraction(c, dd, [0, 1, 2, 3], [0, 1, 2, 3])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.set_option(L.LQC_OPT_WINDOW, window)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3

@@ -106,6 +106,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(c4)
+      : "memory");
+}
 // K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of
 // 1024 B (stride-dimension offset), descriptor version 1, layout SWIZZLE_128B.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -199,9 +208,11 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   CUtensorMap map[4];   // Ahi, Alo, Bhi, Blo
   float* out;           // splits == 1: D' [lt][M][Nr]; else partials [splits][lt][M][Nr]
   int M, Nr, kblocks, splits, lt, ntn, ntm, tiles;
-  int b_mn;             // fused form: B stored [k][n] (n unit-stride), transposed by the converters;
-                        // 2: n split into blocks of b_ni columns (an outer free axis)
-  int b_ni;
+  int b_mn;             // fused form: B read in place with n unit-stride ([k][n] tiles that the
+                        // converters transpose): 1 = one k and one n axis (3-d map); 2 = general
+  int b_ni;             // 2: columns of the inner n axis (b_no: an outer n axis follows the k axes)
+  int b_nk, b_no;       // 2: k axes in the map (innermost first), outer n axis present
+  int b_kext[3];        // 2: extents of the k axes, innermost first
   long long tile_start;
 };
 
@@ -342,10 +353,21 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
             tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
-            if (tk->b_mn == 2)  // the same tile inside one block of the outer n axis
-              tma_load_4d(rp + C::kRawA, &tk->map[2], &rf[st], n0 % (2 * tk->b_ni), k0 / 2,
-                          n0 / (2 * tk->b_ni), t);
-            else if (tk->b_mn)  // [16 complex k rows][kBN/2 complex n], unswizzled
+            if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
+              int c[5], nd = 0, kk = k0 / 2;
+              c[nd++] = n0 % (2 * tk->b_ni);
+              for (int a = 0; a < tk->b_nk; ++a) {
+                c[nd++] = kk % tk->b_kext[a];
+                kk /= tk->b_kext[a];
+              }
+              if (tk->b_no) c[nd++] = n0 / (2 * tk->b_ni);
+              c[nd++] = t;
+              if (nd == 3) tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], c[0], c[1], c[2]);
+              else if (nd == 4)
+                tma_load_4d(rp + C::kRawA, &tk->map[2], &rf[st], c[0], c[1], c[2], c[3]);
+              else
+                tma_load_5d(rp + C::kRawA, &tk->map[2], &rf[st], c[0], c[1], c[2], c[3], c[4]);
+            } else if (tk->b_mn)  // [16 complex k rows][kBN/2 complex n], unswizzled
               tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], n0, k0 / 2, t);
             else
               tma_load_3d(rp + C::kRawA, &tk->map[2], &rf[st], k0, n0 / 2, t);
@@ -1145,19 +1167,37 @@ bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows
   return r == CUDA_SUCCESS;
 }
 
-// [lt][outer][K rows][n2 floats] with the outer n axis of stride outer_stride:
-// boxes of kBN floats x 16 rows inside one outer block
-bool make_raw_map_mn4(CUtensorMap* m, const void* base, int64_t n2, int64_t krows,
-                      int64_t outer, int64_t lt, int64_t row_stride, int64_t outer_stride,
-                      int64_t slice_stride) {
+// A right operand read in place as [k][n] tiles: dimensions (inner n as
+// floats, the k axes innermost first, the outer n axis if any, batch), boxes
+// of kBN floats x 16 k rows x 1 ...; fills the task's coordinate fields
+bool make_raw_map_mnx(CUtensorMap* m, const void* base, const Group& bn, const Group& bk,
+                      int64_t lt, int64_t slice_stride, GemmTask* t) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[4] = {(cuuint64_t)n2, (cuuint64_t)krows, (cuuint64_t)outer, (cuuint64_t)lt};
-  cuuint64_t strides[3] = {(cuuint64_t)(row_stride * 8), (cuuint64_t)(outer_stride * 8),
-                           (cuuint64_t)(slice_stride * 8)};
-  cuuint32_t box[4] = {(cuuint32_t)kBN, 16u, 1u, 1u};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides,
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5];
+  int nd = 0;
+  dims[nd] = (cuuint64_t)(2 * bn.ext[bn.n - 1]);
+  box[nd++] = (cuuint32_t)kBN;
+  t->b_nk = bk.n;
+  for (int a = bk.n - 1; a >= 0; --a) {
+    t->b_kext[bk.n - 1 - a] = bk.ext[a];
+    dims[nd] = (cuuint64_t)bk.ext[a];
+    strides[nd - 1] = (cuuint64_t)(bk.stride[a] * 8);
+    box[nd++] = a == bk.n - 1 ? 16u : 1u;
+  }
+  t->b_no = bn.n == 2 ? 1 : 0;
+  if (bn.n == 2) {
+    dims[nd] = (cuuint64_t)bn.ext[0];
+    strides[nd - 1] = (cuuint64_t)(bn.stride[0] * 8);
+    box[nd++] = 1u;
+  }
+  dims[nd] = (cuuint64_t)lt;
+  strides[nd - 1] = (cuuint64_t)(slice_stride * 8);
+  box[nd++] = 1u;
+  for (int a = 0; a < nd; ++a) estr[a] = 1;
+  t->b_ni = bn.ext[bn.n - 1];
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nd, const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -1278,9 +1318,19 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
   // or [k][outer n][inner n] blocks (a propagator contracted over one
   // distillation axis): one TMA box per tile when the inner n extent is a
   // multiple of the tile's 64 complex columns
-  d->b_mn2 = !d->b_direct && !d->b_mn && !cd.b_kfast && cd.bn.n == 2 && cd.bn.stride[1] == 1 &&
-             cd.bn.ext[1] % (kBN / 2) == 0 && cd.bn.stride[0] % 2 == 0 && cd.bk.n == 1 &&
-             cd.bk.stride[0] % 2 == 0 && cd.b_ts % 2 == 0;
+  // general in-place [k][n] tiles: the inner n axis unit-stride (a multiple
+  // of 64 columns if an outer n axis follows), up to 3 k axes whose innermost
+  // extent is a multiple of 16 (a k block never straddles), at most 5 map
+  // dimensions with the batch axis, all strides 16-byte multiples
+  d->b_mn2 = false;
+  if (!d->b_direct && !d->b_mn && !cd.b_kfast && (cd.bn.n == 1 || cd.bn.n == 2) &&
+      cd.bn.stride[cd.bn.n - 1] == 1 && cd.bk.n >= 1 && cd.bk.n <= 3 &&
+      1 + cd.bk.n + (cd.bn.n - 1) + 1 <= 5 && cd.bk.ext[cd.bk.n - 1] % 16 == 0 &&
+      (cd.bn.n == 1 || cd.bn.ext[1] % (kBN / 2) == 0) && cd.b_ts % 2 == 0) {
+    bool even = cd.bn.stride[0] % 2 == 0 || cd.bn.n == 1;
+    for (int a = 0; a < cd.bk.n; ++a) even = even && cd.bk.stride[a] % 2 == 0;
+    d->b_mn2 = even;
+  }
   if (d->b_mn || d->b_mn2) {
     d->b_direct = true;
     d->b_rowstride = cd.bk.stride[0];
@@ -1343,16 +1393,13 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
     if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) return false;
     if (d.b_mn2) {
-      if (!make_raw_map_mn4(&t->map[2], b, 2 * cd.bn.ext[1], cd.K, cd.bn.ext[0], cd.lt,
-                            d.b_rowstride, cd.bn.stride[0], bts))
-        return false;
+      if (!make_raw_map_mnx(&t->map[2], b, cd.bn, cd.bk, cd.lt, bts, t)) return false;
     } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
                       : !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts,
                                       kBN / 2)) {
       return false;
     }
     t->b_mn = d.b_mn2 ? 2 : (d.b_mn ? 1 : 0);
-    t->b_ni = d.b_mn2 ? cd.bn.ext[1] : 0;
   } else if (!make_map(&t->map[0], as, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[1], as + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[2], bs, d.bf16, d.kp, 2 * cd.N, cd.lt) ||

@@ -284,3 +284,27 @@ def test_propagator_right_operand_in_place_vs_oracle(n, window):
     d.set_option(L.LQC_OPT_WINDOW, window)
     d.execute(torch.cuda.current_stream().cuda_stream)
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_propagator_left_operand_in_place_vs_oracle(n):
+    """P x P over (spin out, distillation out) and a P x M over three axes:
+    left operands whose contracted axes are several groups (and whose rows are
+    two groups at n = 128) are read in place; against the oracle."""
+    lt = 2
+    rng = np.random.default_rng(n)
+
+    def rnd(*s):
+        return (rng.standard_normal((lt,) + s) + 1j * rng.standard_normal((lt,) + s)) / np.sqrt(4 * n)
+    P1, P2, Mm = rnd(4, 4, n, n), rnd(4, 4, n, n), rnd(4, 4)
+    c1 = C.contract_pair(P1, P2, (1, 3), (0, 2))              # (s, i, s', j)
+    ref = C.contract_pair(C.contract_pair(c1, P1, (0, 1, 3), (1, 3, 2)), Mm, (0, 1), (0, 1))
+    d = L.Dag(lt, "tf32x3")
+    a, b, m = d.add_leaf((4, 4, n, n), P1), d.add_leaf((4, 4, n, n), P2), d.add_leaf((4, 4), Mm)
+    x = d.add_contraction(a, b, [1, 3], [0, 2])
+    y = d.add_contraction(x, a, [0, 1, 3], [1, 3, 2])
+    r = d.add_contraction(y, m, [0, 1], [0, 1])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3

@@ -213,10 +213,6 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   int b_ni;             // 2: columns of the inner n axis (b_no: an outer n axis follows the k axes)
   int b_nk, b_no;       // 2: k axes in the map (innermost first), outer n axis present
   int b_kext[3];        // 2: extents of the k axes, innermost first
-  int a_mx;             // fused form: A read in place through a general map (k axes beyond the
-  int a_ki, a_ri;       // unit-stride one, an outer row axis): inner k and inner row extents,
-  int a_nk, a_ro;       // outer k axes in the map (innermost first), outer row axis present
-  int a_kext[2];
   long long tile_start;
 };
 
@@ -356,23 +352,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           if (FUSED) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
-            if (tk->a_mx) {  // [128 rows][16 complex k] inside one block of every outer axis
-              int c[5], nd = 0, kk = k0 / 2;
-              c[nd++] = 2 * (kk % tk->a_ki);
-              kk /= tk->a_ki;
-              c[nd++] = m0 % tk->a_ri;
-              for (int a = 0; a < tk->a_nk; ++a) {
-                c[nd++] = kk % tk->a_kext[a];
-                kk /= tk->a_kext[a];
-              }
-              if (tk->a_ro) c[nd++] = m0 / tk->a_ri;
-              c[nd++] = t;
-              if (nd == 3) tma_load_3d(rp, &tk->map[0], &rf[st], c[0], c[1], c[2]);
-              else if (nd == 4) tma_load_4d(rp, &tk->map[0], &rf[st], c[0], c[1], c[2], c[3]);
-              else tma_load_5d(rp, &tk->map[0], &rf[st], c[0], c[1], c[2], c[3], c[4]);
-            } else {
-              tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
-            }
+            tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
             if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
               int c[5], nd = 0, kk = k0 / 2;
               c[nd++] = n0 % (2 * tk->b_ni);
@@ -1187,49 +1167,6 @@ bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows
   return r == CUDA_SUCCESS;
 }
 
-// A left operand read in place as K-major tiles: dimensions (inner k as
-// floats, inner rows, the outer k axes innermost first, the outer row axis
-// if any, batch), boxes of 32 floats x 128 rows x 1 ..., 128-byte swizzle;
-// fills the task's coordinate fields
-bool make_raw_map_ax(CUtensorMap* m, const void* base, const Group& am, const Group& ak,
-                     int64_t lt, int64_t slice_stride, GemmTask* t) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[5], strides[4];
-  cuuint32_t box[5], estr[5];
-  int nd = 0;
-  t->a_ki = ak.ext[ak.n - 1];
-  dims[nd] = (cuuint64_t)(2 * ak.ext[ak.n - 1]);
-  box[nd++] = 32u;
-  const int rin = am.n ? am.n - 1 : -1;  // inner row axis (none: a single row)
-  t->a_ri = rin >= 0 ? am.ext[rin] : 1;
-  dims[nd] = (cuuint64_t)(rin >= 0 ? am.ext[rin] : 1);
-  strides[nd - 1] = (cuuint64_t)((rin >= 0 ? am.stride[rin] : 1) * 8);
-  box[nd++] = (cuuint32_t)kBM;
-  t->a_nk = ak.n - 1;
-  for (int a = ak.n - 2; a >= 0; --a) {
-    t->a_kext[ak.n - 2 - a] = ak.ext[a];
-    dims[nd] = (cuuint64_t)ak.ext[a];
-    strides[nd - 1] = (cuuint64_t)(ak.stride[a] * 8);
-    box[nd++] = 1u;
-  }
-  t->a_ro = am.n == 2 ? 1 : 0;
-  if (am.n == 2) {
-    dims[nd] = (cuuint64_t)am.ext[0];
-    strides[nd - 1] = (cuuint64_t)(am.stride[0] * 8);
-    box[nd++] = 1u;
-  }
-  dims[nd] = (cuuint64_t)lt;
-  strides[nd - 1] = (cuuint64_t)(slice_stride * 8);
-  box[nd++] = 1u;
-  for (int a = 0; a < nd; ++a) estr[a] = 1;
-  t->a_mx = 1;
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nd, const_cast<void*>(base), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 // A right operand read in place as [k][n] tiles: dimensions (inner n as
 // floats, the k axes innermost first, the outer n axis if any, batch), boxes
 // of kBN floats x 16 k rows x 1 ...; fills the task's coordinate fields
@@ -1371,22 +1308,6 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
            (rows.n == 0 || (rows.n == 1 && rows.stride[0] % 2 == 0));
   };
   d->a_direct = direct(cd.am, cd.ak, cd.a_kfast) && cd.a_ts % 2 == 0;
-  // A read in place through a general map: the innermost k axis unit-stride
-  // with a multiple of 16 (a k block never straddles), up to 2 more k axes,
-  // rows one axis or two whose inner extent is a multiple of the 128-row
-  // tile, at most 5 map dimensions with the batch axis, 16-byte strides
-  d->a_mx = false;
-  if (!d->a_direct && cd.a_kfast && cd.ak.n >= 1 && cd.ak.n <= 3 &&
-      cd.ak.stride[cd.ak.n - 1] == 1 && cd.ak.ext[cd.ak.n - 1] % 16 == 0 && cd.am.n >= 1 &&
-      cd.am.n <= 2 &&
-      (cd.am.n < 2 || cd.am.ext[1] % kBM == 0) && 1 + 1 + (cd.ak.n - 1) + (cd.am.n == 2) + 1 <= 5 &&
-      cd.a_ts % 2 == 0) {
-    bool even = true;
-    for (int a = 0; a < cd.ak.n - 1; ++a) even = even && cd.ak.stride[a] % 2 == 0;
-    for (int a = 0; a < cd.am.n; ++a) even = even && cd.am.stride[a] % 2 == 0;
-    d->a_mx = even;
-    if (d->a_mx) d->a_direct = true;
-  }
   d->b_direct = direct(cd.bn, cd.bk, cd.b_kfast) && cd.b_ts % 2 == 0;
   d->a_rowstride = d->a_direct ? (cd.am.n ? cd.am.stride[0] : cd.K) : cd.K;
   d->b_rowstride = d->b_direct ? (cd.bn.n ? cd.bn.stride[0] : cd.K) : cd.K;
@@ -1470,11 +1391,7 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const void* b = d.b_direct ? (const void*)B : (const void*)bs;
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
-    if (d.a_mx) {
-      if (!make_raw_map_ax(&t->map[0], a, cd.am, cd.ak, cd.lt, ats, t)) return false;
-    } else if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) {
-      return false;
-    }
+    if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) return false;
     if (d.b_mn2) {
       if (!make_raw_map_mnx(&t->map[2], b, cd.bn, cd.bk, cd.lt, bts, t)) return false;
     } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)

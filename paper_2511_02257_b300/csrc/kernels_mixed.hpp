@@ -49,8 +49,7 @@ struct MixedDesc {
   bool fused;
   bool a_direct, b_direct;
   bool b_mn;                // B read in place as [k][n]; the GEMM's converters transpose it
-  bool b_mn2;               // ... through a general map (several k axes, an outer n axis)
-  bool a_mx;                // A read in place through a general map
+  bool b_mn2;               // ... as [k][outer n][inner n] blocks (4-d map)
   int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
   PermDesc a_perm, b_perm;
 };

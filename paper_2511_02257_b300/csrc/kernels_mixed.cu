@@ -1,26 +1,36 @@
 // Mixed-precision kernels: complex64 storage, split (hi + lo) tensor-core
 // products with FP32 accumulation in TMEM, FP64 where sums form results.
 //
-// K3  pack: gathers one operand of a binary contraction (any axis
-//     permutation, folded into the loads) and writes its hi/lo planes in the
-//     real-embedded GEMM layout:
-//       A' [m][2k]   = Re A(m,k),  A' [m][2k+1]  = Im A(m,k)
-//       B'T[2n][2k]  = Re B(k,n),  B'T[2n][2k+1] = -Im B(k,n)
-//       B'T[2n+1][2k]= Im B(k,n),  B'T[2n+1][2k+1]= Re B(k,n)
-//     so that the real product A' B' is the complex product already
-//     interleaved as (re, im): D'[m][2n] = Re C(m,n), D'[m][2n+1] = Im C(m,n).
-//     hi = x rounded to the tensor-core type, lo = (x - hi) rounded.
-// K4  gemm: TMA (128-byte swizzle) feeds a 3-stage shared-memory ring; one
-//     thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 inputs):
-//     hi*hi into one FP32 accumulator in TMEM and the two correction
-//     products lo*hi + hi*lo into a second one, so the small terms never
-//     round against the large running sum.  The tensor core's own FP32
-//     accumulation is kept short: every kChunkBlocks k-blocks the MMA thread
-//     switches to the other of two TMEM buffers and four drain warps add the
-//     finished buffer into FP32 registers (round-to-nearest adds), one output
-//     row per thread.  Contractions longer than kMaxChunk real k are split
-//     over k into FP32 partial tiles summed in FP64 by K4r.
-// K2m contract-all on complex64 operands with FP64 accumulation.
+// Real embedding of a complex contraction C = A B (per time slice):
+//   A' [m][2k]   = Re A(m,k),  A' [m][2k+1]  = Im A(m,k)   (the complex64 row)
+//   B'T[2n][2k]  = Re B(k,n),  B'T[2n][2k+1] = -Im B(k,n)
+//   B'T[2n+1][2k]= Im B(k,n),  B'T[2n+1][2k+1]= Re B(k,n)
+// so that the real product A' B' is the complex product already interleaved
+// as (re, im): D'[m][2n] = Re C(m,n), D'[m][2n+1] = Im C(m,n).  Each operand
+// value x is split into hi = x rounded to the tensor-core type and lo =
+// (x - hi) rounded.
+//
+// K3  pack (plane form): gathers one operand (any axis permutation, folded
+//     into the loads) and writes its hi/lo planes in that layout.
+// K4  gemm, persistent over a tile sequence (one contraction or a grouped
+//     level's task table): TMA (128-byte swizzle) feeds a shared-memory ring;
+//     one thread issues tcgen05.mma (kind::tf32, or kind::f16 with bf16):
+//     hi*hi into one FP32 accumulator in TMEM and lo*hi + hi*lo into a
+//     second, so the small terms never round against the large running sum.
+//     The tensor core's own FP32 accumulation is kept short: every
+//     kChunkBlocks k-blocks the MMA thread switches to the other of two TMEM
+//     buffers and eight drain warps add the finished one into FP32 registers
+//     (one output row per thread), then stage 32x16 output blocks through
+//     shared memory for coalesced stores.  Fused form (TF32): TMA brings raw
+//     complex64 tiles (K-major, or [k][n] for right operands read in place
+//     through maps of up to 5 dimensions) and converter warps build the
+//     hi/lo operand tiles.  Contractions longer than kMaxChunk real k are
+//     split over k into FP32 partial tiles summed in FP64.
+// Reorder / K2m: a PermDesc maps destination elements to source offsets;
+//     blocks of runs or of transposed tiles copy operands into [rows][K]
+//     order, and the correlators (contract-all, double-float per thread, FP64
+//     across threads and blocks) visit their partner in place.
+// Grouped launches run each kind over every member of a window level.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // kernel records an error code, drains what it started and returns.

@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=8.0,
+                    help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--workload", default="multi_meson")
     ap.add_argument("--policy", default="tree")
     ap.add_argument("--evict", default="lru")
@@ -72,6 +74,20 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """Largest value of x over the ranks (the job's time is its slowest
+    rank's): a MAX all-reduce on the process group's device (CUDA under
+    NCCL, the host under gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_init():
@@ -218,8 +234,8 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     wl = synth.make_workload(args.workload)
-    per_step = 8.0
-    oracle_sample(wl, 1.0)  # warm caches
+    per_step = args.ref_seconds
+    oracle_sample(wl, min(1.0, per_step))  # warm caches
     total_f, total_t = 0, 0.0
     for w in range(args.warmup):
         oracle_sample(wl, per_step, rng_seed=100 + w)
@@ -339,10 +355,7 @@ def main():
     ms = e0.elapsed_time(e1)
     info1 = nd.exec_info()
     corr = nd.read_all_correlators()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     flops_step = info1["flops"]
     value = ws * flops_step * args.steps / (ms * 1e-3) / 1e12
     # dominant kernel: the exterior contraction
@@ -369,10 +382,7 @@ def main():
             nd.execute(stream)
             nd.read_all_correlators(out)
         t_e2e = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, ws)
         st = nd.stats()
         e2e = {"value": ws * flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": st["h2d_bytes"],

@@ -65,6 +65,13 @@ class Workload:
     functions: List[List[int]]
     budget_bytes: int = 0     # 0 = unlimited device budget
     seed: int = 0
+    # every term as a graph before any bracketing: (leaf indices of its
+    # items, edges (item a, axis of a, item b, axis of b), one per index
+    # pair), in the order of the diagrams; graph_functions[f] lists the
+    # graphs of function f (empty for workloads built from parts)
+    graphs: List[Tuple[List[int], List[Tuple[int, int, int, int]]]] = \
+        dataclasses.field(default_factory=list)
+    graph_functions: List[List[int]] = dataclasses.field(default_factory=list)
 
     @property
     def n_leaves(self) -> int:
@@ -143,6 +150,19 @@ def _ring_links(kinds: Sequence[str]) -> Dict[Label, Label]:
     for i, j in enumerate(ps):
         tie((j, "sout"), (ps[(i + 1) % len(ps)], "sin"))
     return link
+
+
+def ring_edges(kinds: Sequence[str], link: Dict[Label, Label]) -> List[Tuple[int, int, int, int]]:
+    """The index pairs of a diagram as edges (item a, axis a, item b, axis b),
+    a < b by (item, axis), sorted."""
+    out = set()
+    for la, lb in link.items():
+        a = (la[0], _leaf_axes(kinds[la[0]], la[0]).index(la))
+        b = (lb[0], _leaf_axes(kinds[lb[0]], lb[0]).index(lb))
+        if a > b:
+            a, b = b, a
+        out.add((a[0], a[1], b[0], b[1]))
+    return sorted(out)
 
 
 def _all_brackets(lo: int, hi: int):
@@ -350,6 +370,7 @@ def make_workload(name: str, seed: int = 0, **overrides) -> Workload:
     max_elems = max(int(np.prod(lf.extents)) for lf in leaves)
 
     diagrams: List[Tuple[List[int], list]] = []   # (item leaf indices, pending requests)
+    graphs: List[Tuple[List[int], List[Tuple[int, int, int, int]]]] = []
 
     prefixes = []
     for _ in range(rc.prefix_pool):
@@ -396,6 +417,7 @@ def make_workload(name: str, seed: int = 0, **overrides) -> Workload:
                     if pend is not None:
                         roots.append(len(diagrams))
                         diagrams.append((items, pend))
+                        graphs.append((list(items), ring_edges(kinds, link)))
                         break
         else:
             kinds, seq = _meson_function(rng, rc, pools, prefixes)
@@ -422,12 +444,14 @@ def make_workload(name: str, seed: int = 0, **overrides) -> Workload:
                 if pend is not None:
                     roots.append(len(diagrams))
                     diagrams.append((ti, pend))
+                    graphs.append((list(ti), ring_edges(tk, link)))
         if roots:
             fn_diagrams.append(roots)
     requests, root_of = _emit(diagrams, len(leaves), rc.emission)
     functions = [[root_of[d] for d in fn] for fn in fn_diagrams]
     return Workload(name=rc.name, lt=rc.lt, nvec=n, leaves=leaves, requests=requests,
-                    functions=functions, budget_bytes=rc.budget_bytes, seed=seed)
+                    functions=functions, budget_bytes=rc.budget_bytes, seed=seed,
+                    graphs=graphs, graph_functions=[list(fn) for fn in fn_diagrams])
 
 
 def _emit(diagrams, n_leaves: int, emission: str):

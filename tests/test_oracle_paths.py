@@ -1,0 +1,70 @@
+"""Pins of the oracle's contraction-path selection (oracle.paths, Sec. II-A).
+
+* Hand example: Tr(A B C) and Tr(D B C) share the adjacent pair B.C, so the
+  selection contracts it first in both terms and builds 3 contractions
+  (B.C and one root each) where left-deep brackets (A.B).C, (D.B).C build 4.
+* Any contraction path of a term gives the same correlator: every root of a
+  path-selected DAG equals the generator's own bracketing of the same term
+  (whose values the brute-force pins cover), on meson and baryon terms.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import contract as C
+from oracle import dag as D
+from oracle import paths as PS
+
+
+def _ring3(x, y, z):
+    # Tr(X Y Z): X.dout-Y.din, Y.dout-Z.din, Z.dout-X.din (axes din=0, dout=1)
+    return [x, y, z], [(0, 1, 1, 0), (1, 1, 2, 0), (0, 0, 2, 1)]
+
+
+def test_shared_pair_selected_first():
+    n, lt = 5, 2
+    dag = D.Dag(lt)
+    A, B, Cm, Dm = (dag.add_leaf((n, n), leaf_index=i) for i in range(4))
+    roots = PS.select_paths(dag, [_ring3(A, B, Cm), _ring3(Dm, B, Cm)])
+    contr = [u for u in range(len(dag.nodes)) if not dag.nodes[u].is_leaf]
+    assert len(contr) == 3
+    first = dag.nodes[contr[0]]
+    assert (first.left, first.right, first.la, first.ra) == (B, Cm, (1,), (0,))
+    assert all(dag.nodes[r].extents == () for r in roots)
+    # left-deep brackets of the same two terms share nothing
+    ld = D.Dag(lt)
+    for i in range(4):
+        ld.add_leaf((n, n), leaf_index=i)
+    for x in (0, 3):
+        xy = ld.add_contraction(x, 1, (1,), (0,))
+        ld.add_contraction(xy, 2, (1, 0), (0, 1))
+    assert len(ld.non_leaf()) == 4
+    # and the values agree with a direct trace
+    rng = np.random.default_rng(0)
+    data = [rng.standard_normal((lt, n, n)) + 1j * rng.standard_normal((lt, n, n)) for _ in range(4)]
+    got = C.evaluate(dag, lambda u: data[u], roots)
+    for r, x in zip(roots, (0, 3)):
+        want = np.einsum("tij,tjk,tki->t", data[x], data[1], data[2])
+        assert np.allclose(got[r], want, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("name,kw", [("tiny", {}), ("multi_meson", dict(n_functions=12, nvec=6, lt=3)),
+                                     ("baryon", dict(n_functions=10, nvec=5, lt=2))])
+def test_paths_give_the_generators_values(name, kw):
+    wl = synth.make_workload(name, **kw)
+    od, ids = D.build_from_workload(wl)
+    pd, proots = PS.build_with_paths(wl)
+    assert len(proots) == len(wl.graphs)
+
+    def lf(u):
+        return synth.leaf_data(wl, u)     # leaves are the first nodes on both sides
+    ref = C.evaluate(od, lambda u: synth.leaf_data(wl, od.nodes[u].leaf_index))
+    got = C.evaluate(pd, lf, proots)
+    roots_in_order = [r for f in wl.functions for r in f]
+    graph_roots = [ids[r] for r in roots_in_order]       # generator roots, diagram order
+    assert len(graph_roots) == len(proots)
+    for g, (r_ref, r_path) in enumerate(zip(graph_roots, proots)):
+        a, b = ref[r_ref], got[r_path]
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a), (name, g)
+    # the path-selected DAG merges at least as much as it emits
+    assert len(pd.non_leaf()) <= sum(len(e) for _, e in wl.graphs)

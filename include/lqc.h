@@ -207,6 +207,33 @@ int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
 int lqc_dag_add_contraction(lqc_dag* dag, int64_t left, int64_t right, int npairs,
                             const int* la, const int* ra, int64_t* node_id);
 
+/* Contraction-path selection (Sec. II-A): reduce each of n_graphs tensor
+ * graphs to one node by binary contractions added to the DAG.  The vertices
+ * of graph g are the existing nodes vert_nodes[vert_off[g] .. vert_off[g+1])
+ * (rank >= 1; a node may appear in several graphs and several times in one);
+ * its edges are edges[4*e .. 4*e+4) = (vertex a, axis of a, vertex b, axis of
+ * b) for e in [edge_off[g], edge_off[g+1]), vertices as indices local to the
+ * graph.  Every axis is in at most one edge; paired extents are equal; each
+ * graph must be connected.  An unpaired axis stays open in the graph's root.
+ * Order (the reading of the prose of Sec. II-A used here): a candidate is a
+ * pair of current vertices joined by edges (all of them contracted at once),
+ * keyed like the merge key of lqc_dag_add_contraction (left = the smaller
+ * node id; equal ids: the vertex holding the smaller (vertex, axis) label;
+ * pairs sorted by left axis).  A key's value is the number of graphs holding
+ * it times its complex multiply-adds Lt*M*N*K; a graph's candidates whose
+ * output has more elements than its largest input are left out unless it has
+ * no other.  Each step contracts the key of largest value (ties: smallest
+ * key; axis lists compared lexicographically) in every graph holding it,
+ * repeatedly, lowest vertex pair first, so recurring costly contractions are
+ * done once.  roots[g] receives the final node of graph g.  Host memory:
+ * all arrays are read or written during the call only, caller-owned.
+ * Errors: LQC_ERR_ARG (bad offsets, vertex, edge or extents; disconnected
+ * graph; contractions added up to the failing step stay in the DAG),
+ * LQC_ERR_STATE (after lqc_dag_schedule), LQC_ERR_HOST_MEM. */
+int lqc_dag_add_graphs(lqc_dag* dag, int64_t n_graphs, const int64_t* vert_off,
+                       const int64_t* vert_nodes, const int64_t* edge_off,
+                       const int32_t* edges, int64_t* roots);
+
 /* Freeze the DAG, compute the contraction order with `policy` and replay it
  * under `budget_bytes` (0 = unlimited) with eviction policy `evict`,
  * producing the op list (LOAD / EVICT / CONTRACT / FREE) and its figures.
@@ -294,6 +321,13 @@ int lqc_dag_get_roots(lqc_dag* dag, int64_t* roots, int64_t cap, int64_t* n);
 int lqc_dag_num_nodes(lqc_dag* dag, int64_t* n);
 int lqc_dag_node_info(lqc_dag* dag, int64_t id, int64_t* size_bytes, int* rank,
                       int* is_leaf, int64_t* lt);
+
+/* Operands of a node: left/right ids and the npairs contracted axis pairs
+ * (la/ra: caller arrays of LQC_MAX_RANK ints), as merged by
+ * lqc_dag_add_contraction; a leaf gives left = right = -1, npairs = 0.
+ * Each out-pointer nullable.  Errors: LQC_ERR_ARG (id out of range). */
+int lqc_dag_node_operands(lqc_dag* dag, int64_t id, int64_t* left, int64_t* right,
+                          int* npairs, int* la, int* ra);
 
 /* Figures counted by the last execute (equal to the planned figures by
  * construction of the executor; peak_exec is taken from the plan). */

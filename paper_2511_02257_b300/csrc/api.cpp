@@ -12,10 +12,6 @@
 using lqc::Dag;
 using lqc::Node;
 
-struct lqc_dag {
-  Dag d;
-};
-
 namespace {
 
 int fail(lqc_dag* h, int code, const std::string& msg) {
@@ -325,6 +321,21 @@ int lqc_dag_node_info(lqc_dag* h, int64_t id, int64_t* size_bytes, int* rank, in
   if (lt) *lt = h->d.nodes[id].lt;
   if (rank) *rank = h->d.nodes[id].rank;
   if (is_leaf) *is_leaf = h->d.nodes[id].is_leaf() ? 1 : 0;
+  return LQC_OK;
+}
+
+int lqc_dag_node_operands(lqc_dag* h, int64_t id, int64_t* left, int64_t* right, int* npairs,
+                          int* la, int* ra) {
+  if (!h) return LQC_ERR_ARG;
+  if (id < 0 || id >= (int64_t)h->d.nodes.size()) return fail(h, LQC_ERR_ARG, "id out of range");
+  const Node& n = h->d.nodes[id];
+  if (left) *left = n.left;
+  if (right) *right = n.right;
+  if (npairs) *npairs = n.npairs;
+  for (int i = 0; i < n.npairs; ++i) {
+    if (la) la[i] = n.la[i];
+    if (ra) ra[i] = n.ra[i];
+  }
   return LQC_OK;
 }
 

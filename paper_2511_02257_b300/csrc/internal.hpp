@@ -110,3 +110,8 @@ int host_store_alloc(Dag& g, int64_t leaf, std::string* err);
 void host_store_free(Node& n);
 
 }  // namespace lqc
+
+// The opaque handle of the C ABI.
+struct lqc_dag {
+  lqc::Dag d;
+};

@@ -32,6 +32,14 @@ contractions per launch, CUDA graphs) and as one launch per contraction in
 FP64, with the leaves resident on the device and from pinned host memory;
 reports times, speedups and the TF32x3 error of every correlator against
 the FP64 path (whose parity with the oracle the test suite establishes).
+
+  python -m paper_2511_02257_b300.experiments paths [--workloads multi_meson,...]
+         [--gpu] [--steps 3]
+
+builds each workload's terms twice -- as the generator brackets them and by
+contraction-path selection (Sec. II-A) -- and reports distinct
+contractions, flops and every scheduler's peak; with --gpu also both DAGs'
+tuned TF32x3 time-to-solution and the largest difference of a term's value.
 """
 from __future__ import annotations
 
@@ -277,11 +285,100 @@ def batched_bench(argv):
     print(json.dumps(summary), flush=True)
 
 
+def dag_contraction_flops(nd) -> int:
+    """Real flops (8 per complex multiply-add) of every distinct contraction
+    of a Dag, from its node sizes: M*K, K*N and M*N are the per-slice element
+    counts of the two operands and the output, so K^2 = MK * KN / MN."""
+    import math
+    total = 0
+    for u in range(nd.num_nodes()):
+        left, right, _, _ = nd.node_operands(u)
+        if left < 0:
+            continue
+        lt = nd.node_info(u)["lt"]
+
+        def elems(x):
+            return nd.node_info(x)["size"] // (16 * lt)
+        mk, kn, mn = elems(left), elems(right), elems(u)
+        k = math.isqrt(mk * kn // mn)
+        assert k * k * mn == mk * kn
+        total += 8 * lt * (mk // k) * (kn // k) * k
+    return total
+
+
+def paths_bench(argv):
+    """Contraction-path selection (Sec. II-A) against the generator's own
+    bracketing of the same terms: distinct contractions, flops, peak memory
+    of each scheduler and the host build time; with --gpu also the tuned
+    TF32x3 time-to-solution of both DAGs (leaves on the device) and the
+    largest relative difference of any term's correlator between them."""
+    import paper_2511_02257_b300 as L
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workloads", default="multi_meson,baryon,memory_pressure")
+    ap.add_argument("--policies", default="naive,sibling,tree,rsgs,node")
+    ap.add_argument("--gpu", action="store_true")
+    ap.add_argument("--steps", type=int, default=3)
+    args = ap.parse_args(argv)
+    for name in args.workloads.split(","):
+        wl = synth.make_workload(name)
+        nl = len(wl.leaves)
+        gen_roots = [r for f in wl.functions for r in f]      # stream index of each term
+        rows = {}
+        for arm in ("generator", "paths"):
+            t0 = time.perf_counter()
+            nd, ids = L.build_dag(wl, with_data=False, paths=(arm == "paths"))
+            t_build = time.perf_counter() - t0
+            row = {"workload": name, "arm": arm, "terms": len(wl.graphs),
+                   "contractions": nd.num_nodes() - nl, "build_s": t_build,
+                   "tflop": dag_contraction_flops(nd) / 1e12}
+            for pol in args.policies.split(","):
+                st = nd.schedule(pol, "lru", 0)
+                row["peak_exec_gib_" + pol] = st["peak_exec"] / 2 ** 30
+            rows[arm] = (row, ids)
+            nd.close()
+        if args.gpu:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+            leaves = _gen_leaves(wl)
+            vals = {}
+            for arm in ("generator", "paths"):
+                row, _ = rows[arm]
+                nd, ids = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: leaves[li],
+                                      paths=(arm == "paths"))
+                nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
+                nd.schedule("tree", "lru", wl.budget_bytes)
+                nd.stage_leaves(stream)
+                best = nd.autotune(stream, reps=2)[0]
+                nd.unstage_leaves()
+                t, _, info = _time_arm(nd, stream, args.steps, True)
+                term_roots = [ids[r] for r in gen_roots] if arm == "generator" else ids[nl:]
+                vals[arm] = np.stack([nd.read_correlator(r) for r in term_roots])
+                row.update({"time_to_solution_s": t, "tflops": info["flops"] / t / 1e12,
+                            "autotune_best": best})
+                nd.close()
+                del nd
+                torch.cuda.empty_cache()
+            a, b = vals["generator"], vals["paths"]
+            rel = np.linalg.norm(a - b, axis=1) / np.linalg.norm(a, axis=1)
+            rows["paths"][0]["max_rel_diff_vs_generator"] = float(rel.max())
+        for arm in ("generator", "paths"):
+            print(json.dumps(rows[arm][0]), flush=True)
+        g, p = rows["generator"][0], rows["paths"][0]
+        summ = {"summary": name, "contraction_ratio": p["contractions"] / g["contractions"],
+                "flop_ratio": p["tflop"] / g["tflop"]}
+        if args.gpu:
+            summ["speedup_paths_vs_generator"] = g["time_to_solution_s"] / p["time_to_solution_s"]
+        print(json.dumps(summ), flush=True)
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         return kernel_bench(sys.argv[2:])
     if len(sys.argv) > 1 and sys.argv[1] == "batched":
         return batched_bench(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "paths":
+        return paths_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -84,6 +84,7 @@ _sig("lqc_dag_set_batch", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_add_leaf_tensor", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, P_dbl, P_i64])
 _sig("lqc_dag_set_leaf_data", ctypes.c_int, [c_vp, c_i64, P_dbl])
 _sig("lqc_dag_add_contraction", ctypes.c_int, [c_vp, c_i64, c_i64, ctypes.c_int, P_int, P_int, P_i64])
+_sig("lqc_dag_add_graphs", ctypes.c_int, [c_vp, c_i64, P_i64, P_i64, P_i64, P_i32, P_i64])
 _sig("lqc_dag_schedule", ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.POINTER(lqc_stats)])
 _sig("lqc_dag_set_order", ctypes.c_int, [c_vp, P_i64, c_i64, ctypes.c_int, ctypes.c_uint64,
@@ -102,6 +103,7 @@ _sig("lqc_dag_read_all_correlators", ctypes.c_int, [c_vp, P_dbl, c_i64])
 _sig("lqc_dag_get_roots", ctypes.c_int, [c_vp, P_i64, c_i64, P_i64])
 _sig("lqc_dag_num_nodes", ctypes.c_int, [c_vp, P_i64])
 _sig("lqc_dag_node_info", ctypes.c_int, [c_vp, c_i64, P_i64, P_int, P_int, P_i64])
+_sig("lqc_dag_node_operands", ctypes.c_int, [c_vp, c_i64, P_i64, P_i64, P_int, P_int, P_int])
 _sig("lqc_dag_get_stats", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_stats)])
 _sig("lqc_dag_get_exec_info", ctypes.c_int, [c_vp, ctypes.POINTER(lqc_exec_info)])
 _sig("lqc_last_error", ctypes.c_char_p, [c_vp])
@@ -126,12 +128,12 @@ _sig("lqc_contract_all_c64_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c
 
 # re-export the raw entry points under their C names
 for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
-           "lqc_dag_add_contraction", "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
+           "lqc_dag_add_contraction", "lqc_dag_add_graphs", "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
            "lqc_dag_get_plan", "lqc_dag_set_option", "lqc_dag_stage_leaves",
            "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_autotune",
            "lqc_dag_read_correlator",
            "lqc_dag_read_all_correlators", "lqc_dag_get_roots", "lqc_dag_num_nodes",
-           "lqc_dag_node_info", "lqc_dag_get_stats", "lqc_dag_get_exec_info", "lqc_last_error",
+           "lqc_dag_node_info", "lqc_dag_node_operands", "lqc_dag_get_stats", "lqc_dag_get_exec_info", "lqc_last_error",
            "lqc_dag_get_kernel_times",
            "lqc_contract_fp64", "lqc_contract_all_fp64", "lqc_contract_all_scratch_bytes",
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
@@ -230,6 +232,27 @@ class Dag:
         self._check(_lib.lqc_dag_add_contraction(self.h, int(left), int(right), len(la), pa, pb,
                                                  ctypes.byref(nid)), "add_contraction")
         return nid.value
+
+    def add_graphs(self, graphs) -> List[int]:
+        """Contraction-path selection (Sec. II-A): reduce every graph
+        (vertex node ids, edges (vertex a, axis a, vertex b, axis b) with
+        graph-local vertices) to one node; returns each graph's root id."""
+        vo, vn, eo, ed = [0], [], [0], []
+        for nodes, edges in graphs:
+            vn.extend(int(u) for u in nodes)
+            vo.append(len(vn))
+            for e in edges:
+                ed.extend(int(x) for x in e)
+            eo.append(len(ed) // 4)
+        a, pa = _i64arr(vo)
+        b, pb = _i64arr(vn)
+        c, pc = _i64arr(eo)
+        e = np.ascontiguousarray(np.asarray(ed if ed else [0], dtype=np.int32))
+        roots = np.zeros(max(len(graphs), 1), dtype=np.int64)
+        self._check(_lib.lqc_dag_add_graphs(self.h, len(graphs), pa, pb, pc,
+                                            e.ctypes.data_as(P_i32), roots.ctypes.data_as(P_i64)),
+                    "add_graphs")
+        return roots[:len(graphs)].tolist()
 
     # -- scheduling
     def schedule(self, policy="tree", evict="lru", budget_bytes: int = 0) -> dict:
@@ -336,6 +359,15 @@ class Dag:
                                            ctypes.byref(lf), ctypes.byref(lt)), "node_info")
         return {"size": sz.value, "rank": rk.value, "is_leaf": bool(lf.value), "lt": lt.value}
 
+    def node_operands(self, nid: int):
+        """(left, right, la, ra) of a node; (-1, -1, (), ()) for a leaf."""
+        l, r, n = c_i64(), c_i64(), ctypes.c_int()
+        la = (ctypes.c_int * 8)()
+        ra = (ctypes.c_int * 8)()
+        self._check(_lib.lqc_dag_node_operands(self.h, int(nid), ctypes.byref(l), ctypes.byref(r),
+                                               ctypes.byref(n), la, ra), "node_operands")
+        return l.value, r.value, tuple(la[:n.value]), tuple(ra[:n.value])
+
     def stats(self) -> dict:
         st = lqc_stats()
         self._check(_lib.lqc_dag_get_stats(self.h, ctypes.byref(st)), "get_stats")
@@ -359,10 +391,13 @@ class Dag:
         return info.as_dict()
 
 
-def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=None):
+def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=None,
+              paths: bool = False):
     """Feed a ``synth.Workload`` request stream into a new Dag.
 
-    Returns (dag, ids) where ids maps stream index -> node id."""
+    Returns (dag, ids) where ids maps stream index -> node id.  With
+    ``paths`` the contractions come from path selection over the workload's
+    graphs instead (Sec. II-A) and ids lists the leaf ids then the roots."""
     d = Dag(wl.lt, precision)
     ids = []
     for li, lf in enumerate(wl.leaves):
@@ -370,6 +405,9 @@ def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=
         if with_data:
             data = leaf_data_fn(li) if leaf_data_fn else None
         ids.append(d.add_leaf(lf.extents, data, lt=wl.leaf_lt(li)))
+    if paths:
+        return d, ids + d.add_graphs([([ids[v] for v in items], edges)
+                                      for items, edges in wl.graphs])
     for rq in wl.requests:
         ids.append(d.add_contraction(ids[rq.left], ids[rq.right], rq.la, rq.ra))
     return d, ids

@@ -217,9 +217,9 @@ int lqc_dag_add_contraction(lqc_dag* dag, int64_t left, int64_t right, int npair
  * graph must be connected.  An unpaired axis stays open in the graph's root.
  * Order (the reading of the prose of Sec. II-A used here): a candidate is a
  * pair of current vertices joined by edges (all of them contracted at once),
- * keyed like the merge key of lqc_dag_add_contraction (left = the smaller
- * node id; equal ids: the vertex holding the smaller (vertex, axis) label;
- * pairs sorted by left axis).  A key's value is the number of graphs holding
+ * keyed like the merge key of lqc_dag_add_contraction (left = the operand
+ * with more elements, so M >= N; ties: the smaller node id, then the vertex
+ * holding the smaller (vertex, axis) label; pairs sorted by left axis).  A key's value is the number of graphs holding
  * it times its complex multiply-adds Lt*M*N*K; a graph's candidates whose
  * output has more elements than its largest input are left out unless it has
  * no other.  Each step contracts the key of largest value (ties: smallest

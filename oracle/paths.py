@@ -12,8 +12,10 @@ Reading used (the paper gives the idea in prose only):
 * a candidate of a graph is a pair of its current vertices joined by at
   least one edge; contracting it pairs every edge between the two.  Its key
   is the DAG's merge key: (left node, right node, left axes, right axes),
-  left = the smaller node id (for equal ids, the vertex whose axis labels
-  come first), pairs sorted by the left axis;
+  left = the vertex whose tensor has more elements (the paper leaves the
+  orientation open; this one puts the larger free extent on the output's
+  rows, M >= N), ties to the smaller node id, then to the vertex whose axis
+  labels come first; pairs sorted by the left axis;
 * value of a key = (number of graphs holding a candidate with that key) x
   (complex multiply-adds of the contraction, Lt * M * N * K); outputs with
   more elements than the graph's largest input tensor are not candidates
@@ -48,7 +50,9 @@ def _candidate(dag: Dag, p: _Vertex, q: _Vertex, partner):
              if partner.get(lab) in qpos]
     if not pairs:
         return None
-    if (p.node, min(p.labels)) <= (q.node, min(q.labels)):
+    pe = int(np.prod(dag.nodes[p.node].extents, dtype=np.int64))
+    qe = int(np.prod(dag.nodes[q.node].extents, dtype=np.int64))
+    if (-pe, p.node, min(p.labels)) <= (-qe, q.node, min(q.labels)):
         left, right, lr = p, q, pairs
     else:
         left, right, lr = q, p, [(j, i) for (i, j) in pairs]

@@ -9,8 +9,10 @@
 //  * a candidate of a graph is a pair of its current vertices joined by at
 //    least one edge; contracting it pairs every edge between the two.  Its
 //    key is the DAG's merge key (left node, right node, left axes, right
-//    axes): left = the smaller node id (equal ids: the vertex whose smallest
-//    axis label is smaller), pairs sorted by the left axis;
+//    axes): left = the vertex whose tensor has more elements, so that the
+//    larger free extent runs over the output's rows (M >= N: full 128-row
+//    GEMM tiles), ties to the smaller node id, then to the vertex whose
+//    smallest axis label is smaller; pairs sorted by the left axis;
 //  * value of a key = (graphs holding a candidate with that key) x (complex
 //    multiply-adds, Lt * M * N * K); outputs with more elements than the
 //    graph's largest input tensor are not candidates unless the graph has no
@@ -69,7 +71,8 @@ bool candidate(const lqc::Dag& g, const Vertex& p, const Vertex& q,
   if (pairs.empty()) return false;
   const Label pmin = *std::min_element(p.labels.begin(), p.labels.end());
   const Label qmin = *std::min_element(q.labels.begin(), q.labels.end());
-  const bool p_left = std::make_pair(p.node, pmin) <= std::make_pair(q.node, qmin);
+  const int64_t pe = g.nodes[p.node].elems, qe = g.nodes[q.node].elems;
+  const bool p_left = std::make_tuple(-pe, p.node, pmin) <= std::make_tuple(-qe, q.node, qmin);
   if (!p_left)
     for (auto& pr : pairs) std::swap(pr.first, pr.second);
   std::sort(pairs.begin(), pairs.end());

@@ -285,10 +285,11 @@ def batched_bench(argv):
     print(json.dumps(summary), flush=True)
 
 
-def dag_contraction_flops(nd) -> int:
+def dag_contraction_flops(nd, elem_bytes: int = 16) -> int:
     """Real flops (8 per complex multiply-add) of every distinct contraction
-    of a Dag, from its node sizes: M*K, K*N and M*N are the per-slice element
-    counts of the two operands and the output, so K^2 = MK * KN / MN."""
+    of a Dag stored with `elem_bytes` per element, from its node sizes: M*K,
+    K*N and M*N are the per-slice element counts of the two operands and the
+    output, so K^2 = MK * KN / MN."""
     import math
     total = 0
     for u in range(nd.num_nodes()):
@@ -298,7 +299,7 @@ def dag_contraction_flops(nd) -> int:
         lt = nd.node_info(u)["lt"]
 
         def elems(x):
-            return nd.node_info(x)["size"] // (16 * lt)
+            return nd.node_info(x)["size"] // (elem_bytes * lt)
         mk, kn, mn = elems(left), elems(right), elems(u)
         k = math.isqrt(mk * kn // mn)
         assert k * k * mn == mk * kn
@@ -309,17 +310,20 @@ def dag_contraction_flops(nd) -> int:
 def paths_bench(argv):
     """Contraction-path selection (Sec. II-A) against the generator's own
     bracketing of the same terms: distinct contractions, flops, peak memory
-    of each scheduler and the host build time; with --gpu also the tuned
-    TF32x3 time-to-solution of both DAGs (leaves on the device) and the
-    largest relative difference of any term's correlator between them."""
+    of each scheduler (at the storage size of --precision) and the host
+    build time; with --gpu also the time-to-solution of both DAGs (leaves
+    on the device; mixed precisions autotuned) and the largest relative
+    difference of any term's correlator between them."""
     import paper_2511_02257_b300 as L
     import synth
     ap = argparse.ArgumentParser()
     ap.add_argument("--workloads", default="multi_meson,baryon,memory_pressure")
     ap.add_argument("--policies", default="naive,sibling,tree,rsgs,node")
+    ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--gpu", action="store_true")
     ap.add_argument("--steps", type=int, default=3)
     args = ap.parse_args(argv)
+    eb = 16 if args.precision == "fp64" else 8
     for name in args.workloads.split(","):
         wl = synth.make_workload(name)
         nl = len(wl.leaves)
@@ -327,11 +331,12 @@ def paths_bench(argv):
         rows = {}
         for arm in ("generator", "paths"):
             t0 = time.perf_counter()
-            nd, ids = L.build_dag(wl, with_data=False, paths=(arm == "paths"))
+            nd, ids = L.build_dag(wl, precision=args.precision, with_data=False,
+                                  paths=(arm == "paths"))
             t_build = time.perf_counter() - t0
-            row = {"workload": name, "arm": arm, "terms": len(wl.graphs),
-                   "contractions": nd.num_nodes() - nl, "build_s": t_build,
-                   "tflop": dag_contraction_flops(nd) / 1e12}
+            row = {"workload": name, "arm": arm, "precision": args.precision,
+                   "terms": len(wl.graphs), "contractions": nd.num_nodes() - nl,
+                   "build_s": t_build, "tflop": dag_contraction_flops(nd, eb) / 1e12}
             for pol in args.policies.split(","):
                 st = nd.schedule(pol, "lru", 0)
                 row["peak_exec_gib_" + pol] = st["peak_exec"] / 2 ** 30
@@ -344,16 +349,21 @@ def paths_bench(argv):
             vals = {}
             for arm in ("generator", "paths"):
                 row, _ = rows[arm]
-                nd, ids = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: leaves[li],
-                                      paths=(arm == "paths"))
+                nd, ids = L.build_dag(wl, precision=args.precision,
+                                      leaf_data_fn=lambda li: leaves[li], paths=(arm == "paths"))
                 nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
                 nd.schedule("tree", "lru", wl.budget_bytes)
-                nd.stage_leaves(stream)
-                best = nd.autotune(stream, reps=2)[0]
-                nd.unstage_leaves()
-                t, _, info = _time_arm(nd, stream, args.steps, True)
+                best = None
+                if args.precision != "fp64":
+                    nd.stage_leaves(stream)
+                    best = nd.autotune(stream, reps=2)[0]
+                    nd.unstage_leaves()
+                t, flat, info = _time_arm(nd, stream, args.steps, True)
+                roots = nd.roots()                    # ascending id; one Lt for all
+                row_of = {r: i for i, r in enumerate(roots)}
+                per_root = flat.reshape(len(roots), -1)
                 term_roots = [ids[r] for r in gen_roots] if arm == "generator" else ids[nl:]
-                vals[arm] = np.stack([nd.read_correlator(r) for r in term_roots])
+                vals[arm] = np.stack([per_root[row_of[r]] for r in term_roots])
                 row.update({"time_to_solution_s": t, "tflops": info["flops"] / t / 1e12,
                             "autotune_best": best})
                 nd.close()

@@ -61,6 +61,10 @@ SHAPES = {
     "pxm": lambda n: ((4, 4, n, n), (n, n), (3,), (0,)),             # propagator x meson
     "mxm": lambda n: ((n, n), (n, n), (1,), (0,)),                   # meson x meson
     "bxb": lambda n: ((n, n, n), (n, n, n), (1, 2), (0, 1)),         # baryon x baryon, 2 legs
+    # meson x propagator over the propagator's first distillation axis, in
+    # both operand orders (M = N_dist, N = 16 N_dist and the transpose)
+    "mxp": lambda n: ((n, n), (4, 4, n, n), (1,), (2,)),
+    "pxm2": lambda n: ((4, 4, n, n), (n, n), (2,), (1,)),
 }
 
 

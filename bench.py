@@ -13,8 +13,11 @@ Prints one JSON line (rank 0).  ``value`` = algorithmic complex TFLOP/s
 device memory; ``e2e`` = the same metric through the public C ABI with the
 leaves loaded from the library's pinned host store every step and all
 correlators read back to the host.  N>1 runs independent replicas (one DAG
-per rank, weak scaling).  ``--impl reference`` times the CPU oracle on this
-host's cores on a bounded sample of the same workload.
+per rank, weak scaling), or with ``--shard lt`` one DAG split over the ranks
+along the time-slice axis (each rank executes its slices of every tensor
+under its share of the budget; the root values are gathered at the end of
+every end-to-end step; strong scaling).  ``--impl reference`` times the CPU
+oracle on this host's cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -71,6 +74,8 @@ def parse():
                     help="with --autotune 0: LQC_OPT_FUSED_MAX_N of the mixed path")
     ap.add_argument("--split-policy", type=int, default=0,
                     help="with --autotune 0: LQC_OPT_SPLIT_POLICY of the mixed path")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "lt"],
+                    help="N>1: independent replicas, or one DAG split over the time slices")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -88,6 +93,21 @@ def max_over_ranks(x: float, ws: int) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(x, ws: int):
+    """Sum over the ranks of a number or of a list of numbers, element by
+    element (same device rule as max_over_ranks)."""
+    many = isinstance(x, (list, tuple))
+    if ws <= 1:
+        return [float(v) for v in x] if many else float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in x] if many else [float(x)], dtype=torch.float64,
+                     device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().tolist() if many else float(t.item())
 
 
 def dist_init():
@@ -315,11 +335,19 @@ def main():
         if ws > 1:
             dist.barrier()
 
-    wl = synth.make_workload(args.workload, seed=rank)
-    budget = wl.budget_bytes
+    from paper_2511_02257_b300 import shard as SH
+    sharded = args.shard == "lt" and ws > 1
+    shard = (rank, ws) if sharded else None
+    wl = synth.make_workload(args.workload, seed=0 if sharded else rank)
+    t_lo, t_hi = SH.lt_slices(wl.lt, ws)[rank] if sharded else (0, wl.lt)
+    lt_share = (t_hi - t_lo) / wl.lt
+    budget = SH.shard_budget(wl.budget_bytes, wl.lt, t_hi - t_lo) if sharded else \
+        wl.budget_bytes
+
+    def leaf_fn(li):      # whole leaves; build_dag keeps a shard's own slices
+        return synth.leaf_data(wl, li)
     t0 = time.perf_counter()
-    nd, ids = L.build_dag(wl, precision=args.precision,
-                          leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd, ids = L.build_dag(wl, precision=args.precision, leaf_data_fn=leaf_fn, shard=shard)
     t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
     planned = nd.schedule(args.policy, args.evict, budget)
@@ -357,7 +385,10 @@ def main():
     corr = nd.read_all_correlators()
     ms = max_over_ranks(ms, ws)
     flops_step = info1["flops"]
-    value = ws * flops_step * args.steps / (ms * 1e-3) / 1e12
+    # work of one step over all ranks: replicas each run a whole DAG; shards
+    # together run one
+    job_flops = sum_over_ranks(flops_step, ws)
+    value = job_flops * args.steps / (ms * 1e-3) / 1e12
     # dominant kernel: the exterior contraction
     n_c = info1["n_contract"] - info0["n_contract"]
     ms_c = info1["ms_contract"] - info0["ms_contract"]
@@ -375,25 +406,31 @@ def main():
         nd.unstage_leaves()
         nd.execute(stream)
         out = nd.read_all_correlators()
+        if sharded:   # each root's full batch extent: the sum of its ranks' slices
+            root_lts = [int(v) for v in sum_over_ranks([nd.node_info(r)["lt"]
+                                                        for r in nd.roots()], ws)]
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             nd.execute(stream)
             nd.read_all_correlators(out)
+            if sharded:
+                full = SH.gather_correlators(out, root_lts, ws, device="cuda")
         t_e2e = time.perf_counter() - t0
         t_e2e = max_over_ranks(t_e2e, ws)
         st = nd.stats()
-        e2e = {"value": ws * flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": job_flops * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": st["h2d_bytes"],
                "d2h_bytes_per_step": st["d2h_bytes"] + out.nbytes,
                "ms_per_step": 1e3 * t_e2e / args.steps}
+        if sharded:
+            e2e["gathered_values"] = int(np.asarray(full).size)
 
     # ---- the precision form on the same workload, against this FP64 run
     pform = None
     if args.precision == "fp64" and args.compare != "none":
-        md, _ = L.build_dag(wl, precision=args.compare,
-                            leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+        md, _ = L.build_dag(wl, precision=args.compare, leaf_data_fn=leaf_fn, shard=shard)
         mplanned = md.schedule(args.policy, args.evict, budget)
         md.stage_leaves(stream)
         md.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
@@ -432,6 +469,10 @@ def main():
     from paper_2511_02257_b300.roofline import (FP64_NOMINAL_TFLOPS, TENSOR_RATIO,
                                                  dag_roofline_for, measured_peaks)
     droof = dag_roofline_for(wl, ids, args.precision, ms / args.steps / 1e3)
+    if sharded:   # this rank's slices: every contraction's work and bytes scale with them
+        for k in ("time_s", "compute_bound_s", "memory_bound_s", "flops"):
+            droof[k] *= lt_share
+        droof["frac"] = droof["time_s"] / (ms / args.steps / 1e3)
     if pform:
         pform["dag_roofline"] = dag_roofline_for(wl, ids, args.compare,
                                                  pform["time_to_solution_s"])
@@ -463,7 +504,8 @@ def main():
         line = {
             "metric": "dag_complex_tflops", "value": value, "unit": "TFLOP/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64",
             "data": "synthetic",
             "config": {"workload": args.workload, "lt": wl.lt, "nvec": wl.nvec,
@@ -476,7 +518,8 @@ def main():
                        "fused_max_n": (tuned["best"]["fused_max_n"] if tuned else args.fused_max_n),
                        "split_policy": (tuned["best"]["split_policy"] if tuned
                                         else args.split_policy),
-                       "parallelism": "replicas" if ws > 1 else "single",
+                       "parallelism": ("lt-shard" if sharded else "replicas") if ws > 1
+                                      else "single",
                        "l2": "inputs larger than L2 (leaves %.2f GB, arena %.2f GB)"
                              % (sum(nd.node_info(i)["size"] for i in range(len(wl.leaves))) / 1e9,
                                 info1["arena_bytes"] / 1e9)},

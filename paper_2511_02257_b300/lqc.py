@@ -392,19 +392,28 @@ class Dag:
 
 
 def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=None,
-              paths: bool = False):
+              paths: bool = False, shard=None):
     """Feed a ``synth.Workload`` request stream into a new Dag.
 
     Returns (dag, ids) where ids maps stream index -> node id.  With
     ``paths`` the contractions come from path selection over the workload's
-    graphs instead (Sec. II-A) and ids lists the leaf ids then the roots."""
-    d = Dag(wl.lt, precision)
+    graphs instead (Sec. II-A) and ids lists the leaf ids then the roots.
+    With ``shard=(rank, world)`` the Dag holds only this rank's time slices
+    of every tensor (``shard.lt_slices`` of each leaf's batch extent; leaf
+    data sliced accordingly)."""
+    from .shard import lt_slices
+    rank, world = shard if shard is not None else (0, 1)
+    t0, t1 = lt_slices(wl.lt, world)[rank]
+    d = Dag(t1 - t0, precision)
     ids = []
     for li, lf in enumerate(wl.leaves):
+        a, b = lt_slices(wl.leaf_lt(li), world)[rank]
         data = None
-        if with_data:
-            data = leaf_data_fn(li) if leaf_data_fn else None
-        ids.append(d.add_leaf(lf.extents, data, lt=wl.leaf_lt(li)))
+        if with_data and leaf_data_fn:
+            data = leaf_data_fn(li)
+            if world > 1:
+                data = data[a:b]
+        ids.append(d.add_leaf(lf.extents, data, lt=b - a))
     if paths:
         return d, ids + d.add_graphs([([ids[v] for v in items], edges)
                                       for items, edges in wl.graphs])

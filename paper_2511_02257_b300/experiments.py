@@ -10,7 +10,7 @@ compared bit for bit (each node's arithmetic is fixed; an eviction is a
 copy), so a schedule can change the time but never a result.
 
   python -m paper_2511_02257_b300.experiments [--workload memory_pressure]
-         [--precision tf32x3] [--evict lru] [--steps 2] [--budget-gib 24]
+         [--precision tf32x3] [--evict lru] [--steps 2] [--budget-gib 24[,8]] [--paths]
 
 Prints one JSON line per policy, then a summary line with ratios to the
 naive order.
@@ -399,8 +399,11 @@ def main():
     ap.add_argument("--evict", default="lru")
     ap.add_argument("--policies", default="naive,sibling,tree")
     ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--budget-gib", type=float, default=None)
+    ap.add_argument("--budget-gib", default=None,
+                    help="device budget(s) in GiB, comma-separated (default: the workload's)")
     ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--paths", action="store_true",
+                    help="build the DAG by contraction-path selection over the workload's terms")
     args = ap.parse_args()
 
     import torch
@@ -408,15 +411,23 @@ def main():
     import synth
 
     wl = synth.make_workload(args.workload)
-    budget = int(args.budget_gib * 2 ** 30) if args.budget_gib is not None else wl.budget_bytes
+    budgets = [int(float(b) * 2 ** 30) for b in args.budget_gib.split(",")] \
+        if args.budget_gib is not None else [wl.budget_bytes]
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         leaves = list(ex.map(lambda li: synth.leaf_data(wl, li), range(len(wl.leaves))))
     t_gen = time.perf_counter() - t0
-    nd, _ = L.build_dag(wl, precision=args.precision, leaf_data_fn=lambda li: leaves[li])
+    nd, _ = L.build_dag(wl, precision=args.precision, leaf_data_fn=lambda li: leaves[li],
+                        paths=args.paths)
     del leaves
     stream = torch.cuda.current_stream().cuda_stream
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
+    for budget in budgets:
+        _compare_policies(args, wl, nd, budget, stream, t_gen)
+
+
+def _compare_policies(args, wl, nd, budget, stream, t_gen):
+    import torch
     ref = None
     rows = []
     for pol in args.policies.split(","):
@@ -442,7 +453,8 @@ def main():
         else:
             same = bool(np.array_equal(vals.view(np.float64), ref.view(np.float64)))
         row = {
-            "workload": args.workload, "precision": args.precision, "policy": pol,
+            "workload": args.workload, "paths": bool(args.paths),
+            "precision": args.precision, "policy": pol,
             "evict": args.evict, "budget_bytes": budget, "contractions": len(nd.order()),
             "schedule_ms": 1e3 * t_sched,
             "peak_paper_gib": planned["peak_paper"] / 2 ** 30,
@@ -461,7 +473,7 @@ def main():
         rows.append(row)
         print(json.dumps(row), flush=True)
     base = rows[0]
-    summary = {"summary": "ratios to %s" % base["policy"]}
+    summary = {"summary": "ratios to %s" % base["policy"], "budget_bytes": budget}
     for r in rows[1:]:
         summary[r["policy"]] = {
             k: (base[k] / r[k] if r[k] else None)

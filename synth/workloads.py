@@ -68,7 +68,7 @@ class Workload:
     # every term as a graph before any bracketing: (leaf indices of its
     # items, edges (item a, axis of a, item b, axis of b), one per index
     # pair), in the order of the diagrams; graph_functions[f] lists the
-    # graphs of function f (empty for workloads built from parts)
+    # graphs of function f (a batched workload concatenates its parts')
     graphs: List[Tuple[List[int], List[Tuple[int, int, int, int]]]] = \
         dataclasses.field(default_factory=list)
     graph_functions: List[List[int]] = dataclasses.field(default_factory=list)
@@ -338,6 +338,8 @@ def _make_batched(rc: BatchedRecipe, seed: int) -> Workload:
             leaves.append(Leaf(lf.kind, lf.extents, len(leaves), lt, n))
     requests: List[Request] = []
     functions: List[List[int]] = []
+    graphs: List[Tuple[List[int], List[Tuple[int, int, int, int]]]] = []
+    graph_functions: List[List[int]] = []
     n_leaves = len(leaves)
     for loff, sub in parts:
         roff = n_leaves + len(requests)
@@ -347,9 +349,13 @@ def _make_batched(rc: BatchedRecipe, seed: int) -> Workload:
         for rq in sub.requests:
             requests.append(Request(remap(rq.left), remap(rq.right), rq.la, rq.ra))
         functions.extend([[remap(r) for r in f] for f in sub.functions])
+        goff = len(graphs)
+        graphs.extend([([loff + i for i in items], list(edges)) for items, edges in sub.graphs])
+        graph_functions.extend([[goff + g for g in fn] for fn in sub.graph_functions])
     return Workload(name=rc.name, lt=leaves[0].lt, nvec=max(lf.nvec for lf in leaves),
                     leaves=leaves, requests=requests, functions=functions,
-                    budget_bytes=rc.budget_bytes, seed=seed)
+                    budget_bytes=rc.budget_bytes, seed=seed, graphs=graphs,
+                    graph_functions=graph_functions)
 
 
 def make_workload(name: str, seed: int = 0, **overrides) -> Workload:

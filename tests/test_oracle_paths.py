@@ -49,7 +49,9 @@ def test_shared_pair_selected_first():
 
 
 @pytest.mark.parametrize("name,kw", [("tiny", {}), ("multi_meson", dict(n_functions=12, nvec=6, lt=3)),
-                                     ("baryon", dict(n_functions=10, nvec=5, lt=2))])
+                                     ("baryon", dict(n_functions=10, nvec=5, lt=2)),
+                                     ("batched", dict(n_dags=3, nvecs=(4, 6), lts=(2, 3),
+                                                      n_functions=5))])
 def test_paths_give_the_generators_values(name, kw):
     wl = synth.make_workload(name, **kw)
     od, ids = D.build_from_workload(wl)

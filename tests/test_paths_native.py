@@ -93,7 +93,9 @@ def _build_both(ranks, graphs, n, lt):
                                      ("multi_meson", dict(n_functions=40, seed=3)),
                                      ("baryon", dict(n_functions=10, nvec=5, lt=2)),
                                      ("baryon", dict(n_functions=30, seed=1)),
-                                     ("memory_pressure", dict(n_functions=20))])
+                                     ("memory_pressure", dict(n_functions=20)),
+                                     ("batched", dict(n_dags=6, nvecs=(16, 32), lts=(4, 8),
+                                                      n_functions=10))])
 def test_paths_bit_exact_workloads(name, kw):
     wl = synth.make_workload(name, **kw)
     od, oroots = PS.build_with_paths(wl)

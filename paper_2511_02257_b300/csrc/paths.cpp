@@ -37,6 +37,7 @@ namespace {
 
 using Label = std::pair<int32_t, int32_t>;  // (vertex of the graph, axis)
 using Key = std::tuple<int64_t, int64_t, std::vector<int>, std::vector<int>>;
+using Wide = __int128;  // costs and values: exact for any extents (no overflow)
 
 struct Vertex {
   int64_t node;
@@ -46,7 +47,8 @@ struct Vertex {
 struct Cand {
   int x, y;  // vertex indices, x < y
   Key key;
-  int64_t cost, out_elems;
+  Wide cost;
+  int64_t out_elems;
   const Vertex* left;
   const Vertex* right;
 };
@@ -89,7 +91,7 @@ bool candidate(const lqc::Dag& g, const Vertex& p, const Vertex& q,
   for (int a : la) k *= ln.ext[a];
   const int64_t m = ln.elems / k, n = rn.elems / k;
   c->key = Key(L.node, R.node, la, ra);
-  c->cost = ln.lt * m * n * k;
+  c->cost = (Wide)ln.lt * m * n * k;
   c->out_elems = m * n;
   c->left = &L;
   c->right = &R;
@@ -177,25 +179,26 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
     // only the graphs it contracts in, so only their keys are recounted.
     // The result equals recounting every graph at every step.
     struct KeyStat {
-      int64_t count = 0, cost = 0;
+      int64_t count = 0;
+      Wide cost = 0;
       std::set<int64_t> graphs;
     };
     std::map<Key, KeyStat> stat;
-    std::set<std::pair<int64_t, Key>> by_value;  // (-value, key): first = best
+    std::set<std::pair<Wide, Key>> by_value;  // (-value, key): first = best
     std::vector<std::vector<Key>> held((size_t)n_graphs);
     auto enter = [&](int64_t gi) {
       const Graph& G = graphs[gi];
       held[gi].clear();
       if (G.verts.size() < 2) return;
-      std::map<Key, int64_t> seen;
+      std::map<Key, Wide> seen;
       for (const Cand& c : candidates(g, G)) seen[c.key] = c.cost;
       for (auto& kv : seen) {
         KeyStat& ks = stat[kv.first];
-        if (ks.count) by_value.erase({-ks.count * ks.cost, kv.first});
+        if (ks.count) by_value.erase({-(ks.count * ks.cost), kv.first});
         ks.count += 1;
         ks.cost = kv.second;
         ks.graphs.insert(gi);
-        by_value.insert({-ks.count * ks.cost, kv.first});
+        by_value.insert({-(ks.count * ks.cost), kv.first});
         held[gi].push_back(kv.first);
       }
     };
@@ -203,11 +206,11 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
       for (const Key& k : held[gi]) {
         auto it = stat.find(k);
         KeyStat& ks = it->second;
-        by_value.erase({-ks.count * ks.cost, k});
+        by_value.erase({-(ks.count * ks.cost), k});
         ks.count -= 1;
         ks.graphs.erase(gi);
         if (ks.count)
-          by_value.insert({-ks.count * ks.cost, k});
+          by_value.insert({-(ks.count * ks.cost), k});
         else
           stat.erase(it);
       }

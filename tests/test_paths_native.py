@@ -211,3 +211,20 @@ def test_path_selected_dag_vs_oracle(precision, tol, name, kw):
     errs = [np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r])
             for r in sorted(set(oroots))]
     assert max(errs) < tol, max(errs)
+
+
+def test_paths_values_beyond_int64():
+    """Extents whose contraction costs times their counts exceed 2^63: the
+    native selection keeps exact values (128-bit) like the oracle's
+    integers, so both pick the same keys."""
+    n, lt = 1 << 20, 8
+    od, nd = D.Dag(lt), L.Dag(lt)
+    for i in range(4):
+        od.add_leaf((n, n), leaf_index=i)
+        nd.add_leaf((n, n))
+    ring = [(0, 1, 1, 0), (1, 1, 2, 0), (0, 0, 2, 1)]
+    graphs = [([0, 1, 2], ring), ([3, 1, 2], ring), ([0, 3, 2], ring), ([1, 2, 3], ring)]
+    oroots = PS.select_paths(od, graphs)
+    assert 2 * lt * n ** 3 > 2 ** 63            # count x cost of the shared pair
+    assert nd.add_graphs(graphs) == oroots
+    assert _structure_native(nd) == _structure_oracle(od)

@@ -6,8 +6,11 @@
  * (batch axis = time slice Lt, contracted axes = distillation / spin
  * indices) run in the order chosen by a peak-memory-minimising scheduler
  * (the paper's tree scheduler, Alg. 4-8, or sibling scheduler, Alg. 1-3,
- * or a naive topological order), under a fixed device-memory budget with
- * eviction of tensors to pinned host memory.
+ * or a naive topological order; also a node-based gain order and a
+ * similarity order of trees), under a fixed device-memory budget with
+ * eviction of tensors to pinned host memory.  A DAG is built from explicit
+ * contractions or, by contraction-path selection (Sec. II-A), from each
+ * term's tensor graph.
  *
  * Conventions shared by every call
  *  - Every call returns an lqc_status.  Out-parameters are written only on

@@ -152,6 +152,7 @@ def test_add_graphs_argument_errors():
     a = nd.add_leaf((3, 3))
     b = nd.add_leaf((3, 4))
     c = nd.add_leaf((3,))
+    corr = nd.add_contraction(a, a, [0, 1], [1, 0])
     cases = [
         [([a], [(0, 0, 1, 0)])],                      # vertex index out of range
         [([a, b], [(0, 5, 1, 0)])],                   # axis out of range
@@ -160,6 +161,8 @@ def test_add_graphs_argument_errors():
         [([a, b, c], [(0, 0, 1, 0)])],                # c is not connected
         [([a, 99], [(0, 0, 1, 0)])],                  # not a node
         [([a, a], [(0, 0, 0, 1)])],                   # an edge within one vertex
+        [([a, corr], [])],                            # a correlator (rank 0) as a vertex
+        [([a, b], [(-1, 0, 1, 0)])],                  # negative vertex index
     ]
     for graphs in cases:
         with pytest.raises(L.LqcError) as ei:

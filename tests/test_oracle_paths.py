@@ -70,3 +70,31 @@ def test_paths_give_the_generators_values(name, kw):
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a), (name, g)
     # the path-selected DAG merges at least as much as it emits
     assert len(pd.non_leaf()) <= sum(len(e) for _, e in wl.graphs)
+
+
+def test_orientation_larger_tensor_left():
+    """The orientation reading: the tensor with more elements is the left
+    operand (M >= N), whatever the vertex order or node ids.  A meson M
+    [n][n] traced against the distillation axes of a propagator P
+    [4][4][n][n] leaves the spin axes open: the one contraction has P on
+    the left, its pairs sorted by P's axes."""
+    n, lt = 3, 2
+    for m_first in (True, False):
+        dag = D.Dag(lt)
+        if m_first:
+            Mn = dag.add_leaf((n, n), leaf_index=0)
+            Pn = dag.add_leaf((4, 4, n, n), leaf_index=1)
+        else:
+            Pn = dag.add_leaf((4, 4, n, n), leaf_index=0)
+            Mn = dag.add_leaf((n, n), leaf_index=1)
+        # vertices [M, P]: M.dout - P.din, P.dout - M.din
+        roots = PS.select_paths(dag, [([Mn, Pn], [(0, 1, 1, 2), (1, 3, 0, 0)])])
+        node = dag.nodes[roots[0]]
+        assert (node.left, node.right, node.la, node.ra) == (Pn, Mn, (2, 3), (1, 0))
+        assert node.extents == (4, 4)
+        rng = np.random.default_rng(1)
+        mv = rng.standard_normal((lt, n, n)) + 1j * rng.standard_normal((lt, n, n))
+        pv = rng.standard_normal((lt, 4, 4, n, n)) + 1j * rng.standard_normal((lt, 4, 4, n, n))
+        got = C.evaluate(dag, lambda u: mv if u == Mn else pv, roots)[roots[0]]
+        want = np.einsum("tab,tsuba->tsu", mv, pv)
+        assert np.allclose(got, want, rtol=1e-12, atol=0)

@@ -231,3 +231,15 @@ def test_paths_values_beyond_int64():
     assert 2 * lt * n ** 3 > 2 ** 63            # count x cost of the shared pair
     assert nd.add_graphs(graphs) == oroots
     assert _structure_native(nd) == _structure_oracle(od)
+
+
+def test_orientation_larger_tensor_left_native():
+    n, lt = 3, 2
+    for m_first in (True, False):
+        nd = L.Dag(lt)
+        if m_first:
+            Mn, Pn = nd.add_leaf((n, n)), nd.add_leaf((4, 4, n, n))
+        else:
+            Pn, Mn = nd.add_leaf((4, 4, n, n)), nd.add_leaf((n, n))
+        r = nd.add_graphs([([Mn, Pn], [(0, 1, 1, 2), (1, 3, 0, 0)])])[0]
+        assert nd.node_operands(r) == (Pn, Mn, (2, 3), (1, 0))

@@ -159,18 +159,21 @@ typedef struct {
   double ms;             /* device time per execute (CUDA events) */
 } lqc_tune_entry;
 
-/* Create an empty DAG.  lt >= 1 time slices (the batch extent of the
- * leaves registered next, see lqc_dag_set_batch); prec selects storage and
- * arithmetic.  *out receives the handle (owned by the caller, released with
- * lqc_dag_destroy). */
+/* Create an empty DAG.  lt in [1, 2^31) time slices (the batch extent of
+ * the leaves registered next, see lqc_dag_set_batch); prec selects storage
+ * and arithmetic.  *out receives the handle (owned by the caller, released
+ * with lqc_dag_destroy).
+ * Size limits of every tensor: at most 2^40 elements per time slice and
+ * 2^58 over all slices (checked as nodes are added, before any product can
+ * overflow). */
 int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec);
 
 /* Batch extent (time slices) of the leaves registered after this call.
  * Lets one DAG hold several independent problems with different lt (a
  * batched workload): a contraction's operands must share one batch extent,
  * which its output inherits; a node's size (Sec. II-C) is lt_node *
- * prod(extents) * element bytes.  Errors: LQC_ERR_ARG (lt < 1),
- * LQC_ERR_STATE (after lqc_dag_schedule). */
+ * prod(extents) * element bytes.  Errors: LQC_ERR_ARG (lt outside
+ * [1, 2^31)), LQC_ERR_STATE (after lqc_dag_schedule). */
 int lqc_dag_set_batch(lqc_dag* dag, int64_t lt);
 
 /* Release every host and device resource of the DAG.  Synchronises with any
@@ -186,8 +189,8 @@ int lqc_dag_destroy(lqc_dag* dag);
  *  into the library's pinned host store (mixed precisions store them
  *  normalised to complex64, see lqc_precision); the caller keeps ownership
  *  of `data`.  *node_id receives the new id.
- *  Errors: LQC_ERR_ARG (rank/extents), LQC_ERR_HOST_MEM, LQC_ERR_STATE
- *  (after lqc_dag_schedule). */
+ *  Errors: LQC_ERR_ARG (rank/extents, size limits of lqc_dag_create),
+ *  LQC_ERR_HOST_MEM, LQC_ERR_STATE (after lqc_dag_schedule). */
 int lqc_dag_add_leaf_tensor(lqc_dag* dag, int rank, const int64_t* extents,
                             const double* data, int64_t* node_id);
 
@@ -201,7 +204,8 @@ int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
  *  la[i] (axis of left) is contracted with ra[i] (axis of right), extents
  *  equal, axes distinct on each side; both operands have the same batch
  *  extent (else LQC_ERR_ARG).  The output rank is
- *  rank(left) + rank(right) - 2*npairs and must not exceed LQC_MAX_RANK.
+ *  rank(left) + rank(right) - 2*npairs and must not exceed LQC_MAX_RANK;
+ *  the output obeys the size limits of lqc_dag_create.
  *  A request identical to an earlier one (same left, right, la, ra) returns
  *  the earlier node's id: identical sub-contractions of different trees are
  *  merged into one DAG node.  A rank-0 output must not be an operand of a

@@ -77,10 +77,17 @@ int copy_out(lqc_dag* h, const std::vector<T>& v, T* dst, int64_t cap, int64_t* 
 
 }  // namespace
 
+// Size limits: a slice holds at most 2^40 elements; a tensor (all slices)
+// at most 2^58, so byte sizes stay below 2^62; the batch extent fits the
+// kernels' 32-bit slice index.
+constexpr int64_t kMaxSliceElems = (int64_t)1 << 40;
+constexpr int64_t kMaxTensorElems = (int64_t)1 << 58;
+constexpr int64_t kMaxLt = ((int64_t)1 << 31) - 1;
+
 extern "C" {
 
 int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
-  if (!out || lt < 1) return LQC_ERR_ARG;
+  if (!out || lt < 1 || lt > kMaxLt) return LQC_ERR_ARG;
   if (prec != LQC_PREC_FP64 && prec != LQC_PREC_TF32X3 && prec != LQC_PREC_BF16X3)
     return LQC_ERR_ARG;
   try {
@@ -98,7 +105,7 @@ int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
 int lqc_dag_set_batch(lqc_dag* h, int64_t lt) {
   if (!h) return LQC_ERR_ARG;
   if (h->d.frozen) return fail(h, LQC_ERR_STATE, "DAG is frozen by lqc_dag_schedule");
-  if (lt < 1) return fail(h, LQC_ERR_ARG, "batch extent must be >= 1");
+  if (lt < 1 || lt > kMaxLt) return fail(h, LQC_ERR_ARG, "batch extent must be in [1, 2^31)");
   h->d.lt = lt;
   return LQC_OK;
 }
@@ -126,10 +133,11 @@ int lqc_dag_add_leaf_tensor(lqc_dag* h, int rank, const int64_t* extents, const 
   for (int i = 0; i < rank; ++i) {
     if (extents[i] < 1 || extents[i] > (int64_t)1 << 31)
       return fail(h, LQC_ERR_ARG, "leaf extent out of range");
+    if (n.elems > kMaxSliceElems / extents[i]) return fail(h, LQC_ERR_ARG, "leaf too large");
     n.ext[i] = extents[i];
     n.elems *= extents[i];
-    if (n.elems > ((int64_t)1 << 40)) return fail(h, LQC_ERR_ARG, "leaf too large");
   }
+  if (n.elems > kMaxTensorElems / n.lt) return fail(h, LQC_ERR_ARG, "leaf too large");
   g.nodes.push_back(n);
   int64_t id = (int64_t)g.nodes.size() - 1;
   if (data) {
@@ -188,11 +196,17 @@ int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs,
   n.lt = L.lt;
   n.rank = 0;
   n.elems = 1;
+  bool fits = true;
+  auto take = [&](int64_t e) {
+    n.ext[n.rank++] = e;
+    if (n.elems > kMaxSliceElems / e) fits = false;
+    else n.elems *= e;
+  };
   for (int a = 0; a < L.rank; ++a)
-    if (!usedL[a]) { n.ext[n.rank++] = L.ext[a]; n.elems *= L.ext[a]; }
+    if (!usedL[a]) take(L.ext[a]);
   for (int b = 0; b < R.rank; ++b)
-    if (!usedR[b]) { n.ext[n.rank++] = R.ext[b]; n.elems *= R.ext[b]; }
-  if (n.elems > ((int64_t)1 << 40)) return fail(h, LQC_ERR_ARG, "output too large");
+    if (!usedR[b]) take(R.ext[b]);
+  if (!fits || n.elems > kMaxTensorElems / n.lt) return fail(h, LQC_ERR_ARG, "output too large");
   g.nodes.push_back(n);
   const int64_t id = N;
   g.nodes[left].parents.push_back(id);

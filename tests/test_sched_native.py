@@ -167,3 +167,32 @@ def test_argument_errors():
     assert ei.value.code == L.LQC_ERR_STATE
     with pytest.raises(L.LqcError):
         d.set_order([c, c])
+
+
+def test_size_limits_without_overflow():
+    """Sizes are checked before they are multiplied: a slice holds at most
+    2^40 elements, a tensor at most 2^58, the batch extent is below 2^31;
+    rank-8 extents near 2^31 are rejected instead of wrapping around."""
+    with pytest.raises(L.LqcError):
+        L.Dag(1 << 31)
+    d = L.Dag(1)
+    with pytest.raises(L.LqcError) as ei:
+        d.set_batch(1 << 31)
+    assert ei.value.code == L.LQC_ERR_ARG
+    big = [(1 << 31)] * 8                      # product 2^248 per slice
+    with pytest.raises(L.LqcError) as ei:
+        d.add_leaf(big)
+    assert ei.value.code == L.LQC_ERR_ARG
+    a = d.add_leaf([1 << 20, 1 << 19, 2])      # 2^40 elements: at the limit
+    b = d.add_leaf([2, 1 << 20, 1 << 19])
+    ok = d.add_contraction(a, b, [0, 1], [1, 2])  # valid pairing, 2 x 2 output
+    assert d.node_info(ok)["rank"] == 2
+    with pytest.raises(L.LqcError) as ei:      # paired over the 2s only: 2^78 elements
+        d.add_contraction(a, b, [2], [0])
+    assert ei.value.code == L.LQC_ERR_ARG
+    assert "output too large" in str(ei.value)
+    d.set_batch(1 << 20)
+    with pytest.raises(L.LqcError) as ei:      # 2^20 slices x 2^40 elements
+        d.add_leaf([1 << 20, 1 << 20])
+    assert ei.value.code == L.LQC_ERR_ARG
+    d.add_leaf([1 << 19, 1 << 19])             # 2^20 x 2^38 = 2^58: at the limit

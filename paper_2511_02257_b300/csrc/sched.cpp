@@ -185,13 +185,26 @@ struct TreeSched {
   std::vector<int64_t> cgain, tgain;
   std::vector<uint8_t> state;
   std::vector<int64_t> outav;                 // |u.outAv|
+  // tau/delta of a node x per tree (Alg. 7-8), kept implicitly: tau =
+  // tau0 - in (parents of x in the tree processed so far), delta = delta0 -
+  // (pc - in) with pc = parents of x processed so far.  A tree's "delta
+  // reaches 0" event (case 2b) fires at the call that makes pc equal
+  // th = delta0 + in, so each entry waits in the bucket of its threshold
+  // and a call visits only the trees of its parent u (cases 1a-1c) and the
+  // bucket of the new pc, instead of every tree of x.
   struct Ent {
     int32_t tree;
-    int32_t tau;
-    int32_t delta;
-    uint8_t inpred;  // u in T_tree.pred
+    int32_t tau;     // tau0 - in
+    int32_t delta0;
+    int32_t in;
+    uint8_t inpred;  // x in T_tree.pred
   };
-  std::vector<std::vector<Ent>> S;            // tau/delta of u, set by PROCESS-NODE
+  struct XState {
+    std::vector<Ent> ent;                       // ascending tree id
+    std::vector<std::vector<int32_t>> bucket;   // threshold -> entry indices
+    int32_t pc = 0;
+  };
+  std::vector<XState> S;                      // set by PROCESS-NODE
   std::vector<int32_t> slot_of;               // scratch: tree -> index in S[u]
   std::vector<int64_t> slot_owner;
   std::vector<uint8_t> alive, dirty_flag;
@@ -237,17 +250,23 @@ struct TreeSched {
         }
       }
     }
-    // individual gains: g(u, T_i) = |outAv(u)| - #{parents of u in T_i}
+    // individual gains: g(u, T_i) = |outAv(u)| - #{parents of u in T_i};
+    // the parents in each tree are counted in one pass over the parents'
+    // tree lists (a parent's trees all contain u)
+    std::vector<int32_t> in_count(K, 0);
     for (int64_t u = 0; u < N; ++u) {
       const auto& cu = ctree[u];
+      const auto& par = g.nodes[u].parents;
+      for (int64_t v : par)
+        for (int32_t i : ctree[v]) ++in_count[i];
       igain[u].assign(cu.size(), 0);
       for (size_t k = 0; k < cu.size(); ++k) {
-        int64_t gcount = (int64_t)g.nodes[u].parents.size();
-        for (int64_t v : g.nodes[u].parents)
-          if (in_tree(v, cu[k])) --gcount;
+        const int64_t gcount = (int64_t)par.size() - in_count[cu[k]];
         igain[u][k] = gcount == 0 ? 0 : -g.size_bytes(u);
         tgain[cu[k]] += igain[u][k];
       }
+      for (int64_t v : par)
+        for (int32_t i : ctree[v]) in_count[i] = 0;
     }
     S.assign(N, {});
     slot_of.assign(K, -1);
@@ -259,25 +278,49 @@ struct TreeSched {
 
   void process_child(int64_t u, int64_t x) {  // Alg. 7
     const int64_t sz = g.size_bytes(x);
-    for (Ent& e : S[x]) {
+    XState& xs = S[x];
+    const int32_t pc_before = xs.pc++;
+    // cases 1a-1c: the trees of u (every one holds an entry of x)
+    for (int32_t i : ctree[u]) {
+      auto it = std::lower_bound(xs.ent.begin(), xs.ent.end(), i,
+                                 [](const Ent& e, int32_t t) { return e.tree < t; });
+      Ent& e = *it;
       if (!e.inpred) continue;
-      if (in_tree(u, e.tree)) {  // cases 1a-1c
-        if (e.tau == 1 && e.delta == 0) {
-          cgain[e.tree] -= sz;
-          tgain[e.tree] -= sz;
-          touch(e.tree);
-        }
-        if (--e.tau == 0) e.inpred = 0;
-      } else {  // cases 2a-2b
-        if (e.delta == 1) {
+      const int32_t delta = e.delta0 - (pc_before - e.in);
+      if (e.tau == 1 && delta == 0) {
+        cgain[i] -= sz;
+        tgain[i] -= sz;
+        touch(i);
+      }
+      ++e.in;
+      if (--e.tau == 0) {
+        e.inpred = 0;
+      } else {
+        // delta = th - pc: only a threshold still ahead can fire later (a
+        // tree whose outside parents are all processed has delta 0 for good)
+        const int32_t th = e.delta0 + e.in;
+        if (th > xs.pc && th < (int32_t)xs.bucket.size())
+          xs.bucket[th].push_back((int32_t)(it - xs.ent.begin()));
+      }
+    }
+    // cases 2a-2b: every other live tree loses one outside parent; delta
+    // goes 1 -> 0 for those whose threshold is the new pc
+    if (xs.pc < (int32_t)xs.bucket.size()) {
+      for (int32_t k : xs.bucket[xs.pc]) {
+        const Ent& e = xs.ent[k];
+        if (e.inpred && e.delta0 + e.in == xs.pc) {
           cgain[e.tree] += sz;
           tgain[e.tree] += sz;
           touch(e.tree);
         }
-        --e.delta;
       }
+      std::vector<int32_t>().swap(xs.bucket[xs.pc]);
     }
-    if (--outav[x] == 0) state[x] = TR_RELEASED;
+    if (--outav[x] == 0) {
+      state[x] = TR_RELEASED;
+      XState().ent.swap(xs.ent);
+      std::vector<std::vector<int32_t>>().swap(xs.bucket);
+    }
   }
 
   void process_node(int64_t u) {  // Alg. 8
@@ -291,27 +334,33 @@ struct TreeSched {
     }
     // every consumer of an AVAIL node is AVAIL, so u.outAv = u.parents here
     const int32_t n_out = (int32_t)outav[u];
-    std::vector<Ent>& su = S[u];
+    XState& xs = S[u];
+    std::vector<Ent>& su = xs.ent;
     su.clear();
     for (int64_t v : g.nodes[u].parents) {
       for (int32_t i : ctree[v]) {
         if (slot_owner[i] != u) {
           slot_owner[i] = u;
           slot_of[i] = (int32_t)su.size();
-          su.push_back(Ent{i, 0, n_out, 1});
+          su.push_back(Ent{i, 0, n_out, 0, 1});
         }
         Ent& e = su[slot_of[i]];
-        --e.delta;
+        --e.delta0;
         ++e.tau;
       }
     }
     for (Ent& e : su) {
-      if (e.delta == 0) {
+      if (e.delta0 == 0) {
         cgain[e.tree] += sz;
         tgain[e.tree] += sz;
         touch(e.tree);
       }
     }
+    std::sort(su.begin(), su.end(), [](const Ent& a, const Ent& b) { return a.tree < b.tree; });
+    xs.pc = 0;
+    xs.bucket.assign((size_t)n_out + 1, {});
+    for (size_t k = 0; k < su.size(); ++k)
+      if (su[k].delta0 >= 1) xs.bucket[su[k].delta0].push_back((int32_t)k);
     state[u] = outav[u] == 0 ? TR_RELEASED : TR_INMEM;
   }
 
@@ -456,7 +505,9 @@ std::vector<int64_t> schedule_rsgs(const Dag& g) {
     }
   }
   std::vector<uint8_t> done(N, 0), used(K, 0);
-  std::vector<int64_t> order, shared(K, 0);
+  std::vector<int64_t> order, shared(K, 0), seen(N, -1);
+  std::vector<int32_t> touched;
+  int64_t next_unused = 0;
   std::vector<std::pair<int64_t, bool>> walk;
   int64_t cur = K ? 0 : -1;
   while (cur >= 0) {
@@ -475,21 +526,29 @@ std::vector<int64_t> schedule_rsgs(const Dag& g) {
       walk.push_back({u, true});
       for (int k = n.n_children() - 1; k >= 0; --k) walk.push_back({n.child(k), false});
     }
-    // contractions shared by the tree just processed and every other tree
-    std::fill(shared.begin(), shared.end(), 0);
-    std::fill(stamp.begin(), stamp.end(), -1);
+    // contractions shared by the tree just processed and every other tree;
+    // only trees met here can share any, the rest count 0
+    touched.clear();
     stack.assign(1, roots[cur]);
     while (!stack.empty()) {
       const int64_t u = stack.back();
       stack.pop_back();
-      if (stamp[u] == cur || g.nodes[u].is_leaf()) continue;
-      stamp[u] = cur;
-      for (int32_t j : trees_of[u]) ++shared[j];
+      if (seen[u] == cur || g.nodes[u].is_leaf()) continue;
+      seen[u] = cur;
+      for (int32_t j : trees_of[u])
+        if (shared[j]++ == 0) touched.push_back(j);
       for (int k = 0; k < g.nodes[u].n_children(); ++k) stack.push_back(g.nodes[u].child(k));
     }
+    // the unused tree sharing the most, ties to the smallest index; with
+    // none sharing, the smallest unused index
     int64_t best = -1;
-    for (int64_t j = 0; j < K; ++j)
-      if (!used[j] && (best < 0 || shared[j] > shared[best])) best = j;
+    for (int32_t j : touched)
+      if (!used[j] && (best < 0 || shared[j] > shared[best] ||
+                       (shared[j] == shared[best] && j < best)))
+        best = j;
+    for (int32_t j : touched) shared[j] = 0;
+    while (next_unused < K && used[next_unused]) ++next_unused;
+    if (best < 0 && next_unused < K) best = next_unused;
     cur = best;
   }
   return order;

@@ -192,21 +192,24 @@ struct TreeSched {
   // th = delta0 + in, so each entry waits in the bucket of its threshold
   // and a call visits only the trees of its parent u (cases 1a-1c) and the
   // bucket of the new pc, instead of every tree of x.
-  struct Ent {
-    int32_t tree;
-    int32_t tau;     // tau0 - in
+  struct Ent {       // one per tree of x, aligned with ctree[x]
+    int32_t tau;     // tau0 - in; tau0 = parents of x in the tree
     int32_t delta0;
     int32_t in;
-    uint8_t inpred;  // x in T_tree.pred
+    uint8_t inpred;  // x in T_tree.pred (a tree without parents of x never is)
   };
   struct XState {
-    std::vector<Ent> ent;                       // ascending tree id
-    std::vector<std::vector<int32_t>> bucket;   // threshold -> entry indices
+    std::vector<Ent> ent;
+    std::vector<int32_t> head;                  // threshold -> first pool link, -1 = none
+    std::vector<std::pair<int32_t, int32_t>> pool;  // (entry, next link)
     int32_t pc = 0;
+    void bucket_push(int32_t th, int32_t k) {
+      pool.push_back({k, head[th]});
+      head[th] = (int32_t)pool.size() - 1;
+    }
   };
   std::vector<XState> S;                      // set by PROCESS-NODE
-  std::vector<int32_t> slot_of;               // scratch: tree -> index in S[u]
-  std::vector<int64_t> slot_owner;
+  std::vector<int32_t> pos_of;                // scratch: tree -> index in ctree[u]
   std::vector<uint8_t> alive, dirty_flag;
   std::vector<int32_t> dirty;
   std::vector<int64_t> visit_stamp;
@@ -269,8 +272,7 @@ struct TreeSched {
         for (int32_t i : ctree[v]) in_count[i] = 0;
     }
     S.assign(N, {});
-    slot_of.assign(K, -1);
-    slot_owner.assign(K, -1);
+    pos_of.assign(K, -1);
     alive.assign(K, 1);
     dirty_flag.assign(K, 0);
     visit_stamp.assign(N, -1);
@@ -280,11 +282,11 @@ struct TreeSched {
     const int64_t sz = g.size_bytes(x);
     XState& xs = S[x];
     const int32_t pc_before = xs.pc++;
-    // cases 1a-1c: the trees of u (every one holds an entry of x)
+    // cases 1a-1c: the trees of u (each is a tree of x)
+    const auto& cx = ctree[x];
     for (int32_t i : ctree[u]) {
-      auto it = std::lower_bound(xs.ent.begin(), xs.ent.end(), i,
-                                 [](const Ent& e, int32_t t) { return e.tree < t; });
-      Ent& e = *it;
+      const int32_t k = (int32_t)(std::lower_bound(cx.begin(), cx.end(), i) - cx.begin());
+      Ent& e = xs.ent[k];
       if (!e.inpred) continue;
       const int32_t delta = e.delta0 - (pc_before - e.in);
       if (e.tau == 1 && delta == 0) {
@@ -299,27 +301,28 @@ struct TreeSched {
         // delta = th - pc: only a threshold still ahead can fire later (a
         // tree whose outside parents are all processed has delta 0 for good)
         const int32_t th = e.delta0 + e.in;
-        if (th > xs.pc && th < (int32_t)xs.bucket.size())
-          xs.bucket[th].push_back((int32_t)(it - xs.ent.begin()));
+        if (th > xs.pc && th < (int32_t)xs.head.size()) xs.bucket_push(th, k);
       }
     }
     // cases 2a-2b: every other live tree loses one outside parent; delta
     // goes 1 -> 0 for those whose threshold is the new pc
-    if (xs.pc < (int32_t)xs.bucket.size()) {
-      for (int32_t k : xs.bucket[xs.pc]) {
+    if (xs.pc < (int32_t)xs.head.size()) {
+      for (int32_t l = xs.head[xs.pc]; l >= 0; l = xs.pool[l].second) {
+        const int32_t k = xs.pool[l].first;
         const Ent& e = xs.ent[k];
         if (e.inpred && e.delta0 + e.in == xs.pc) {
-          cgain[e.tree] += sz;
-          tgain[e.tree] += sz;
-          touch(e.tree);
+          const int32_t i = cx[k];
+          cgain[i] += sz;
+          tgain[i] += sz;
+          touch(i);
         }
       }
-      std::vector<int32_t>().swap(xs.bucket[xs.pc]);
     }
     if (--outav[x] == 0) {
       state[x] = TR_RELEASED;
       XState().ent.swap(xs.ent);
-      std::vector<std::vector<int32_t>>().swap(xs.bucket);
+      std::vector<int32_t>().swap(xs.head);
+      std::vector<std::pair<int32_t, int32_t>>().swap(xs.pool);
     }
   }
 
@@ -336,31 +339,31 @@ struct TreeSched {
     const int32_t n_out = (int32_t)outav[u];
     XState& xs = S[u];
     std::vector<Ent>& su = xs.ent;
-    su.clear();
+    su.assign(cu.size(), Ent{0, n_out, 0, 0});
+    for (size_t k = 0; k < cu.size(); ++k) pos_of[cu[k]] = (int32_t)k;
     for (int64_t v : g.nodes[u].parents) {
-      for (int32_t i : ctree[v]) {
-        if (slot_owner[i] != u) {
-          slot_owner[i] = u;
-          slot_of[i] = (int32_t)su.size();
-          su.push_back(Ent{i, 0, n_out, 0, 1});
-        }
-        Ent& e = su[slot_of[i]];
+      for (int32_t i : ctree[v]) {  // a parent's trees all hold u
+        Ent& e = su[pos_of[i]];
         --e.delta0;
         ++e.tau;
       }
     }
-    for (Ent& e : su) {
+    for (int32_t i : cu) pos_of[i] = -1;
+    xs.pc = 0;
+    xs.head.assign((size_t)n_out + 1, -1);
+    xs.pool.clear();
+    for (size_t k = 0; k < cu.size(); ++k) {
+      Ent& e = su[k];
+      if (e.tau == 0) continue;  // no parent of u in this tree: no entry
+      e.inpred = 1;
       if (e.delta0 == 0) {
-        cgain[e.tree] += sz;
-        tgain[e.tree] += sz;
-        touch(e.tree);
+        cgain[cu[k]] += sz;
+        tgain[cu[k]] += sz;
+        touch(cu[k]);
+      } else {
+        xs.bucket_push(e.delta0, (int32_t)k);
       }
     }
-    std::sort(su.begin(), su.end(), [](const Ent& a, const Ent& b) { return a.tree < b.tree; });
-    xs.pc = 0;
-    xs.bucket.assign((size_t)n_out + 1, {});
-    for (size_t k = 0; k < su.size(); ++k)
-      if (su[k].delta0 >= 1) xs.bucket[su[k].delta0].push_back((int32_t)k);
     state[u] = outav[u] == 0 ? TR_RELEASED : TR_INMEM;
   }
 
@@ -392,29 +395,59 @@ struct TreeSched {
     }
   }
 
+  // indexed binary max-heap of the alive trees on (tgain, -index): a
+  // changed gain is sifted in place, so the heap never holds stale entries.
+  // The heap compares its own copy of the gains (hkey), brought up to date
+  // one tree at a time, so every sift runs on a valid heap.
+  std::vector<int32_t> heap, hpos;
+  std::vector<int64_t> hkey;
+  bool above(int32_t a, int32_t b) const {  // a before b
+    return hkey[a] != hkey[b] ? hkey[a] > hkey[b] : a < b;
+  }
+  void hswap(size_t x, size_t y) {
+    std::swap(heap[x], heap[y]);
+    hpos[heap[x]] = (int32_t)x;
+    hpos[heap[y]] = (int32_t)y;
+  }
+  void sift_up(size_t x) {
+    while (x > 0 && above(heap[x], heap[(x - 1) / 2])) {
+      hswap(x, (x - 1) / 2);
+      x = (x - 1) / 2;
+    }
+  }
+  void sift_down(size_t x) {
+    for (;;) {
+      size_t b = x, l = 2 * x + 1, r = l + 1;
+      if (l < heap.size() && above(heap[l], heap[b])) b = l;
+      if (r < heap.size() && above(heap[r], heap[b])) b = r;
+      if (b == x) return;
+      hswap(x, b);
+      x = b;
+    }
+  }
+
   void run() {  // Alg. 4
     init();
-    // max-heap on (tgain, -index) with lazy invalidation
-    typedef std::pair<int64_t, int32_t> E;
-    auto cmp = [](const E& a, const E& b) {
-      if (a.first != b.first) return a.first < b.first;
-      return a.second > b.second;
-    };
-    std::priority_queue<E, std::vector<E>, decltype(cmp)> heap(cmp);
-    for (int32_t i = 0; i < K; ++i) heap.push({tgain[i], i});
+    heap.resize(K);
+    hpos.resize(K);
+    hkey = tgain;
+    for (int32_t i = 0; i < K; ++i) { heap[i] = i; hpos[i] = i; }
+    for (int32_t x = K / 2 - 1; x >= 0; --x) sift_down((size_t)x);
     for (int32_t step = 0; step < K; ++step) {
       for (int32_t i : dirty) {
         dirty_flag[i] = 0;
-        if (alive[i]) heap.push({tgain[i], i});
+        if (alive[i] && hkey[i] != tgain[i]) {
+          hkey[i] = tgain[i];
+          sift_up((size_t)hpos[i]);
+          sift_down((size_t)hpos[i]);
+        }
       }
       dirty.clear();
-      int32_t best = -1;
-      while (!heap.empty()) {
-        E e = heap.top();
-        heap.pop();
-        if (alive[e.second] && e.first == tgain[e.second]) { best = e.second; break; }
-      }
-      if (best < 0) throw std::runtime_error("tree scheduler: empty selection");
+      if (heap.empty()) throw std::runtime_error("tree scheduler: empty selection");
+      const int32_t best = heap[0];
+      hswap(0, heap.size() - 1);
+      heap.pop_back();
+      if (!heap.empty()) sift_down(0);
       alive[best] = 0;
       process_ctree(best);
     }

@@ -40,6 +40,11 @@ builds each workload's terms twice -- as the generator brackets them and by
 contraction-path selection (Sec. II-A) -- and reports distinct
 contractions, flops and every scheduler's peak; with --gpu also both DAGs'
 tuned TF32x3 time-to-solution and the largest difference of a term's value.
+
+  python -m paper_2511_02257_b300.experiments sched [--dags multi_meson:5000,...] [--reps 5]
+
+times each scheduler's order on the host for synthetic DAGs of the vertex
+counts of the paper's Table 2, with their trees, vertices, edges, F_v, F_e.
 """
 from __future__ import annotations
 
@@ -396,6 +401,67 @@ def paths_bench(argv):
         print(json.dumps(summ), flush=True)
 
 
+def dag_properties(nd) -> dict:
+    """The DAG columns of the paper's Table 2: trees (roots), vertices,
+    edges (operand -> consumer, distinct), F_v = average number of trees a
+    vertex belongs to, F_e = the same for edges (an edge belongs to the trees
+    holding its consumer)."""
+    n = nd.num_nodes()
+    kids = []
+    for u in range(n):
+        left, right, _, _ = nd.node_operands(u)
+        kids.append(() if left < 0 else ((left,) if left == right else (left, right)))
+    roots = nd.roots()
+    stamp = [-1] * n
+    ntrees = [0] * n
+    for i, r in enumerate(roots):
+        stack = [r]
+        while stack:
+            u = stack.pop()
+            if stamp[u] == i:
+                continue
+            stamp[u] = i
+            ntrees[u] += 1
+            stack.extend(kids[u])
+    edges = sum(len(k) for k in kids)
+    return {"trees": len(roots), "vertices": n, "edges": edges,
+            "F_v": sum(ntrees) / n,
+            "F_e": sum(ntrees[u] * len(kids[u]) for u in range(n)) / max(edges, 1)}
+
+
+def sched_bench(argv):
+    """Host time of each scheduler's order (the paper's Table 4) on synthetic
+    DAGs scaled to the vertex counts of the paper's Table 2: the median of
+    `--reps` calls of lqc_dag_schedule minus the plan replay of the same
+    order (lqc_dag_set_order), so that only the order is timed."""
+    import paper_2511_02257_b300 as L
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dags", default="multi_meson:1000,multi_meson:5000,multi_meson:20000,"
+                                      "baryon:3000,baryon:20000")
+    ap.add_argument("--policies", default="naive,rsgs,sibling,tree,node")
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args(argv)
+    for spec in args.dags.split(","):
+        name, nf = spec.split(":")
+        wl = synth.make_workload(name, n_functions=int(nf))
+        nd, _ = L.build_dag(wl, with_data=False)
+        row = {"workload": name, "functions": int(nf)}
+        row.update(dag_properties(nd))
+        for pol in args.policies.split(","):
+            ts = []
+            for _ in range(args.reps):
+                t0 = time.perf_counter()
+                nd.schedule(pol, "lru", 0)
+                t1 = time.perf_counter()
+                nd.set_order(nd.order(), "lru", 0)
+                t2 = time.perf_counter()
+                ts.append((t1 - t0) - (t2 - t1))
+            row["order_ms_" + pol] = 1e3 * max(float(np.median(ts)), 0.0)
+        print(json.dumps(row), flush=True)
+        nd.close()
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         return kernel_bench(sys.argv[2:])
@@ -403,6 +469,8 @@ def main():
         return batched_bench(sys.argv[2:])
     if len(sys.argv) > 1 and sys.argv[1] == "paths":
         return paths_bench(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "sched":
+        return sched_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

@@ -196,3 +196,15 @@ def test_size_limits_without_overflow():
         d.add_leaf([1 << 20, 1 << 20])
     assert ei.value.code == L.LQC_ERR_ARG
     d.add_leaf([1 << 19, 1 << 19])             # 2^20 x 2^38 = 2^58: at the limit
+
+
+@pytest.mark.parametrize("sched", ["tree", "rsgs", "sibling", "node"])
+def test_orders_bit_exact_large_dag(sched):
+    """A 9.5k-vertex DAG (3,580 trees, a leaf with 487 consumers):
+    the native schedulers' incremental bookkeeping (threshold buckets,
+    indexed heap, touched-tree scans) gives the oracle's orders."""
+    wl = synth.make_workload("multi_meson", n_functions=1000)
+    od, _ = D.build_from_workload(wl)
+    nd, _ = L.build_dag(wl, with_data=False)
+    nd.schedule(sched, "lru", 0)
+    assert nd.order() == S.SCHEDULERS[sched](od)

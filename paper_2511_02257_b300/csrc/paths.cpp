@@ -27,7 +27,7 @@
 #include <map>
 #include <set>
 #include <string>
-#include <tuple>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -35,84 +35,123 @@
 
 namespace {
 
-using Label = std::pair<int32_t, int32_t>;  // (vertex of the graph, axis)
-using Key = std::tuple<int64_t, int64_t, std::vector<int>, std::vector<int>>;
+// an axis of one of the graph's original vertices: vertex * LQC_MAX_RANK +
+// axis, so that code order is (vertex, axis) order
+using Label = int32_t;
 using Wide = __int128;  // costs and values: exact for any extents (no overflow)
+
+// (left node, right node, left axes, right axes), ordered like the tuple
+// (l, r, la, ra) with the axis lists compared lexicographically
+struct Key {
+  int64_t l = 0, r = 0;
+  int32_t n = 0;
+  int8_t la[LQC_MAX_RANK] = {0}, ra[LQC_MAX_RANK] = {0};
+  friend bool operator<(const Key& a, const Key& b) {
+    if (a.l != b.l) return a.l < b.l;
+    if (a.r != b.r) return a.r < b.r;
+    const int m = std::min(a.n, b.n);
+    for (int i = 0; i < m; ++i)
+      if (a.la[i] != b.la[i]) return a.la[i] < b.la[i];
+    if (a.n != b.n) return a.n < b.n;
+    for (int i = 0; i < a.n; ++i)
+      if (a.ra[i] != b.ra[i]) return a.ra[i] < b.ra[i];
+    return false;
+  }
+  friend bool operator==(const Key& a, const Key& b) {
+    return a.l == b.l && a.r == b.r && a.n == b.n && std::memcmp(a.la, b.la, a.n) == 0 &&
+           std::memcmp(a.ra, b.ra, a.n) == 0;
+  }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = (uint64_t)k.l * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)k.r + 0x632BE59BD9B4E019ULL);
+    for (int i = 0; i < k.n; ++i) h = (h ^ (uint64_t)(k.la[i] * 8 + k.ra[i] + 1)) * 0x100000001B3ULL;
+    return (size_t)(h ^ (h >> 29));
+  }
+};
 
 struct Vertex {
   int64_t node;
-  std::vector<Label> labels;  // every axis of the node, in axis order
+  int32_t nl = 0;
+  Label labels[LQC_MAX_RANK];  // every axis of the node, in axis order
+  Label min_label() const { return *std::min_element(labels, labels + nl); }
 };
 
 struct Cand {
-  int x, y;  // vertex indices, x < y
+  int x, y;     // vertex indices, x < y
+  bool x_left;  // the x vertex is the left operand
   Key key;
   Wide cost;
   int64_t out_elems;
-  const Vertex* left;
-  const Vertex* right;
 };
 
 struct Graph {
   std::vector<Vertex> verts;
-  std::map<Label, Label> partner;
+  std::vector<Label> partner;  // label -> paired label, -1 = open axis
   int64_t cap = 0;
 };
 
 bool candidate(const lqc::Dag& g, const Vertex& p, const Vertex& q,
-               const std::map<Label, Label>& partner, Cand* c) {
-  std::map<Label, int> qpos;
-  for (int j = 0; j < (int)q.labels.size(); ++j) qpos[q.labels[j]] = j;
-  std::vector<std::pair<int, int>> pairs;
-  for (int i = 0; i < (int)p.labels.size(); ++i) {
-    auto it = partner.find(p.labels[i]);
-    if (it == partner.end()) continue;
-    auto jt = qpos.find(it->second);
-    if (jt != qpos.end()) pairs.push_back({i, jt->second});
+               const std::vector<Label>& partner, Cand* c) {
+  int pi[LQC_MAX_RANK], qj[LQC_MAX_RANK], np = 0;
+  for (int i = 0; i < p.nl; ++i) {
+    const Label other = partner[p.labels[i]];
+    if (other < 0) continue;
+    for (int j = 0; j < q.nl; ++j)
+      if (q.labels[j] == other) {
+        pi[np] = i;
+        qj[np++] = j;
+        break;
+      }
   }
-  if (pairs.empty()) return false;
-  const Label pmin = *std::min_element(p.labels.begin(), p.labels.end());
-  const Label qmin = *std::min_element(q.labels.begin(), q.labels.end());
+  if (np == 0) return false;
   const int64_t pe = g.nodes[p.node].elems, qe = g.nodes[q.node].elems;
-  const bool p_left = std::make_tuple(-pe, p.node, pmin) <= std::make_tuple(-qe, q.node, qmin);
-  if (!p_left)
-    for (auto& pr : pairs) std::swap(pr.first, pr.second);
-  std::sort(pairs.begin(), pairs.end());
+  const Label pmin = p.min_label(), qmin = q.min_label();
+  const bool p_left = pe != qe ? pe > qe : (p.node != q.node ? p.node < q.node : pmin <= qmin);
   const Vertex& L = p_left ? p : q;
   const Vertex& R = p_left ? q : p;
-  std::vector<int> la, ra;
-  for (auto& pr : pairs) {
-    la.push_back(pr.first);
-    ra.push_back(pr.second);
+  Key& k = c->key;
+  k = Key();
+  k.l = L.node;
+  k.r = R.node;
+  k.n = np;
+  for (int t = 0; t < np; ++t) {  // pairs by ascending left axis
+    k.la[t] = (int8_t)(p_left ? pi[t] : qj[t]);
+    k.ra[t] = (int8_t)(p_left ? qj[t] : pi[t]);
   }
+  for (int t = 1; t < np; ++t)
+    for (int s = t; s > 0 && k.la[s - 1] > k.la[s]; --s) {
+      std::swap(k.la[s - 1], k.la[s]);
+      std::swap(k.ra[s - 1], k.ra[s]);
+    }
   const lqc::Node& ln = g.nodes[L.node];
   const lqc::Node& rn = g.nodes[R.node];
-  int64_t k = 1;
-  for (int a : la) k *= ln.ext[a];
-  const int64_t m = ln.elems / k, n = rn.elems / k;
-  c->key = Key(L.node, R.node, la, ra);
-  c->cost = (Wide)ln.lt * m * n * k;
+  int64_t kext = 1;
+  for (int t = 0; t < np; ++t) kext *= ln.ext[k.la[t]];
+  const int64_t m = ln.elems / kext, n = rn.elems / kext;
+  c->cost = (Wide)ln.lt * m * n * kext;
   c->out_elems = m * n;
-  c->left = &L;
-  c->right = &R;
+  c->x_left = p_left;
   return true;
 }
 
-std::vector<Cand> candidates(const lqc::Dag& g, const Graph& G) {
-  std::vector<Cand> out;
+void candidates(const lqc::Dag& g, const Graph& G, std::vector<Cand>* out) {
+  out->clear();
   for (int x = 0; x < (int)G.verts.size(); ++x)
     for (int y = x + 1; y < (int)G.verts.size(); ++y) {
       Cand c;
       if (candidate(g, G.verts[x], G.verts[y], G.partner, &c)) {
         c.x = x;
         c.y = y;
-        out.push_back(std::move(c));
+        out->push_back(c);
       }
     }
-  std::vector<Cand> ok;
-  for (const Cand& c : out)
-    if (c.out_elems <= G.cap) ok.push_back(c);
-  return ok.empty() ? out : ok;
+  bool any_fits = false;
+  for (const Cand& c : *out) any_fits |= c.out_elems <= G.cap;
+  if (any_fits)
+    out->erase(std::remove_if(out->begin(), out->end(),
+                              [&](const Cand& c) { return c.out_elems > G.cap; }),
+               out->end());
 }
 
 }  // namespace
@@ -137,10 +176,13 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
       Graph& G = graphs[gi];
       const int64_t v0 = vert_off[gi], v1 = vert_off[gi + 1];
       const int64_t e0 = edge_off[gi], e1 = edge_off[gi + 1];
-      if (v0 < 0 || e0 < 0 || v1 <= v0 || e1 < e0 || (e1 > e0 && !edges)) {
+      if (v0 < 0 || e0 < 0 || v1 <= v0 || e1 < e0 || (e1 > e0 && !edges) ||
+          v1 - v0 > ((int64_t)1 << 24)) {
         g.err = "graph " + std::to_string(gi) + ": empty or bad offsets";
         return LQC_ERR_ARG;
       }
+      const int nv = (int)(v1 - v0);
+      G.partner.assign((size_t)nv * LQC_MAX_RANK, -1);
       for (int64_t v = v0; v < v1; ++v) {
         const int64_t u = vert_nodes[v];
         if (u < 0 || u >= N || g.nodes[u].rank == 0) {
@@ -149,21 +191,21 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
         }
         Vertex vx;
         vx.node = u;
-        for (int a = 0; a < g.nodes[u].rank; ++a) vx.labels.push_back({(int32_t)(v - v0), a});
+        vx.nl = g.nodes[u].rank;
+        for (int a = 0; a < vx.nl; ++a) vx.labels[a] = (Label)((v - v0) * LQC_MAX_RANK + a);
         G.cap = std::max(G.cap, g.nodes[u].elems);
-        G.verts.push_back(std::move(vx));
+        G.verts.push_back(vx);
       }
       for (int64_t e = e0; e < e1; ++e) {
         const int32_t* q = edges + 4 * e;
-        const int nv = (int)(v1 - v0);
         if (q[0] < 0 || q[0] >= nv || q[2] < 0 || q[2] >= nv || q[0] == q[2] || q[1] < 0 ||
             q[1] >= g.nodes[vert_nodes[v0 + q[0]]].rank || q[3] < 0 ||
             q[3] >= g.nodes[vert_nodes[v0 + q[2]]].rank) {
           g.err = "graph " + std::to_string(gi) + ": edge out of range";
           return LQC_ERR_ARG;
         }
-        const Label a{q[0], q[1]}, b{q[2], q[3]};
-        if (G.partner.count(a) || G.partner.count(b)) {
+        const Label a = q[0] * LQC_MAX_RANK + q[1], b = q[2] * LQC_MAX_RANK + q[3];
+        if (G.partner[a] >= 0 || G.partner[b] >= 0) {
           g.err = "graph " + std::to_string(gi) + ": an axis is paired twice";
           return LQC_ERR_ARG;
         }
@@ -176,55 +218,112 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
       }
     }
     // Key values are kept incrementally: a step changes the candidates of
-    // only the graphs it contracts in, so only their keys are recounted.
-    // The result equals recounting every graph at every step.
+    // only the graphs it contracts in, and of those only the keys that
+    // appear or disappear are recounted.  The result equals recounting
+    // every graph at every step.
     struct KeyStat {
       int64_t count = 0;
       Wide cost = 0;
       std::set<int64_t> graphs;
     };
-    std::map<Key, KeyStat> stat;
-    std::set<std::pair<Wide, Key>> by_value;  // (-value, key): first = best
-    std::vector<std::vector<Key>> held((size_t)n_graphs);
-    auto enter = [&](int64_t gi) {
+    std::unordered_map<Key, KeyStat, KeyHash> stat;
+    // max-heap on (value, -key) with lazy invalidation: every change of a
+    // key's value pushes its new value; an entry whose value is no longer
+    // the key's is dropped when it reaches the top
+    typedef std::pair<Wide, Key> HE;
+    auto worse = [](const HE& a, const HE& b) {
+      if (a.first != b.first) return a.first < b.first;
+      return b.second < a.second;
+    };
+    std::vector<HE> heap;
+    auto push = [&](const Key& k, const KeyStat& ks) {
+      heap.push_back({ks.count * ks.cost, k});
+      std::push_heap(heap.begin(), heap.end(), worse);
+    };
+    std::vector<std::vector<std::pair<Key, Wide>>> held((size_t)n_graphs);  // sorted keys
+    std::vector<Cand> cs;
+    std::vector<std::pair<Key, Wide>> now;
+    auto add_key = [&](int64_t gi, const Key& k, Wide cost) {
+      KeyStat& ks = stat[k];
+      ks.count += 1;
+      ks.cost = cost;
+      ks.graphs.insert(gi);
+      push(k, ks);
+    };
+    auto drop_key = [&](int64_t gi, const Key& k) {
+      auto it = stat.find(k);
+      KeyStat& ks = it->second;
+      ks.count -= 1;
+      ks.graphs.erase(gi);
+      if (ks.count)
+        push(k, ks);
+      else
+        stat.erase(it);
+    };
+    // the graph's current keys replace held[gi]: only the difference is
+    // applied to the counts
+    auto refresh = [&](int64_t gi, bool cs_current) {
       const Graph& G = graphs[gi];
-      held[gi].clear();
-      if (G.verts.size() < 2) return;
-      std::map<Key, Wide> seen;
-      for (const Cand& c : candidates(g, G)) seen[c.key] = c.cost;
-      for (auto& kv : seen) {
-        KeyStat& ks = stat[kv.first];
-        if (ks.count) by_value.erase({-(ks.count * ks.cost), kv.first});
-        ks.count += 1;
-        ks.cost = kv.second;
-        ks.graphs.insert(gi);
-        by_value.insert({-(ks.count * ks.cost), kv.first});
-        held[gi].push_back(kv.first);
+      now.clear();
+      if (G.verts.size() >= 2) {
+        if (!cs_current) candidates(g, G, &cs);
+        for (const Cand& c : cs) now.push_back({c.key, c.cost});
+        std::sort(now.begin(), now.end(),
+                  [](const std::pair<Key, Wide>& a, const std::pair<Key, Wide>& b) {
+                    return a.first < b.first;
+                  });
+        now.erase(std::unique(now.begin(), now.end(),
+                              [](const std::pair<Key, Wide>& a, const std::pair<Key, Wide>& b) {
+                                return a.first == b.first;
+                              }),
+                  now.end());
       }
-    };
-    auto leave = [&](int64_t gi) {
-      for (const Key& k : held[gi]) {
-        auto it = stat.find(k);
-        KeyStat& ks = it->second;
-        by_value.erase({-(ks.count * ks.cost), k});
-        ks.count -= 1;
-        ks.graphs.erase(gi);
-        if (ks.count)
-          by_value.insert({-(ks.count * ks.cost), k});
-        else
-          stat.erase(it);
+      auto& old = held[gi];
+      size_t i = 0, j = 0;
+      while (i < old.size() || j < now.size()) {
+        if (j == now.size() || (i < old.size() && old[i].first < now[j].first)) {
+          drop_key(gi, old[i++].first);
+        } else if (i == old.size() || now[j].first < old[i].first) {
+          add_key(gi, now[j].first, now[j].second);
+          ++j;
+        } else {
+          ++i;
+          ++j;
+        }
       }
-      held[gi].clear();
+      old.swap(now);
     };
-    for (int64_t gi = 0; gi < n_graphs; ++gi) enter(gi);
-    while (!by_value.empty()) {
-      const Key bk = by_value.begin()->second;
-      const std::vector<int64_t> hold(stat[bk].graphs.begin(), stat[bk].graphs.end());
+    for (int64_t gi = 0; gi < n_graphs; ++gi) refresh(gi, false);
+    std::vector<int64_t> hold;
+    for (;;) {
+      if (heap.size() > 2 * stat.size() + 4096) {  // drop stale entries
+        heap.clear();
+        for (auto& kv : stat) heap.push_back({kv.second.count * kv.second.cost, kv.first});
+        std::make_heap(heap.begin(), heap.end(), worse);
+      }
+      bool found = false;
+      while (!heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), worse);
+        const HE top = heap.back();
+        heap.pop_back();
+        auto it = stat.find(top.second);
+        if (it != stat.end() && it->second.count * it->second.cost == top.first) {
+          heap.push_back(top);  // still current: keep it until the key is used up
+          std::push_heap(heap.begin(), heap.end(), worse);
+          found = true;
+          break;
+        }
+      }
+      if (!found) break;
+      const Key bk = heap.front().second;
+      const std::set<int64_t>& holders = stat[bk].graphs;
+      hold.assign(holders.begin(), holders.end());
       for (int64_t gi : hold) {
         Graph& G = graphs[gi];
-        leave(gi);
+        bool cs_current = false;
         while (G.verts.size() >= 2) {
-          std::vector<Cand> cs = candidates(g, G);
+          candidates(g, G, &cs);
+          cs_current = true;
           const Cand* hit = nullptr;
           for (const Cand& c : cs)
             if (c.key == bk) {
@@ -232,23 +331,28 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
               break;
             }
           if (!hit) break;
-          const std::vector<int>& la = std::get<2>(hit->key);
-          const std::vector<int>& ra = std::get<3>(hit->key);
+          int la[LQC_MAX_RANK], ra[LQC_MAX_RANK];
+          for (int t = 0; t < bk.n; ++t) {
+            la[t] = bk.la[t];
+            ra[t] = bk.ra[t];
+          }
           int64_t node = -1;
-          const int rc = lqc_dag_add_contraction(h, std::get<0>(hit->key), std::get<1>(hit->key),
-                                                 (int)la.size(), la.data(), ra.data(), &node);
+          const int rc = lqc_dag_add_contraction(h, bk.l, bk.r, bk.n, la, ra, &node);
           if (rc != LQC_OK) return rc;
+          const Vertex& Lv = G.verts[hit->x_left ? hit->x : hit->y];
+          const Vertex& Rv = G.verts[hit->x_left ? hit->y : hit->x];
           Vertex nv;
           nv.node = node;
-          for (int i = 0; i < (int)hit->left->labels.size(); ++i)
-            if (std::find(la.begin(), la.end(), i) == la.end()) nv.labels.push_back(hit->left->labels[i]);
-          for (int j = 0; j < (int)hit->right->labels.size(); ++j)
-            if (std::find(ra.begin(), ra.end(), j) == ra.end()) nv.labels.push_back(hit->right->labels[j]);
+          for (int i = 0; i < Lv.nl; ++i)
+            if (std::find(la, la + bk.n, i) == la + bk.n) nv.labels[nv.nl++] = Lv.labels[i];
+          for (int j = 0; j < Rv.nl; ++j)
+            if (std::find(ra, ra + bk.n, j) == ra + bk.n) nv.labels[nv.nl++] = Rv.labels[j];
           const int x = hit->x, y = hit->y;
-          G.verts[x] = std::move(nv);
+          G.verts[x] = nv;
           G.verts.erase(G.verts.begin() + y);
+          cs_current = false;
         }
-        enter(gi);
+        refresh(gi, cs_current);
       }
     }
     for (int64_t gi = 0; gi < n_graphs; ++gi) {

@@ -1,6 +1,7 @@
 """The bench's multi-rank path on the host (gloo, world size 2): the job's
-time is the slowest rank's (a MAX all-reduce), and under torchrun the
-reference arm runs on rank 0 alone, which prints the one JSON line."""
+time is the slowest rank's (a MAX all-reduce), a sharded job's work and
+root extents are sums over the ranks, and under torchrun the reference arm
+runs on rank 0 alone, which prints the one JSON line."""
 import json
 import os
 import socket
@@ -32,6 +33,34 @@ def _rank_main(rank, ws, port, out):
     out[rank] = got
     dist.barrier()
     dist.destroy_process_group()
+
+
+def _sum_rank_main(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    sys.path.insert(0, ROOT)
+    import bench
+    # a sharded DAG: each rank's flops, and each root's slices on this rank
+    total = bench.sum_over_ranks(10.0 * (rank + 1), ws)
+    lts = bench.sum_over_ranks([3 + rank, 2, 5 - rank], ws)
+    out[rank] = (total, tuple(lts))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sum_over_ranks_gloo_world_size_2():
+    """The sharded bench sums the ranks' flops and each root's slices."""
+    ws = 2
+    out = mp.Manager().dict()
+    mp.spawn(_sum_rank_main, args=(ws, _free_port(), out), nprocs=ws, join=True)
+    assert dict(out) == {0: (30.0, (7.0, 4.0, 9.0)), 1: (30.0, (7.0, 4.0, 9.0))}
+
+
+def test_sum_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.sum_over_ranks(2.5, 1) == 2.5
+    assert bench.sum_over_ranks([1, 2], 1) == [1.0, 2.0]
 
 
 def test_max_over_ranks_gloo_world_size_2():

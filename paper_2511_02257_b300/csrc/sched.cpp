@@ -217,10 +217,6 @@ struct TreeSched {
 
   explicit TreeSched(const Dag& d) : g(d) {}
 
-  bool in_tree(int64_t u, int32_t i) const {
-    const auto& c = ctree[u];
-    return std::binary_search(c.begin(), c.end(), i);
-  }
   void touch(int32_t i) {
     if (!dirty_flag[i]) { dirty_flag[i] = 1; dirty.push_back(i); }
   }

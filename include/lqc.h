@@ -235,8 +235,10 @@ int lqc_dag_add_contraction(lqc_dag* dag, int64_t left, int64_t right, int npair
  * done once.  roots[g] receives the final node of graph g.  Host memory:
  * all arrays are read or written during the call only, caller-owned.
  * Errors: LQC_ERR_ARG (bad offsets, vertex, edge or extents; disconnected
- * graph; contractions added up to the failing step stay in the DAG),
- * LQC_ERR_STATE (after lqc_dag_schedule), LQC_ERR_HOST_MEM. */
+ * graph; a contraction beyond LQC_MAX_RANK or the size limits of
+ * lqc_dag_create), LQC_ERR_STATE (after lqc_dag_schedule),
+ * LQC_ERR_HOST_MEM.  On any error the DAG is left as it was before the
+ * call (contractions the call had added are removed again). */
 int lqc_dag_add_graphs(lqc_dag* dag, int64_t n_graphs, const int64_t* vert_off,
                        const int64_t* vert_nodes, const int64_t* edge_off,
                        const int32_t* edges, int64_t* roots);

@@ -154,6 +154,40 @@ void candidates(const lqc::Dag& g, const Graph& G, std::vector<Cand>* out) {
                out->end());
 }
 
+// true when every vertex of the graph is reached from vertex 0 by its edges
+bool connected(int nv, const int32_t* edges, int64_t ne) {
+  std::vector<int> parent(nv);
+  for (int v = 0; v < nv; ++v) parent[v] = v;
+  auto find = [&](int v) {
+    while (parent[v] != v) v = parent[v] = parent[parent[v]];
+    return v;
+  };
+  int parts = nv;
+  for (int64_t e = 0; e < ne; ++e) {
+    const int a = find(edges[4 * e]), b = find(edges[4 * e + 2]);
+    if (a != b) {
+      parent[a] = b;
+      --parts;
+    }
+  }
+  return parts == 1;
+}
+
+// remove the nodes from id n0 on (the contractions one call added), newest
+// first: each is the last consumer of its operands and has a merge entry
+void roll_back(lqc::Dag& g, int64_t n0) {
+  for (int64_t u = (int64_t)g.nodes.size() - 1; u >= n0; --u) {
+    const lqc::Node& n = g.nodes[u];
+    for (int c = 0; c < n.n_children(); ++c) {
+      auto& par = g.nodes[n.child(c)].parents;
+      if (!par.empty() && par.back() == u) par.pop_back();
+    }
+    g.nodes.pop_back();
+  }
+  for (auto it = g.dedup.begin(); it != g.dedup.end();)
+    it = it->second >= n0 ? g.dedup.erase(it) : std::next(it);
+}
+
 }  // namespace
 
 extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* vert_off,
@@ -161,6 +195,7 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
                                   const int32_t* edges, int64_t* roots) {
   if (!h) return LQC_ERR_ARG;
   lqc::Dag& g = h->d;
+  int64_t n0 = -1;  // first node this call adds, once validation passed
   try {
     if (g.frozen) {
       g.err = "DAG is frozen by lqc_dag_schedule";
@@ -216,7 +251,13 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
         G.partner[a] = b;
         G.partner[b] = a;
       }
+      if (!connected(nv, edges + 4 * e0, e1 - e0)) {
+        g.err = "graph " + std::to_string(gi) + " is not connected";
+        return LQC_ERR_ARG;
+      }
     }
+    // from here on contractions are added; a failure removes them again
+    n0 = (int64_t)g.nodes.size();
     // Key values are kept incrementally: a step changes the candidates of
     // only the graphs it contracts in, and of those only the keys that
     // appear or disappear are recounted.  The result equals recounting
@@ -338,7 +379,12 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
           }
           int64_t node = -1;
           const int rc = lqc_dag_add_contraction(h, bk.l, bk.r, bk.n, la, ra, &node);
-          if (rc != LQC_OK) return rc;
+          if (rc != LQC_OK) {
+            const std::string why = g.err;
+            roll_back(g, n0);
+            g.err = "graph " + std::to_string(gi) + ": " + why + " (no contraction added)";
+            return rc;
+          }
           const Vertex& Lv = G.verts[hit->x_left ? hit->x : hit->y];
           const Vertex& Rv = G.verts[hit->x_left ? hit->y : hit->x];
           Vertex nv;
@@ -356,14 +402,16 @@ extern "C" int lqc_dag_add_graphs(lqc_dag* h, int64_t n_graphs, const int64_t* v
       }
     }
     for (int64_t gi = 0; gi < n_graphs; ++gi) {
-      if (graphs[gi].verts.size() != 1) {
-        g.err = "graph " + std::to_string(gi) + " is not connected";
+      if (graphs[gi].verts.size() != 1) {  // not reached for connected graphs
+        roll_back(g, n0);
+        g.err = "graph " + std::to_string(gi) + " was not reduced to one node";
         return LQC_ERR_ARG;
       }
     }
     for (int64_t gi = 0; gi < n_graphs; ++gi) roots[gi] = graphs[gi].verts[0].node;
     return LQC_OK;
   } catch (const std::bad_alloc&) {
+    if (n0 >= 0) roll_back(g, n0);
     g.err = "host allocation failed";
     return LQC_ERR_HOST_MEM;
   }

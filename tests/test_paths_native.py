@@ -243,3 +243,35 @@ def test_orientation_larger_tensor_left_native():
             Pn, Mn = nd.add_leaf((4, 4, n, n)), nd.add_leaf((n, n))
         r = nd.add_graphs([([Mn, Pn], [(0, 1, 1, 2), (1, 3, 0, 0)])])[0]
         assert nd.node_operands(r) == (Pn, Mn, (2, 3), (1, 0))
+
+
+def test_failed_call_leaves_the_dag_unchanged():
+    """A call that fails after it began adding contractions (here: a chain
+    of propagators whose products pass LQC_MAX_RANK = 8 axes) removes them
+    again; a disconnected graph is rejected before anything is added.  The
+    DAG then builds exactly as a fresh one does."""
+    n, lt = 3, 2
+
+    def fresh():
+        d = L.Dag(lt)
+        ids = [d.add_leaf((4, 4, n, n)) for _ in range(4)] + [d.add_leaf((n, n))]
+        return d, ids
+    good = [([0, 4], [(0, 2, 1, 1), (0, 3, 1, 0)]), ([1, 4, 2], [(0, 3, 1, 0), (1, 1, 2, 2)])]
+    # P0 - P1 - P2 - P3 joined by one spin axis each: the product reaches rank 10
+    chain = ([0, 1, 2, 3], [(0, 0, 1, 0), (1, 1, 2, 0), (2, 1, 3, 0)])
+    split = ([0, 1, 4], [(0, 2, 1, 2)])          # vertex 2 has no edge
+    d, ids = fresh()
+    n_before = d.num_nodes()
+    for bad in ([good[0], chain], [good[0], split]):
+        with pytest.raises(L.LqcError) as ei:
+            d.add_graphs(bad)
+        assert ei.value.code == L.LQC_ERR_ARG
+        assert d.num_nodes() == n_before
+        assert all(d.node_info(u)["is_leaf"] for u in range(d.num_nodes()))
+    roots = d.add_graphs(good)
+    ref, _ = fresh()
+    assert roots == ref.add_graphs(good)
+    assert _structure_native(d) == _structure_native(ref)
+    d.schedule("tree", "lru", 0)
+    ref.schedule("tree", "lru", 0)
+    assert d.order() == ref.order() and d.plan() == ref.plan()

@@ -1,0 +1,42 @@
+"""The memory-pressure workload at full size (Lt 128, N 128, 4,826
+contractions, leaves of 32 MiB and 512 MiB in complex128) under its 24 GiB
+device budget, in the launch configuration the bench times for it: TF32x3,
+tree order, grouped windows, CUDA graph, leaves from the library's pinned
+host store.  The oracle cannot evaluate the whole DAG in seconds, so a
+seeded sample of correlators is checked, each on its own descendant
+closure (<= 1e-6), and the executor's counters must equal the plan's.
+"""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import contract as C
+from oracle import dag as D
+
+L = pytest.importorskip("paper_2511_02257_b300")
+
+
+@pytest.mark.gpu
+def test_memory_pressure_full_size_sampled_roots_tf32x3():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = synth.make_workload("memory_pressure")
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        leaves = list(ex.map(lambda li: synth.leaf_data(wl, li), range(len(wl.leaves))))
+    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: leaves[li])
+    nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
+    planned = nd.schedule("tree", "lru", wl.budget_bytes)
+    assert planned["peak_exec"] <= wl.budget_bytes
+    nd.execute(torch.cuda.current_stream().cuda_stream)
+    assert nd.stats() == planned
+    od, _ = D.build_from_workload(wl)
+    rng = np.random.default_rng(11)
+    pick = sorted(rng.choice(od.roots(), size=12, replace=False).tolist())
+    ref = C.evaluate(od, lambda u: leaves[od.nodes[u].leaf_index], pick)
+    errs = {r: float(np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r]))
+            for r in pick}
+    assert max(errs.values()) < 1e-6, errs

@@ -40,3 +40,30 @@ def test_memory_pressure_full_size_sampled_roots_tf32x3():
     errs = {r: float(np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r]))
             for r in pick}
     assert max(errs.values()) < 1e-6, errs
+
+
+@pytest.mark.gpu
+def test_memory_pressure_full_size_fp64_with_evictions():
+    """The same workload on the FP64 path (complex128 storage, model peak
+    12.4 GiB) under an 8 GiB budget, so that the tree order evicts
+    intermediates to pinned host memory and reloads them: 12 seeded roots
+    against the oracle (<= 1e-12), counters equal to the plan's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = synth.make_workload("memory_pressure")
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        leaves = list(ex.map(lambda li: synth.leaf_data(wl, li), range(len(wl.leaves))))
+    nd, _ = L.build_dag(wl, precision="fp64", leaf_data_fn=lambda li: leaves[li])
+    planned = nd.schedule("tree", "lru", 8 << 30)
+    assert planned["n_evict"] > 0 and planned["d2h_bytes"] > 0
+    nd.execute(torch.cuda.current_stream().cuda_stream)
+    nd.wait(600000)
+    assert nd.stats() == planned
+    od, _ = D.build_from_workload(wl)
+    rng = np.random.default_rng(12)
+    pick = sorted(rng.choice(od.roots(), size=12, replace=False).tolist())
+    ref = C.evaluate(od, lambda u: leaves[od.nodes[u].leaf_index], pick)
+    errs = {r: float(np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r]))
+            for r in pick}
+    assert max(errs.values()) < 1e-12, errs

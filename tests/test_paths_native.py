@@ -275,3 +275,49 @@ def test_failed_call_leaves_the_dag_unchanged():
     d.schedule("tree", "lru", 0)
     ref.schedule("tree", "lru", 0)
     assert d.order() == ref.order() and d.plan() == ref.plan()
+
+
+def _random_graphs_mixed(seed, n_leaves=8, n_graphs=30, lt=2):
+    """Like _random_graphs, with axis extents drawn from {2, 3, 4}: edges
+    pair only equal extents, so contraction costs differ and decide the
+    order, not only the ties."""
+    rng = np.random.default_rng(100 + seed)
+    shapes = [tuple(int(e) for e in rng.integers(2, 5, size=int(rng.integers(1, 4))))
+              for _ in range(n_leaves)]
+    graphs = []
+    tries = 0
+    while len(graphs) < n_graphs and tries < 10000:
+        tries += 1
+        nv = int(rng.integers(2, 5))
+        verts = [int(x) for x in rng.integers(0, n_leaves, size=nv)]
+        free = {(v, a) for v in range(nv) for a in range(len(shapes[verts[v]]))}
+        ext = lambda va: shapes[verts[va[0]]][va[1]]  # noqa: E731
+        edges, ok = [], True
+        for v in range(1, nv):
+            pairs = [(b, a) for a in sorted(free) if a[0] == v
+                     for b in sorted(free) if b[0] < v and ext(a) == ext(b)]
+            if not pairs:
+                ok = False
+                break
+            b, a = pairs[int(rng.integers(len(pairs)))]
+            free -= {a, b}
+            edges.append((b[0], b[1], a[0], a[1]))
+        if not ok:
+            continue
+        graphs.append((verts, edges))
+        if rng.random() < 0.4:
+            graphs.append((list(verts), list(edges)))
+    return shapes, graphs, lt
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_paths_bit_exact_random_graphs_mixed_extents(seed):
+    shapes, graphs, lt = _random_graphs_mixed(seed)
+    assert len(graphs) >= 20
+    od, nd = D.Dag(lt), L.Dag(lt)
+    for i, sh in enumerate(shapes):
+        od.add_leaf(sh, leaf_index=i)
+        nd.add_leaf(sh)
+    oroots = PS.select_paths(od, graphs)
+    assert nd.add_graphs(graphs) == oroots
+    assert _structure_native(nd) == _structure_oracle(od)

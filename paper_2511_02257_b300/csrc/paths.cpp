@@ -24,7 +24,6 @@
 //  * a graph is done when one vertex is left: its root.
 #include <algorithm>
 #include <cstring>
-#include <map>
 #include <set>
 #include <string>
 #include <unordered_map>

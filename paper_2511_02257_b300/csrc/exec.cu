@@ -23,6 +23,7 @@
 #include "internal.hpp"
 #include "kernels.hpp"
 #include "kernels_mixed.hpp"
+#include "placer.hpp"
 
 namespace lqc {
 
@@ -63,68 +64,6 @@ struct WinRec {
   std::vector<LevelDev> ldev;                // task tables per level
   int64_t flops = 0;
   bool any_exterior = false;
-};
-
-struct Seg {
-  int64_t size;
-  int32_t dep[3];     // last instruction per stream that touched the bytes
-};
-
-// Best-fit placement with coalescing; grows the high-water mark on demand.
-struct Placer {
-  std::map<int64_t, Seg> free_;  // offset -> free segment
-  int64_t top = 0;
-  static int32_t mx(int32_t a, int32_t b) { return a > b ? a : b; }
-
-  int64_t alloc(int64_t size, int32_t dep[3]) {
-    size = (size + 255) & ~int64_t(255);
-    auto best = free_.end();
-    for (auto it = free_.begin(); it != free_.end(); ++it)
-      if (it->second.size >= size && (best == free_.end() || it->second.size < best->second.size))
-        best = it;
-    if (best == free_.end()) {
-      // extend: merge with a free tail segment if there is one
-      int64_t off = top;
-      dep[0] = dep[1] = dep[2] = -1;
-      if (!free_.empty()) {
-        auto last = std::prev(free_.end());
-        if (last->first + last->second.size == top) {
-          off = last->first;
-          for (int s = 0; s < 3; ++s) dep[s] = last->second.dep[s];
-          free_.erase(last);
-        }
-      }
-      top = off + size;
-      return off;
-    }
-    int64_t off = best->first;
-    Seg sg = best->second;
-    free_.erase(best);
-    for (int s = 0; s < 3; ++s) dep[s] = sg.dep[s];
-    if (sg.size > size) free_[off + size] = Seg{sg.size - size, {sg.dep[0], sg.dep[1], sg.dep[2]}};
-    return off;
-  }
-
-  void release(int64_t off, int64_t size, const int32_t dep[3]) {
-    size = (size + 255) & ~int64_t(255);
-    Seg s{size, {dep[0], dep[1], dep[2]}};
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && off + size == nx->first) {
-      s.size += nx->second.size;
-      for (int k = 0; k < 3; ++k) s.dep[k] = mx(s.dep[k], nx->second.dep[k]);
-      free_.erase(nx);
-    }
-    auto it = free_.lower_bound(off);
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second.size == off) {
-        pv->second.size += s.size;
-        for (int k = 0; k < 3; ++k) pv->second.dep[k] = mx(pv->second.dep[k], s.dep[k]);
-        return;
-      }
-    }
-    free_[off] = s;
-  }
 };
 
 }  // namespace

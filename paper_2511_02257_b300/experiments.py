@@ -45,6 +45,11 @@ tuned TF32x3 time-to-solution and the largest difference of a term's value.
 
 times each scheduler's order on the host for synthetic DAGs of the vertex
 counts of the paper's Table 2, with their trees, vertices, edges, F_v, F_e.
+
+  python -m paper_2511_02257_b300.experiments optimal [--dags 200] [--max-contr 9]
+
+scores every scheduler's model peak against the optimal peak over all
+contraction orders of small synthetic DAGs (exhaustive enumeration).
 """
 from __future__ import annotations
 
@@ -462,6 +467,83 @@ def sched_bench(argv):
         nd.close()
 
 
+def contraction_orders(nd):
+    """Every topological order of a Dag's contractions (operands first), by
+    depth-first enumeration over the contractions whose operands are done."""
+    n = nd.num_nodes()
+    deps = {}
+    for u in range(n):
+        left, right, _, _ = nd.node_operands(u)
+        if left >= 0:
+            deps[u] = [c for c in {left, right} if nd.node_operands(c)[0] >= 0]
+    todo = sorted(deps)
+    done, cur = set(), []
+
+    def rec():
+        if len(cur) == len(todo):
+            yield list(cur)
+            return
+        for u in todo:
+            if u not in done and all(c in done for c in deps[u]):
+                done.add(u)
+                cur.append(u)
+                yield from rec()
+                cur.pop()
+                done.discard(u)
+    yield from rec()
+
+
+def optimal_peak(nd):
+    """(smallest model peak over every contraction order, number of orders):
+    each order's peak from the native plan replay (no budget)."""
+    best, count = None, 0
+    for order in contraction_orders(nd):
+        p = nd.set_order(order, "lru", 0)["peak_paper"]
+        best = p if best is None else min(best, p)
+        count += 1
+    return best, count
+
+
+def optimal_bench(argv):
+    """Each scheduler's model peak against the optimal peak over all
+    contraction orders, on small synthetic DAGs (at most --max-contr
+    contractions) built by the meson and baryon generators."""
+    import paper_2511_02257_b300 as L
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dags", type=int, default=200)
+    ap.add_argument("--max-contr", type=int, default=9)
+    ap.add_argument("--policies", default="naive,rsgs,sibling,tree,node")
+    args = ap.parse_args(argv)
+    pols = args.policies.split(",")
+    ratios = {p: [] for p in pols}
+    n_dags = n_orders = seed = 0
+    while n_dags < args.dags and seed < 100 * args.dags:
+        name = "baryon" if seed % 3 == 2 else "multi_meson"
+        kw = dict(n_functions=1 + seed % 3, nvec=4, lt=2, prefix_pool=2)
+        if name == "baryon":
+            kw = dict(n_functions=1 + seed % 2, nvec=3, lt=2)
+        seed += 1
+        wl = synth.make_workload(name, seed=seed, **kw)
+        nd, _ = L.build_dag(wl, with_data=False)
+        nc = nd.num_nodes() - len(wl.leaves)
+        if nc < 3 or nc > args.max_contr:
+            nd.close()
+            continue
+        opt, count = optimal_peak(nd)
+        n_dags += 1
+        n_orders += count
+        for p in pols:
+            ratios[p].append(nd.schedule(p, "lru", 0)["peak_paper"] / opt)
+        nd.close()
+    out = {"dags": n_dags, "orders_enumerated": n_orders}
+    for p in pols:
+        r = np.asarray(ratios[p])
+        out[p] = {"optimal_fraction": float(np.mean(r <= 1.0)), "mean_ratio": float(r.mean()),
+                  "max_ratio": float(r.max())}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         return kernel_bench(sys.argv[2:])
@@ -471,6 +553,8 @@ def main():
         return paths_bench(sys.argv[2:])
     if len(sys.argv) > 1 and sys.argv[1] == "sched":
         return sched_bench(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "optimal":
+        return optimal_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

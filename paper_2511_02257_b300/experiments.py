@@ -50,6 +50,12 @@ counts of the paper's Table 2, with their trees, vertices, edges, F_v, F_e.
 
 scores every scheduler's model peak against the optimal peak over all
 contraction orders of small synthetic DAGs (exhaustive enumeration).
+
+  python -m paper_2511_02257_b300.experiments model [--workloads ...] [--fractions 1,0.5,0.25]
+
+gives the memory model's peak, evictions and transfer bytes of every
+scheduler's plan at budgets relative to the tree order's peak, without
+executing.
 """
 from __future__ import annotations
 
@@ -544,6 +550,40 @@ def optimal_bench(argv):
     print(json.dumps(out), flush=True)
 
 
+def model_bench(argv):
+    """The memory model's figures (Sec. II-C) for every scheduler without
+    executing: model peak, evictions and host<->device bytes of the plan at
+    budgets given as fractions of the tree order's peak (1 = no eviction for
+    the tree order).  Storage at the size of --precision."""
+    import paper_2511_02257_b300 as L
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workloads", default="multi_meson,baryon,memory_pressure,batched")
+    ap.add_argument("--precision", default="tf32x3")
+    ap.add_argument("--fractions", default="1,0.5,0.25")
+    ap.add_argument("--policies", default="naive,rsgs,sibling,tree,node")
+    ap.add_argument("--evict", default="lru")
+    args = ap.parse_args(argv)
+    for spec in args.workloads.split(","):
+        name, _, nf = spec.partition(":")
+        wl = synth.make_workload(name, **({"n_functions": int(nf)} if nf else {}))
+        nd, _ = L.build_dag(wl, precision=args.precision, with_data=False)
+        tree_peak = nd.schedule("tree", args.evict, 0)["peak_exec"]
+        for frac in (float(f) for f in args.fractions.split(",")):
+            budget = int(tree_peak * frac)
+            row = {"workload": spec, "precision": args.precision, "budget_fraction": frac,
+                   "budget_bytes": budget}
+            for pol in args.policies.split(","):
+                try:
+                    st = nd.schedule(pol, args.evict, budget)
+                    row[pol] = {"peak_paper": st["peak_paper"], "n_evict": st["n_evict"],
+                                "h2d_bytes": st["h2d_bytes"], "d2h_bytes": st["d2h_bytes"]}
+                except L.LqcError as e:
+                    row[pol] = {"error": str(e)}
+            print(json.dumps(row), flush=True)
+        nd.close()
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         return kernel_bench(sys.argv[2:])
@@ -555,6 +595,8 @@ def main():
         return sched_bench(sys.argv[2:])
     if len(sys.argv) > 1 and sys.argv[1] == "optimal":
         return optimal_bench(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "model":
+        return model_bench(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="memory_pressure")
     ap.add_argument("--precision", default="tf32x3")

@@ -214,6 +214,18 @@ int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
 int lqc_dag_add_contraction(lqc_dag* dag, int64_t left, int64_t right, int npairs,
                             const int* la, const int* ra, int64_t* node_id);
 
+/* n contractions at once, each as lqc_dag_add_contraction: request i has
+ * operands left[i], right[i] -- an existing id, or -(j+1) for the node that
+ * request j < i of this call received -- and npairs[i] axis pairs taken in
+ * order from la/ra (the pairs of request i start where those of request
+ * i-1 end).  node_ids[i] receives its id (a merged request gives the
+ * earlier id).  All arrays are
+ * caller-owned and read or written during the call only.  Errors: those of
+ * lqc_dag_add_contraction for the first failing request; the DAG is then
+ * left as it was before the call. */
+int lqc_dag_add_contractions(lqc_dag* dag, int64_t n, const int64_t* left, const int64_t* right,
+                             const int* npairs, const int* la, const int* ra, int64_t* node_ids);
+
 /* Contraction-path selection (Sec. II-A): reduce each of n_graphs tensor
  * graphs to one node by binary contractions added to the DAG.  The vertices
  * of graph g are the existing nodes vert_nodes[vert_off[g] .. vert_off[g+1])

@@ -217,6 +217,43 @@ int lqc_dag_add_contraction(lqc_dag* h, int64_t left, int64_t right, int npairs,
   LQC_GUARD_END(h)
 }
 
+int lqc_dag_add_contractions(lqc_dag* h, int64_t n, const int64_t* left, const int64_t* right,
+                             const int* npairs, const int* la, const int* ra, int64_t* node_ids) {
+  if (!h) return LQC_ERR_ARG;
+  Dag& g = h->d;
+  if (n < 0 || (n > 0 && (!left || !right || !npairs || !la || !ra || !node_ids)))
+    return fail(h, LQC_ERR_ARG, "null or negative request arrays");
+  const int64_t n0 = (int64_t)g.nodes.size();
+  int64_t at = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int np = npairs[i];
+    // -(j+1): the node request j of this call received
+    auto resolve = [&](int64_t x) { return x >= 0 ? x : (-x - 1 < i ? node_ids[-x - 1] : -1); };
+    const int64_t l = resolve(left[i]), r = resolve(right[i]);
+    const int rc = np < 1 || np > LQC_MAX_RANK
+                       ? fail(h, LQC_ERR_ARG, "npairs must be in [1, LQC_MAX_RANK]")
+                       : lqc_dag_add_contraction(h, l, r, np, la + at, ra + at, &node_ids[i]);
+    if (rc != LQC_OK) {
+      // remove what this call added, newest first (each is the last
+      // consumer of its operands and owns one merge entry)
+      for (int64_t u = (int64_t)g.nodes.size() - 1; u >= n0; --u) {
+        const Node& nu = g.nodes[u];
+        for (int c = 0; c < nu.n_children(); ++c) {
+          auto& par = g.nodes[nu.child(c)].parents;
+          if (!par.empty() && par.back() == u) par.pop_back();
+        }
+        g.nodes.pop_back();
+      }
+      for (auto it = g.dedup.begin(); it != g.dedup.end();)
+        it = it->second >= n0 ? g.dedup.erase(it) : std::next(it);
+      g.err = "request " + std::to_string(i) + ": " + g.err;
+      return rc;
+    }
+    at += np;
+  }
+  return LQC_OK;
+}
+
 int lqc_dag_schedule(lqc_dag* h, lqc_policy policy, lqc_evict evict, uint64_t budget_bytes,
                      lqc_stats* planned) {
   if (!h) return LQC_ERR_ARG;

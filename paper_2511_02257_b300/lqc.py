@@ -85,6 +85,8 @@ _sig("lqc_dag_add_leaf_tensor", ctypes.c_int, [c_vp, ctypes.c_int, P_i64, P_dbl,
 _sig("lqc_dag_set_leaf_data", ctypes.c_int, [c_vp, c_i64, P_dbl])
 _sig("lqc_dag_add_contraction", ctypes.c_int, [c_vp, c_i64, c_i64, ctypes.c_int, P_int, P_int, P_i64])
 _sig("lqc_dag_add_graphs", ctypes.c_int, [c_vp, c_i64, P_i64, P_i64, P_i64, P_i32, P_i64])
+_sig("lqc_dag_add_contractions", ctypes.c_int, [c_vp, c_i64, P_i64, P_i64, P_int, P_int, P_int,
+                                                P_i64])
 _sig("lqc_dag_schedule", ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.POINTER(lqc_stats)])
 _sig("lqc_dag_set_order", ctypes.c_int, [c_vp, P_i64, c_i64, ctypes.c_int, ctypes.c_uint64,
@@ -128,7 +130,8 @@ _sig("lqc_contract_all_c64_scratch_bytes", c_i64, [ctypes.c_int, P_i64, ctypes.c
 
 # re-export the raw entry points under their C names
 for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_add_leaf_tensor", "lqc_dag_set_leaf_data",
-           "lqc_dag_add_contraction", "lqc_dag_add_graphs", "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
+           "lqc_dag_add_contraction", "lqc_dag_add_contractions", "lqc_dag_add_graphs",
+           "lqc_dag_schedule", "lqc_dag_set_order", "lqc_dag_get_order",
            "lqc_dag_get_plan", "lqc_dag_set_option", "lqc_dag_stage_leaves",
            "lqc_dag_unstage_leaves", "lqc_dag_execute", "lqc_dag_wait", "lqc_dag_autotune",
            "lqc_dag_read_correlator",
@@ -232,6 +235,26 @@ class Dag:
         self._check(_lib.lqc_dag_add_contraction(self.h, int(left), int(right), len(la), pa, pb,
                                                  ctypes.byref(nid)), "add_contraction")
         return nid.value
+
+    def add_contractions(self, requests) -> List[int]:
+        """Many contractions in one call: requests = [(left, right, la, ra)];
+        an operand is an existing id, or -(k + 1) for the node request k < i
+        of this call receives.  Returns the node ids; on error nothing is
+        added."""
+        n = len(requests)
+        if n == 0:
+            return []
+        ids = np.zeros(n, dtype=np.int64)
+        left = np.fromiter((q[0] for q in requests), dtype=np.int64, count=n)
+        right = np.fromiter((q[1] for q in requests), dtype=np.int64, count=n)
+        npairs = np.fromiter((len(q[2]) for q in requests), dtype=np.intc, count=n)
+        la_a, pla = _intarr([a for q in requests for a in q[2]] or [0])
+        ra_a, pra = _intarr([b for q in requests for b in q[3]] or [0])
+        self._check(_lib.lqc_dag_add_contractions(self.h, n, left.ctypes.data_as(P_i64),
+                                                  right.ctypes.data_as(P_i64),
+                                                  npairs.ctypes.data_as(P_int), pla, pra,
+                                                  ids.ctypes.data_as(P_i64)), "add_contractions")
+        return ids.tolist()
 
     def add_graphs(self, graphs) -> List[int]:
         """Contraction-path selection (Sec. II-A): reduce every graph
@@ -417,6 +440,12 @@ def build_dag(wl, precision: str = "fp64", with_data: bool = True, leaf_data_fn=
     if paths:
         return d, ids + d.add_graphs([([ids[v] for v in items], edges)
                                       for items, edges in wl.graphs])
-    for rq in wl.requests:
-        ids.append(d.add_contraction(ids[rq.left], ids[rq.right], rq.la, rq.ra))
+    # the request stream in one call: stream index k >= n_leaves refers to
+    # request k - n_leaves of this same call
+    nl = len(ids)
+
+    def ref(k):
+        return ids[k] if k < nl else -(k - nl + 1)
+    ids.extend(d.add_contractions([(ref(rq.left), ref(rq.right), rq.la, rq.ra)
+                                   for rq in wl.requests]))
     return d, ids

@@ -208,3 +208,42 @@ def test_orders_bit_exact_large_dag(sched):
     nd, _ = L.build_dag(wl, with_data=False)
     nd.schedule(sched, "lru", 0)
     assert nd.order() == S.SCHEDULERS[sched](od)
+
+
+@pytest.mark.parametrize("name", ["tiny", "multi_meson", "baryon", "batched"])
+def test_bulk_contractions_equal_single_calls(name):
+    """lqc_dag_add_contractions (one call for the request stream, operands
+    of earlier requests given as back-references) builds the DAG that one
+    lqc_dag_add_contraction per request builds: same ids, operands, sizes."""
+    kw = {} if name == "tiny" else dict(n_functions=20) if name != "batched" else \
+        dict(n_dags=3, nvecs=(8, 12), lts=(2, 3), n_functions=6)
+    wl = synth.make_workload(name, **kw)
+    bulk, ids_b = L.build_dag(wl, with_data=False)
+    one = L.Dag(wl.lt)
+    ids = [one.add_leaf(lf.extents, lt=wl.leaf_lt(i)) for i, lf in enumerate(wl.leaves)]
+    for rq in wl.requests:
+        ids.append(one.add_contraction(ids[rq.left], ids[rq.right], rq.la, rq.ra))
+    assert ids_b == ids and bulk.num_nodes() == one.num_nodes()
+    for u in range(one.num_nodes()):
+        assert bulk.node_operands(u) == one.node_operands(u)
+        assert bulk.node_info(u) == one.node_info(u)
+
+
+def test_bulk_contractions_errors_leave_dag_unchanged():
+    """A failing request anywhere in a bulk call (here the second, whose
+    paired extents differ) or a reference to a later request leaves the DAG
+    as it was; identical requests within one call merge."""
+    d = L.Dag(2)
+    a = d.add_leaf((3, 4))
+    b = d.add_leaf((4, 5))
+    n0 = d.num_nodes()
+    with pytest.raises(L.LqcError) as ei:
+        # request 0: A.B -> (3, 5); request 1 pairs its axis 0 (3) with A's axis 1 (4)
+        d.add_contractions([(a, b, [1], [0]), (-1, a, [0], [1])])
+    assert ei.value.code == L.LQC_ERR_ARG and d.num_nodes() == n0
+    with pytest.raises(L.LqcError) as ei:
+        d.add_contractions([(-2, b, [1], [0]), (a, b, [1], [0])])
+    assert ei.value.code == L.LQC_ERR_ARG and d.num_nodes() == n0
+    ids = d.add_contractions([(a, b, [1], [0]), (a, b, [1], [0]), (-2, -1, [0], [0])])
+    assert ids[0] == ids[1] == n0 and ids[2] == n0 + 1
+    assert d.node_operands(ids[2]) == (n0, n0, (0,), (0,))

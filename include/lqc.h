@@ -106,6 +106,19 @@ typedef struct {
   int64_t peak_paper, peak_exec, n_evict, n_h2d, n_d2h, h2d_bytes, d2h_bytes;
 } lqc_stats;
 
+/* Kinds of the grouped launches of a window level (mixed precisions), in
+ * the order a level issues them; lqc_exec_info times each kind apart. */
+typedef enum {
+  LQC_KIND_REORDER = 0,         /* operand reorders of fused GEMMs, correlator partners */
+  LQC_KIND_PACK = 1,            /* hi/lo planes of the plane form                  */
+  LQC_KIND_GEMM_PLANES = 2,     /* split-3 tensor-core GEMM over planes            */
+  LQC_KIND_GEMM_FUSED = 3,      /* split-3 tensor-core GEMM splitting raw complex64 */
+  LQC_KIND_REDUCE = 4,          /* FP64 sum of k-split partials                    */
+  LQC_KIND_CORRELATOR = 5,      /* correlator partial sums                         */
+  LQC_KIND_CORRELATOR_SUM = 6,  /* correlator final sums                           */
+  LQC_NUM_KINDS = 8
+} lqc_launch_kind;
+
 /* Execution report of the last lqc_dag_execute (filled by lqc_dag_get_exec_info). */
 typedef struct {
   int64_t n_kernels;      /* kernels launched by the last execute            */
@@ -121,6 +134,18 @@ typedef struct {
   double ms_contract, ms_contract_all;    /* summed kernel time (ms)          */
   int64_t flops_contract, flops_contract_all;
   int64_t host_arena_bytes; /* pinned host bytes holding written-back tensors */
+  /* with LQC_OPT_TIMING and grouped windows: per lqc_launch_kind, launches
+   * and CUDA-event time (events recorded between the launches of a level on
+   * the compute stream), summed like the fields above; flops_gemm = the
+   * algorithmic flops of the levels whose GEMM launches were timed          */
+  int64_t n_kind[LQC_NUM_KINDS];
+  double ms_kind[LQC_NUM_KINDS];
+  int64_t flops_gemm;
+  /* largest sum of device bytes the executor holds at once (arena tensors,
+   * staged leaves a contraction reads, a root's output), frees of grouped
+   * windows taking effect at the window's end; the op-level figure with
+   * frees at their op is lqc_stats.peak_exec of lqc_dag_get_stats          */
+  int64_t resident_peak_bytes;
 } lqc_exec_info;
 
 /* Option keys for lqc_dag_set_option. */
@@ -301,6 +326,16 @@ int lqc_dag_unstage_leaves(lqc_dag* dag);
  * arena (sized by the plan) and the results buffer; later calls reuse them.
  * Errors: LQC_ERR_STATE (not scheduled, leaf without data), LQC_ERR_CUDA. */
 int lqc_dag_execute(lqc_dag* dag, void* stream);
+
+/* Do everything the next lqc_dag_execute on `stream` would do before its
+ * first launch, and nothing else: allocate the device arena, results buffer,
+ * scratch and pinned write-back arena, build the instruction program (task
+ * tables of grouped windows included) and, with LQC_OPT_CUDA_GRAPH, capture
+ * the graph.  Nothing runs on the device, so the first execute after it
+ * times only the work (an allocation-free first execute for a caller that
+ * wants it off a latency-critical path).  No counterpart in the paper.
+ * Errors: as lqc_dag_execute. */
+int lqc_dag_prepare(lqc_dag* dag, void* stream);
 
 /* Autotuner of the mixed precisions (no counterpart in the paper: the
  * batching form's tile and grouping choices).  After lqc_dag_schedule, with

@@ -38,7 +38,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in sources():
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
         cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -47,8 +47,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
         else:
             cmd += ["-x", "c++"]
-        subprocess.run(cmd, check=True)
+        cmds.append(cmd)
         objs.append(obj)
+    # one compiler process per source file, all at once
+    procs = [subprocess.Popen(c) for c in cmds]
+    failed = [c for c, p in zip(cmds, procs) if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
     tmp = LIB + ".tmp"
     subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], check=True)
     os.replace(tmp, LIB)

@@ -448,6 +448,14 @@ int lqc_dag_execute(lqc_dag* h, void* stream) {
   LQC_GUARD_END(h)
 }
 
+int lqc_dag_prepare(lqc_dag* h, void* stream) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  if (!h->d.scheduled) return fail(h, LQC_ERR_STATE, "prepare before schedule");
+  return lqc::exec_prepare(h->d, stream);
+  LQC_GUARD_END(h)
+}
+
 int lqc_dag_autotune(lqc_dag* h, void* stream, int reps, lqc_tune_entry* entries, int64_t cap,
                      int64_t* n) {
   if (!h || !n) return LQC_ERR_ARG;

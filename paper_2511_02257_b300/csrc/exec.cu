@@ -62,6 +62,7 @@ struct WinRec {
   std::vector<std::vector<int32_t>> levels;  // members per level
   std::vector<int32_t> waits;                // cross-stream waits of the members
   std::vector<LevelDev> ldev;                // task tables per level
+  std::vector<int32_t> lev_slot;             // LQC_OPT_TIMING: first mark slot per level
   int64_t flops = 0;
   bool any_exterior = false;
 };
@@ -110,6 +111,14 @@ struct ExecState {
   std::vector<int64_t> tev_flops;
   std::vector<int64_t> tev_node;          // node of each timed instruction
   std::vector<double> tev_ms;             // summed duration per timed instruction
+  // LQC_OPT_TIMING with windows: marks between the launches of every level
+  // (two sets like tev); per slot the kind of the launch it opens (-1 after
+  // a level's last launch) and, for GEMM launches, the level's flops
+  std::vector<cudaEvent_t> kev[2];
+  std::vector<int8_t> kev_kind;
+  std::vector<int64_t> kev_flops;
+  // figures of the executor's own walk of the op list
+  int64_t walk_evict = 0, walk_peak = 0, resident_peak = 0;
   bool timing_pending[2] = {false, false};
   int tset = 0;
 };
@@ -147,12 +156,16 @@ void free_program(ExecState& x) {
   for (int k = 0; k < 2; ++k) {
     for (cudaEvent_t e : x.tev[k]) cudaEventDestroy(e);
     x.tev[k].clear();
+    for (cudaEvent_t e : x.kev[k]) cudaEventDestroy(e);
+    x.kev[k].clear();
     x.timing_pending[k] = false;
   }
   x.tev_kind.clear();
   x.tev_node.clear();
   x.tev_ms.clear();
   x.tev_flops.clear();
+  x.kev_kind.clear();
+  x.kev_flops.clear();
   for (cudaEvent_t e : x.ev) cudaEventDestroy(e);
   x.ev.clear();
   if (x.arena) { cudaFree(x.arena); x.arena = nullptr; }
@@ -231,6 +244,19 @@ int build_program(Dag& g) {
   std::vector<int64_t> lvl_need;       // scratch bytes per level of the open window
   std::vector<int32_t> owner;          // member instruction -> its window instruction
   const int64_t kLevelScratchCap = (int64_t)2 << 30;
+  // the executor's own account of the device bytes it holds: `held` with
+  // frees as they really happen (window frees at the window's end), `res`
+  // with every EVICT / FREE at its op (the plan's model); a staged leaf
+  // counts from the LOAD the executor skips to its release
+  std::vector<uint8_t> holds(N, 0);
+  int64_t held = 0, res = 0;
+  x.walk_evict = x.walk_peak = x.resident_peak = 0;
+  auto take_bytes = [&](int64_t u) {
+    if (!holds[u]) { holds[u] = 1; held += g.size_bytes(u); }
+  };
+  auto drop_bytes = [&](int64_t u) {
+    if (holds[u]) { holds[u] = 0; held -= g.size_bytes(u); }
+  };
   auto add_wait = [&](Instr& in, int32_t on) {
     if (on < 0 || P[on].stream == in.stream) return;
     for (int k = 0; k < in.nwait; ++k)
@@ -238,6 +264,7 @@ int build_program(Dag& g) {
     in.wait[in.nwait++] = on;
   };
   auto release = [&](int64_t u) {
+    drop_bytes(u);
     if (off[u] < 0) return;
     int32_t dep[3] = {last_compute[u], last_h2d[u], last_d2h[u]};
     if (g.opt_poison) {
@@ -310,6 +337,8 @@ int build_program(Dag& g) {
     const int64_t u = op.node;
     const Node& n = g.nodes[u];
     if (op.kind == OP_LOAD) {
+      take_bytes(u);
+      res += g.size_bytes(u);
       if (staged && n.is_leaf()) continue;  // leaves already on the device
       Instr in{};
       in.kind = I_LOAD;
@@ -340,6 +369,8 @@ int build_program(Dag& g) {
       writer[u] = -1;
       waited_for_load[u] = 0;
     } else if (op.kind == OP_EVICT) {
+      ++x.walk_evict;
+      res -= g.size_bytes(u);
       if (op.flag) {
         Instr in{};
         in.kind = I_WRITEBACK;
@@ -362,8 +393,10 @@ int build_program(Dag& g) {
       }
       release(u);
     } else if (op.kind == OP_FREE && W > 0 && !win.empty()) {
+      res -= g.size_bytes(u);
       win_free.push_back(u);  // no evictions in windowed plans: no host copy to drop
     } else if (op.kind == OP_FREE) {
+      res -= g.size_bytes(u);
       if (hoff[u] >= 0) {  // final release: the host copy is dead too
         int32_t hdep[3] = {-1, last_h2d[u], wb_instr[u]};
         hpl.release(hoff[u], g.size_bytes(u), hdep);
@@ -460,6 +493,11 @@ int build_program(Dag& g) {
       x.adesc.push_back(ad);
       x.mdesc.push_back(md);
       const int32_t me = (int32_t)P.size() - 1;
+      // the output's bytes (a root's: its Lt values, held only while it runs)
+      x.walk_peak = std::max(x.walk_peak, res + g.size_bytes(u));
+      x.resident_peak = std::max(x.resident_peak, held + g.size_bytes(u));
+      res += g.size_bytes(u);        // a root's FREE op follows at once
+      if (n.rank != 0) take_bytes(u);  // a root's values go to the results buffer
       if (W > 0) {
         win.push_back(me);
         (void)member_need;
@@ -600,6 +638,33 @@ int build_program(Dag& g) {
     CK(cudaMemcpy(x.taskbuf, tbuf.data(), tbuf.size(), cudaMemcpyHostToDevice), "task tables");
     for (WinRec& r : x.wins)
       for (LevelDev& d : r.ldev) rebase_level(&d, x.taskbuf);
+    if (g.opt_timing) {
+      for (WinRec& r : x.wins) {
+        r.lev_slot.resize(r.levels.size());
+        for (size_t l = 0; l < r.levels.size(); ++l) {
+          int kinds[LQC_NUM_KINDS];
+          const int nk = level_launch_kinds(r.ldev[l], kinds);
+          int64_t fl = 0;
+          for (int32_t m : r.levels[l])
+            if (P[m].kind == I_CONTRACT) {
+              const ContractDesc& cd = x.cdesc[m];
+              fl += 8 * cd.lt * cd.M * cd.N * cd.K;
+            }
+          r.lev_slot[l] = (int32_t)x.kev_kind.size();
+          for (int k = 0; k < nk; ++k) {
+            x.kev_kind.push_back((int8_t)kinds[k]);
+            x.kev_flops.push_back(
+                kinds[k] == LQC_KIND_GEMM_PLANES || kinds[k] == LQC_KIND_GEMM_FUSED ? fl : 0);
+          }
+          x.kev_kind.push_back(-1);
+          x.kev_flops.push_back(0);
+        }
+      }
+      for (int k = 0; k < 2; ++k) {
+        x.kev[k].resize(x.kev_kind.size(), nullptr);
+        for (cudaEvent_t& e : x.kev[k]) CK(cudaEventCreate(&e), "timing event");
+      }
+    }
   }
   x.host_arena_bytes = hpl.top;
   if (hpl.top > 0)
@@ -610,6 +675,11 @@ int build_program(Dag& g) {
   g.info.n_contract = g.info.n_contract_all = 0;
   g.info.ms_contract = g.info.ms_contract_all = 0.0;
   g.info.flops_contract = g.info.flops_contract_all = 0;
+  for (int k = 0; k < LQC_NUM_KINDS; ++k) {
+    g.info.n_kind[k] = 0;
+    g.info.ms_kind[k] = 0.0;
+  }
+  g.info.flops_gemm = 0;
   return LQC_OK;
 }
 
@@ -638,8 +708,10 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
       for (int32_t w : r.waits) CK(cudaStreamWaitEvent(s, x.ev[w], 0), "wait");
       const bool timed = g.opt_timing && tk < x.tev_kind.size();
       if (timed) CK(cudaEventRecordWithFlags(x.tev[x.tset][2 * tk], s, tflag), "timing record");
-      for (const LevelDev& d : r.ldev) {
-        const int nk = launch_level(d, s);
+      for (size_t l = 0; l < r.ldev.size(); ++l) {
+        cudaEvent_t* marks = timed && !r.lev_slot.empty() ? &x.kev[x.tset][r.lev_slot[l]]
+                                                          : nullptr;
+        const int nk = launch_level(r.ldev[l], s, marks, tflag);
         if (nk < 0) return cuda_fail(g, cudaGetLastError(), "window level launch");
         x.n_kernels += nk;
       }
@@ -730,9 +802,11 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
     CK(cudaEventRecord(x.start_ev, st[k]), "record join");
     CK(cudaStreamWaitEvent(cs, x.start_ev, 0), "wait join");
   }
-  // counted figures of the walk (evictions and peaks come from the plan)
-  c.n_evict = g.planned.n_evict;
-  c.peak_exec = g.planned.peak_exec;
+  // counted figures: copies from this walk; evictions and the op-level peak
+  // from the program build's walk of the op list; peak_paper is the plan's
+  // model figure of the order (the executor runs the order as planned)
+  c.n_evict = x.walk_evict;
+  c.peak_exec = x.walk_peak;
   c.peak_paper = g.planned.peak_paper;
   // with staged leaves the leaf loads are served on the device: c counts
   // only what really crossed the host link
@@ -870,12 +944,56 @@ int collect_set(Dag& g, int set) {
       g.info.flops_contract_all += x.tev_flops[k];
     }
   }
+  const std::vector<cudaEvent_t>& kv = x.kev[set];
+  for (size_t k = 0; k + 1 < kv.size(); ++k) {
+    const int kind = x.kev_kind[k];
+    if (kind < 0) continue;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, kv[k], kv[k + 1]), "timing elapsed");
+    g.info.n_kind[kind]++;
+    g.info.ms_kind[kind] += ms;
+    g.info.flops_gemm += x.kev_flops[k];
+  }
   x.timing_pending[set] = false;
   return LQC_OK;
 }
 }  // namespace
 
-int exec_run(Dag& g, void* stream) {
+namespace {
+// capture the whole issue into a graph for stream `cs` (once per stream)
+int ensure_graph(Dag& g, cudaStream_t cs) {
+  ExecState& x = *g.ex;
+  if (x.graph && x.graph_stream == cs) return LQC_OK;
+  if (x.graph) { cudaGraphExecDestroy(x.graph); x.graph = nullptr; }
+  cudaStream_t cap = cs;
+  bool own = false;
+  if (cap == nullptr) {  // the legacy stream cannot be captured
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+    own = true;
+  }
+  CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = issue(g, cap, true);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  if (rc != LQC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    if (own) cudaStreamDestroy(cap);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    if (own) cudaStreamDestroy(cap);
+    return cuda_fail(g, e, "end capture");
+  }
+  e = cudaGraphInstantiate(&x.graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (own) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+  x.graph_stream = cs;
+  return LQC_OK;
+}
+}  // namespace
+
+int exec_prepare(Dag& g, void* stream) {
   int rc = ensure_state(g);
   if (rc != LQC_OK) return rc;
   ExecState& x = *g.ex;
@@ -892,6 +1010,14 @@ int exec_run(Dag& g, void* stream) {
       return rc;
     }
   }
+  if (g.opt_graph) return ensure_graph(g, static_cast<cudaStream_t>(stream));
+  return LQC_OK;
+}
+
+int exec_run(Dag& g, void* stream) {
+  int rc = exec_prepare(g, stream);
+  if (rc != LQC_OK) return rc;
+  ExecState& x = *g.ex;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if (g.opt_graph) x.tset = 0;  // a captured graph always records timing set 0
   if (g.opt_timing && x.timing_pending[x.tset]) {
@@ -901,33 +1027,6 @@ int exec_run(Dag& g, void* stream) {
     if (rc != LQC_OK) return rc;
   }
   if (g.opt_graph) {
-    if (!x.graph || x.graph_stream != cs) {
-      if (x.graph) { cudaGraphExecDestroy(x.graph); x.graph = nullptr; }
-      cudaStream_t cap = cs;
-      bool own = false;
-      if (cap == nullptr) {  // the legacy stream cannot be captured
-        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
-        own = true;
-      }
-      CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-      rc = issue(g, cap, true);
-      cudaGraph_t graph = nullptr;
-      cudaError_t e = cudaStreamEndCapture(cap, &graph);
-      if (rc != LQC_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        if (own) cudaStreamDestroy(cap);
-        return rc;
-      }
-      if (e != cudaSuccess) {
-        if (own) cudaStreamDestroy(cap);
-        return cuda_fail(g, e, "end capture");
-      }
-      e = cudaGraphInstantiate(&x.graph, graph, 0);
-      cudaGraphDestroy(graph);
-      if (own) cudaStreamDestroy(cap);
-      if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
-      x.graph_stream = cs;
-    }
     CK(cudaGraphLaunch(x.graph, cs), "graph launch");
   } else {
     rc = issue(g, cs, false);
@@ -947,6 +1046,7 @@ int exec_run(Dag& g, void* stream) {
   g.info.copied_h2d = x.copy_h2d;
   g.info.copied_d2h = x.copy_d2h;
   g.info.n_ops = (int64_t)g.ops.size();
+  g.info.resident_peak_bytes = x.resident_peak;
   g.executed = true;
   return LQC_OK;
 }

@@ -95,6 +95,7 @@ int64_t model_peak(const Dag& g, const std::vector<int64_t>& order);
 
 // ---- executor (exec.cu) ----
 int exec_run(Dag& g, void* stream);
+int exec_prepare(Dag& g, void* stream);
 int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64_t cap,
                   int64_t* n);
 int exec_wait(Dag& g, int64_t timeout_ms);

@@ -1822,14 +1822,36 @@ void rebase_level(LevelDev* lvl, const char* base) {
   rb(lvl->ca_starts);
 }
 
-int launch_level(const LevelDev& L, cudaStream_t s) {
+int level_launch_kinds(const LevelDev& L, int kinds[LQC_NUM_KINDS]) {
+  int n = 0;
+  if (L.nperm > 0) kinds[n++] = LQC_KIND_REORDER;
+  if (L.npack > 0) {
+    kinds[n++] = LQC_KIND_PACK;
+    kinds[n++] = LQC_KIND_GEMM_PLANES;
+  }
+  if (L.ngemm_fused > 0) kinds[n++] = LQC_KIND_GEMM_FUSED;
+  if (L.nred > 0) kinds[n++] = LQC_KIND_REDUCE;
+  if (L.nca > 0) {
+    kinds[n++] = LQC_KIND_CORRELATOR;
+    kinds[n++] = LQC_KIND_CORRELATOR_SUM;
+  }
+  return n;
+}
+
+int launch_level(const LevelDev& L, cudaStream_t s, cudaEvent_t* marks, unsigned mark_flags) {
   int nk = 0;
+  // marks[i] before the i-th launch, marks[n] after the last
+  auto mark = [&]() {
+    if (marks) cudaEventRecordWithFlags(marks[nk], s, mark_flags);
+  };
   if (L.nperm > 0) {  // operand reorders of fused GEMMs and correlator partners
+    mark();
     k_permute_grouped<<<(unsigned)L.perm_blocks, 256, 0, s>>>(
         static_cast<const PermTask*>(L.perm), L.perm_starts, L.nperm);
     ++nk;
   }
   if (L.npack > 0) {
+    mark();
     if (L.bf16)
       k_pack_grouped<true><<<(unsigned)L.pack_blocks, 256, 0, s>>>(
           static_cast<const PackTask*>(L.pack), L.pack_starts, L.npack);
@@ -1842,6 +1864,7 @@ int launch_level(const LevelDev& L, cudaStream_t s) {
     gp.tasks = static_cast<const GemmTask*>(L.gemm);
     gp.ntasks = L.ngemm;
     gp.total_tiles = L.gemm_tiles;
+    mark();
     if (launch_gemm(gp, L.bf16, false, s) < 0) return -1;
     ++nk;
   }
@@ -1851,21 +1874,27 @@ int launch_level(const LevelDev& L, cudaStream_t s) {
     gp.tasks = static_cast<const GemmTask*>(L.gemm_fused);
     gp.ntasks = L.ngemm_fused;
     gp.total_tiles = L.gemm_fused_tiles;
+    mark();
     if (launch_gemm(gp, false, true, s) < 0) return -1;
     ++nk;
   }
   if (L.nred > 0) {
+    mark();
     k_reduce_grouped<<<(unsigned)L.red_blocks, 256, 0, s>>>(
         static_cast<const ReduceTask*>(L.red), L.red_starts, L.nred);
     ++nk;
   }
   if (L.nca > 0) {
+    mark();
     k_contract_all_grouped<<<(unsigned)L.ca_blocks, 256, 0, s>>>(
         static_cast<const CATask*>(L.ca), L.ca_starts, L.nca);
+    ++nk;
+    mark();
     k_contract_all_final_grouped<<<(unsigned)((L.ca_threads + 127) / 128), 128, 0, s>>>(
         static_cast<const CATask*>(L.ca), L.nca, L.ca_threads);
-    nk += 2;
+    ++nk;
   }
+  mark();
   return cudaPeekAtLastError() == cudaSuccess ? nk : -1;
 }
 

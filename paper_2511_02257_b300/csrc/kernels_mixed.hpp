@@ -136,8 +136,14 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
                         bool bf16, std::vector<char>* buf, LevelDev* lvl);
 // turn the offsets into device addresses once buf has been copied to `base`
 void rebase_level(LevelDev* lvl, const char* base);
-// launch one level on `s`; returns kernels launched or -1
-int launch_level(const LevelDev& lvl, cudaStream_t s);
+// kinds (lqc_launch_kind) of the launches of one level, in launch order;
+// returns their number
+int level_launch_kinds(const LevelDev& lvl, int kinds[LQC_NUM_KINDS]);
+// launch one level on `s`; returns kernels launched or -1.  marks (nullable):
+// level_launch_kinds() + 1 events, marks[i] recorded before the i-th launch
+// and the last after the final one, with cudaEventRecordWithFlags(mark_flags)
+int launch_level(const LevelDev& lvl, cudaStream_t s, cudaEvent_t* marks = nullptr,
+                 unsigned mark_flags = 0);
 
 // First error code recorded by a mixed kernel (bounded wait expired), or 0;
 // -1 if it cannot be read.  reset = clear it after reading.

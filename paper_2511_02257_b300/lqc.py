@@ -36,6 +36,9 @@ LQC_PREC_FP64, LQC_PREC_TF32X3, LQC_PREC_BF16X3 = 0, 1, 2
 LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING, LQC_OPT_WINDOW = 1, 2, 3, 4
 LQC_OPT_FUSED_MAX_N, LQC_OPT_SPLIT_POLICY = 5, 6
 OP_NAMES = {0: "LOAD", 1: "EVICT", 2: "CONTRACT", 3: "FREE"}
+LQC_NUM_KINDS = 8
+KIND_NAMES = {0: "reorder", 1: "pack", 2: "gemm_planes", 3: "gemm_fused", 4: "reduce",
+              5: "correlator", 6: "correlator_sum"}
 POLICIES = {"naive": LQC_SCHED_NAIVE_TOPO, "tree": LQC_SCHED_TREE, "sibling": LQC_SCHED_SIBLING,
             "node": LQC_SCHED_NODE, "rsgs": LQC_SCHED_RSGS}
 EVICTS = {"lru": LQC_EVICT_LRU, "next_use": LQC_EVICT_NEXT_USE}
@@ -57,10 +60,15 @@ class lqc_exec_info(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in ("n_kernels", "flops", "arena_bytes", "copied_h2d",
                                      "copied_d2h", "n_ops", "n_contract", "n_contract_all")] + \
         [("ms_contract", ctypes.c_double), ("ms_contract_all", ctypes.c_double),
-         ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64)]
+         ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64),
+         ("n_kind", c_i64 * LQC_NUM_KINDS), ("ms_kind", ctypes.c_double * LQC_NUM_KINDS),
+         ("flops_gemm", c_i64), ("resident_peak_bytes", c_i64)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d["n_kind"] = {KIND_NAMES[k]: int(self.n_kind[k]) for k in KIND_NAMES}
+        d["ms_kind"] = {KIND_NAMES[k]: float(self.ms_kind[k]) for k in KIND_NAMES}
+        return d
 
 
 class lqc_tune_entry(ctypes.Structure):
@@ -97,6 +105,7 @@ _sig("lqc_dag_set_option", ctypes.c_int, [c_vp, ctypes.c_int, c_i64])
 _sig("lqc_dag_stage_leaves", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_unstage_leaves", ctypes.c_int, [c_vp])
 _sig("lqc_dag_execute", ctypes.c_int, [c_vp, c_vp])
+_sig("lqc_dag_prepare", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_wait", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_autotune", ctypes.c_int, [c_vp, c_vp, ctypes.c_int, ctypes.POINTER(lqc_tune_entry),
                                         c_i64, P_i64])
@@ -323,6 +332,9 @@ class Dag:
 
     def execute(self, stream: int = 0):
         self._check(_lib.lqc_dag_execute(self.h, c_vp(stream)), "execute")
+
+    def prepare(self, stream: int = 0):
+        self._check(_lib.lqc_dag_prepare(self.h, c_vp(stream)), "prepare")
 
     def autotune(self, stream: int = 0, reps: int = 3):
         """Time every candidate of (window, fused-form limit, split policy)

@@ -29,7 +29,8 @@
  *    right axis ra[i] (equal extents), f_L are the left operand's unpaired
  *    axes in order and f_R the right operand's.  A rank-0 output is a
  *    correlator: one complex number per time slice (the paper's
- *    "contract all" of a root, Sec. IV-A).
+ *    "contract all" (HCA) of a root, Sec. II-A, beside the exterior
+ *    contractions (HEC) that produce the intermediate tensors).
  *  - Node types (Sec. II-B): LEAF = no inputs, ROOT = no consumers,
  *    INTERIOR = the rest.  Contraction tree T_r = descendant closure of
  *    root r.  A correlation function made of several trees is the caller's
@@ -184,10 +185,14 @@ typedef struct {
   double ms;             /* device time per execute (CUDA events) */
 } lqc_tune_entry;
 
-/* Create an empty DAG.  lt in [1, 2^31) time slices (the batch extent of
- * the leaves registered next, see lqc_dag_set_batch); prec selects storage
- * and arithmetic.  *out receives the handle (owned by the caller, released
- * with lqc_dag_destroy).
+/* Create an empty DAG: the contraction DAG G = (V, E) of Sec. II-B, into
+ * which the contraction trees of every correlation function are merged, as
+ * Redstar forms one DAG over all correlation functions (Sec. II-A).
+ * lt in [1, 2^31) time slices (the batch extent of the leaves registered
+ * next, see lqc_dag_set_batch); prec selects storage and arithmetic.  *out
+ * receives the handle (owned by the caller, released with lqc_dag_destroy).
+ * Errors: LQC_ERR_ARG (out NULL, lt or prec out of range),
+ * LQC_ERR_HOST_MEM.
  * Size limits of every tensor: at most 2^40 elements per time slice and
  * 2^58 over all slices (checked as nodes are added, before any product can
  * overflow). */
@@ -201,8 +206,10 @@ int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec);
  * [1, 2^31)), LQC_ERR_STATE (after lqc_dag_schedule). */
 int lqc_dag_set_batch(lqc_dag* dag, int64_t lt);
 
-/* Release every host and device resource of the DAG.  Synchronises with any
- * outstanding execution first.  NULL is accepted. */
+/* Release every host and device resource of the DAG (the end of the DAG's
+ * life; the paper has no counterpart beyond releasing tensors, Sec. II-C).
+ * Synchronises with any outstanding execution first (bounded wait; a
+ * device error is not reported here).  NULL is accepted. */
 int lqc_dag_destroy(lqc_dag* dag);
 
 /* Register a leaf tensor (Sec. II-B: a node with no inputs).
@@ -283,6 +290,13 @@ int lqc_dag_add_graphs(lqc_dag* dag, int64_t n_graphs, const int64_t* vert_off,
 /* Freeze the DAG, compute the contraction order with `policy` and replay it
  * under `budget_bytes` (0 = unlimited) with eviction policy `evict`,
  * producing the op list (LOAD / EVICT / CONTRACT / FREE) and its figures.
+ * The order solves the problem of Sec. II-C: a topological order c_1..c_n of
+ * the contractions whose peak max_i M_i of the memory model is small (tree
+ * scheduler, Sec. III-B, Alg. 4-8; sibling scheduler, Sec. III-A, Alg. 1-3;
+ * the node-based scheduler named in Sec. VI; the similarity order of trees
+ * Redstar uses, Sec. II-A).  The replay adds the device budget and the
+ * evictions to host memory that MemHC performs in Redstar (Sec. II-A), by
+ * the rules written with lqc_evict.
  * `planned` (nullable) receives the figures.  May be called again with other
  * arguments (replaces the previous schedule).
  * Errors: LQC_ERR_BUDGET if one contraction's inputs + output exceed the
@@ -296,7 +310,9 @@ int lqc_dag_schedule(lqc_dag* dag, lqc_policy policy, lqc_evict evict,
 int lqc_dag_set_order(lqc_dag* dag, const int64_t* order, int64_t n, lqc_evict evict,
                       uint64_t budget_bytes, lqc_stats* planned);
 
-/* Copy the current order (non-leaf ids) into order[0..cap); *n receives
+/* The contraction order c_1..c_n of Sec. II-C chosen by the last
+ * lqc_dag_schedule or lqc_dag_set_order.
+ * Copy the current order (non-leaf ids) into order[0..cap); *n receives
  * its length (also when cap is too small, in which case nothing is copied
  * and LQC_ERR_ARG is returned).  LQC_ERR_STATE before scheduling. */
 int lqc_dag_get_order(lqc_dag* dag, int64_t* order, int64_t cap, int64_t* n);
@@ -319,7 +335,11 @@ int lqc_dag_stage_leaves(lqc_dag* dag, void* stream);
 int lqc_dag_unstage_leaves(lqc_dag* dag);
 
 /* Execute the scheduled op list asynchronously on `stream` (a cudaStream_t;
- * NULL = the legacy default stream).  Host-to-device loads and write-backs
+ * NULL = the legacy default stream): per contraction c_i the steps of the
+ * memory model of Sec. II-C -- bring the leaves it needs to the device,
+ * perform it (an exterior contraction, or the contract-all of a root,
+ * Sec. II-A), release what no later contraction needs -- plus the planned
+ * evictions and reloads (Sec. II-A, MemHC).  Host-to-device loads and write-backs
  * run on two side streams owned by the library, ordered with the compute
  * stream by events.  Correlators land in a device buffer read by
  * lqc_dag_read_correlator.  The first call on a DAG allocates the device
@@ -358,8 +378,10 @@ int lqc_dag_autotune(lqc_dag* dag, void* stream, int reps, lqc_tune_entry* entri
  * usable; call again), LQC_ERR_CUDA on a device error. */
 int lqc_dag_wait(lqc_dag* dag, int64_t timeout_ms);
 
-/* Correlator of a rank-0 root: out[2*t], out[2*t+1] = re, im of C_root(t),
- * t in [0, lt of the root).  Waits for the last execute (60 s bound).
+/* Correlator of a rank-0 root, the final value its contract-all (HCA,
+ * Sec. II-A) produced: out[2*t], out[2*t+1] = re, im of C_root(t), t in
+ * [0, lt of the root); out is a caller-owned host array of 2 * lt doubles,
+ * written only on LQC_OK.  Waits for the last execute (60 s bound).
  * Errors: LQC_ERR_ARG (not a rank-0 root), LQC_ERR_STATE (not executed). */
 int lqc_dag_read_correlator(lqc_dag* dag, int64_t root_id, double* out);
 
@@ -385,8 +407,16 @@ int lqc_dag_node_info(lqc_dag* dag, int64_t id, int64_t* size_bytes, int* rank,
 int lqc_dag_node_operands(lqc_dag* dag, int64_t id, int64_t* left, int64_t* right,
                           int* npairs, int* la, int* ra);
 
-/* Figures counted by the last execute (equal to the planned figures by
- * construction of the executor; peak_exec is taken from the plan). */
+/* Figures of the last execute, counted by the executor (the quantities of
+ * Sec. II-C and those the paper measures in Sec. IV-B/IV-C: peak memory,
+ * evictions, host<->device transfers).  n_h2d, n_d2h and the bytes count
+ * the copies the execute issued (with staged leaves, leaf loads are served
+ * from the device copy and not counted); n_evict and peak_exec come from the
+ * executor's own walk of the op list (evictions it performed; device bytes
+ * held while each contraction runs, frees at their op); peak_paper is the
+ * model figure of the order (Sec. II-C), taken from the plan.  A DAG that
+ * executes its plan unchanged reports the planned figures.  Errors:
+ * LQC_ERR_STATE (not executed). */
 int lqc_dag_get_stats(lqc_dag* dag, lqc_stats* measured);
 int lqc_dag_get_exec_info(lqc_dag* dag, lqc_exec_info* info);
 
@@ -410,15 +440,15 @@ const char* lqc_last_error(const lqc_dag* dag);
  * --------------------------------------------------------------------- */
 
 /* Exterior contraction (output rank >= 1), FP64 arithmetic (Sec. II-B
- * binary contraction; the paper's "exterior contract" queue op, Sec. IV-A).
+ * binary contraction; an exterior contraction (HEC) of Sec. II-A).
  * Errors: LQC_ERR_ARG (shapes/pairs), LQC_ERR_CUDA (launch). */
 int lqc_contract_fp64(const double* A, int rank_a, const int64_t* ext_a,
                       const double* B, int rank_b, const int64_t* ext_b,
                       int npairs, const int* la, const int* ra, int64_t lt,
                       double* C, void* stream);
 
-/* Contract-all (every axis paired; rank-0 output = correlator, Sec. IV-A):
- * C[t] = sum over all indices of A[t][...] * B[t][paired ...], FP64
+/* Contract-all (every axis paired; rank-0 output = correlator, the
+ * contract-all (HCA) of Sec. II-A): C[t] = sum over all indices of A[t][...] * B[t][paired ...], FP64
  * accumulation in a fixed order (results are bit-reproducible).
  * `scratch` must hold lqc_contract_all_scratch_bytes(...) bytes of device
  * memory (caller-owned; its previous contents are ignored).

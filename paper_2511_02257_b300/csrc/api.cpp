@@ -228,7 +228,8 @@ int lqc_dag_add_contractions(lqc_dag* h, int64_t n, const int64_t* left, const i
   for (int64_t i = 0; i < n; ++i) {
     const int np = npairs[i];
     // -(j+1): the node request j of this call received
-    auto resolve = [&](int64_t x) { return x >= 0 ? x : (-x - 1 < i ? node_ids[-x - 1] : -1); };
+    // (x >= -i before negating: -x of INT64_MIN would overflow)
+    auto resolve = [&](int64_t x) { return x >= 0 ? x : (x >= -i ? node_ids[-(x + 1)] : -1); };
     const int64_t l = resolve(left[i]), r = resolve(right[i]);
     const int rc = np < 1 || np > LQC_MAX_RANK
                        ? fail(h, LQC_ERR_ARG, "npairs must be in [1, LQC_MAX_RANK]")

@@ -994,6 +994,7 @@ int ensure_graph(Dag& g, cudaStream_t cs) {
 }  // namespace
 
 int exec_prepare(Dag& g, void* stream) {
+  clear_pending_error();  // an earlier, unrelated error must not fail this DAG's launches
   int rc = ensure_state(g);
   if (rc != LQC_OK) return rc;
   ExecState& x = *g.ex;

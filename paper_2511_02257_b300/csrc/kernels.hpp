@@ -11,6 +11,17 @@
 
 namespace lqc {
 
+// One-shot C entry points: an error that earlier, unrelated runtime calls of
+// this thread left pending must not fail this call, and this call's own
+// launch error must not fail later ones.  Clear before launching, consume
+// after a failed launch (a sticky device error still fails both).
+inline void clear_pending_error() { (void)cudaGetLastError(); }
+inline int launch_status(int kernels) {
+  if (kernels >= 0) return LQC_OK;
+  (void)cudaGetLastError();
+  return LQC_ERR_CUDA;
+}
+
 // A set of tensor axes flattened row-major into one index: element offset of
 // flattened index i = sum_d digit_d(i) * stride[d], digits taken with the
 // last axis innermost.

@@ -7,7 +7,7 @@
 //     rate, so this kernel is bound by the FP64 pipe; the tile loop keeps that
 //     pipe fed (register-blocked complex MACs, smem-staged operand tiles,
 //     register prefetch of the next k-slab).
-// K2  contract-all (a root's "contract all", Sec. IV-A): per time slice the
+// K2  contract-all (a root's "contract all" (HCA), Sec. II-A): per time slice the
 //     full pairing sum of two tensors, FP64 accumulation in a fixed order:
 //     per-CTA partials in scratch memory, then an ordered per-slice sum.
 #include <algorithm>
@@ -408,8 +408,9 @@ int lqc_contract_fp64(const double* A, int rank_a, const int64_t* ext_a, const d
   std::string err;
   if (!lqc::make_contract_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &d, &err))
     return LQC_ERR_ARG;
+  lqc::clear_pending_error();
   int k = lqc::launch_contract_fp64(d, A, B, C, static_cast<cudaStream_t>(stream));
-  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+  return lqc::launch_status(k);
 }
 
 int lqc_measure_fp64_peak(double* tflops) {
@@ -461,9 +462,10 @@ int lqc_contract_all_fp64(const double* A, int rank_a, const int64_t* ext_a, con
   std::string err;
   if (!lqc::make_contract_all_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &d, &err))
     return LQC_ERR_ARG;
+  lqc::clear_pending_error();
   int k = lqc::launch_contract_all_fp64(d, A, B, C, static_cast<double*>(scratch),
                                          static_cast<cudaStream_t>(stream));
-  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+  return lqc::launch_status(k);
 }
 
 }  // extern "C"

@@ -1930,8 +1930,9 @@ int lqc_contract_mixed(const float* A, int rank_a, const int64_t* ext_a, const f
     return LQC_ERR_ARG;
   if (!lqc::make_mixed_desc(cd, prec == LQC_PREC_BF16X3, &md)) return LQC_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return LQC_ERR_ARG;
+  lqc::clear_pending_error();
   int k = lqc::launch_contract_mixed(md, A, B, C, scratch, static_cast<cudaStream_t>(stream));
-  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+  return lqc::launch_status(k);
 }
 
 int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a, const float* B,
@@ -1943,9 +1944,10 @@ int lqc_contract_all_c64(const float* A, int rank_a, const int64_t* ext_a, const
   std::string err;
   if (!lqc::make_contract_all_desc(rank_a, ext_a, rank_b, ext_b, npairs, la, ra, lt, &d, &err))
     return LQC_ERR_ARG;
+  lqc::clear_pending_error();
   int k = lqc::launch_contract_all_c64(d, A, B, C, static_cast<double*>(scratch), scale,
                                        static_cast<cudaStream_t>(stream));
-  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+  return lqc::launch_status(k);
 }
 
 int64_t lqc_contract_all_c64_scratch_bytes(int rank_a, const int64_t* ext_a, int rank_b,

@@ -71,9 +71,10 @@ int lqc_contract_all_fp64_noalloc(const double* A, int rank_a, const int64_t* ex
   void* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc != LQC_OK) return rc;
+  lqc::clear_pending_error();
   int k = lqc::launch_contract_all_fp64(d, A, B, C, static_cast<double*>(scratch),
                                          static_cast<cudaStream_t>(stream));
-  return k < 0 ? LQC_ERR_CUDA : LQC_OK;
+  return lqc::launch_status(k);
 }
 
 }  // extern "C"

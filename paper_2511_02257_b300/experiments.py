@@ -1,4 +1,4 @@
-"""Scheduler comparisons on the device (the paper's Sec. IV-B measurements).
+"""Scheduler comparisons on the device (the paper's Sec. IV-B and IV-C measurements).
 
 For one synthetic workload and a device budget, every policy (naive
 topological order, sibling, tree) is scheduled, planned and executed; the

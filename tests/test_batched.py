@@ -164,34 +164,55 @@ def test_batched_dag_vs_oracle(precision, tol):
 @pytest.mark.gpu
 def test_batched_full_size_sampled_roots_tf32x3():
     """The full batched workload (50 parts, ~18k contractions, N 32..256,
-    Lt 16..128) in grouped windows with CUDA graphs; a seeded sample of
-    correlators (one per size class where possible) against the oracle."""
+    Lt 16..128) in grouped windows with CUDA graphs: 64 seeded correlators,
+    at least two of every (N, Lt) class of the parts, against the oracle
+    (<= 1e-6), and every correlator against the FP64 GPU path (whose parity
+    with the oracle the other tests pin) within the same bar."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     wl = synth.make_workload("batched")
-    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: synth.leaf_data(wl, li))
-    nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
-    planned = nd.schedule("tree", "lru", wl.budget_bytes)
-    nd.execute(torch.cuda.current_stream().cuda_stream)
-    assert nd.stats() == planned
-    od, _ = D.build_from_workload(wl)
-    roots = od.roots()
-    rng = np.random.default_rng(9)
-    by_n = {}
-    for r in rng.permutation(roots).tolist():
-        leaf = next(u for u in od.tree(r) if od.nodes[u].is_leaf)
-        by_n.setdefault(wl.leaves[od.nodes[leaf].leaf_index].nvec, r)
-    pick = sorted(by_n.values())
-    assert len(pick) >= 5
     cache = {}
 
-    def lf(u):
-        li = od.nodes[u].leaf_index
+    def leaf(li):
         if li not in cache:
             cache[li] = synth.leaf_data(wl, li)
         return cache[li]
-    ref = C.evaluate(od, lf, pick)
-    errs = {r: float(np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r]))
+    stream = torch.cuda.current_stream().cuda_stream
+    vals = {}
+    for precision in ("tf32x3", "fp64"):
+        nd, _ = L.build_dag(wl, precision=precision, leaf_data_fn=leaf)
+        nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
+        if precision != "fp64":
+            nd.set_option(L.LQC_OPT_WINDOW, 512)
+            nd.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+        planned = nd.schedule("tree", "lru", wl.budget_bytes)
+        nd.execute(stream)
+        assert nd.stats() == planned
+        vals[precision] = {r: nd.read_correlator(r) for r in nd.roots()}
+        nd.close()
+    od, _ = D.build_from_workload(wl)
+    roots = od.roots()
+    assert sorted(roots) == sorted(vals["tf32x3"])
+    # every correlator against the FP64 path
+    e64 = [np.linalg.norm(vals["tf32x3"][r] - vals["fp64"][r]) / np.linalg.norm(vals["fp64"][r])
+           for r in roots]
+    assert max(e64) < 1e-6, max(e64)
+    # 64 seeded roots against the oracle, two or more from every class
+    rng = np.random.default_rng(9)
+    by_class = {}
+    for r in rng.permutation(roots).tolist():
+        leafnode = next(u for u in od.tree(r) if od.nodes[u].is_leaf)
+        li = od.nodes[leafnode].leaf_index
+        by_class.setdefault((wl.leaf_nvec(li), wl.leaf_lt(li)), []).append(r)
+    assert len(by_class) >= 10
+    pick = [r for rs in by_class.values() for r in rs[:2]]
+    rest = [r for r in rng.permutation(roots).tolist() if r not in set(pick)]
+    pick += rest[:max(0, 64 - len(pick))]
+    assert len(pick) >= 64
+    ref = C.evaluate(od, lambda u: leaf(od.nodes[u].leaf_index), pick)
+    errs = {r: float(np.linalg.norm(vals["tf32x3"][r] - ref[r]) / np.linalg.norm(ref[r]))
             for r in pick}
-    assert max(errs.values()) < 1e-6, errs
+    assert max(errs.values()) < 1e-6, max(errs.values())
+    e64o = [np.linalg.norm(vals["fp64"][r] - ref[r]) / np.linalg.norm(ref[r]) for r in pick]
+    assert max(e64o) < 1e-12, max(e64o)

@@ -168,7 +168,7 @@ def test_tiny_dag_all_schedules(seed):
     od, ref = _oracle(wl)
     nd, _ = _native(wl)
     base = None
-    for pol in ("tree", "naive", "sibling"):
+    for pol in ("tree", "naive", "sibling", "rsgs", "node"):
         planned, vals = _run(nd, pol)
         assert set(vals) == set(ref)
         for r in ref:
@@ -201,9 +201,12 @@ def test_budgeted_eviction_matches_oracle(evict):
     free = M.replay(od, S.naive(od))
     budget = free.stats.peak_exec // 4
     nd, _ = _native(wl)
-    for pol in ("naive", "sibling", "tree"):
+    base = None
+    evicted = {}
+    for pol in ("naive", "sibling", "tree", "rsgs", "node"):
         planned, vals = _run(nd, pol, evict, budget)
         oplan = M.replay(od, S.SCHEDULERS[pol](od), budget=budget, policy=evict)
+        assert nd.order() == S.SCHEDULERS[pol](od), pol
         assert tuple(planned[k] for k in planned) == oplan.stats.as_tuple()
         assert nd.stats() == planned
         info = nd.exec_info()
@@ -211,7 +214,12 @@ def test_budgeted_eviction_matches_oracle(evict):
         assert info["copied_d2h"] == planned["d2h_bytes"]
         for r in ref:
             assert rel_err(vals[r], ref[r]) < TOL, (pol, r)
-    assert oplan.stats.n_evict >= 0
+        if base is None:
+            base = vals
+        for r in ref:           # orders, budgets and evictions do not change a bit
+            assert np.array_equal(vals[r].view(np.float64), base[r].view(np.float64)), pol
+        evicted[pol] = planned["n_evict"]
+    assert evicted["naive"] > 0
 
 
 def test_naive_budget_really_evicts():

@@ -80,22 +80,15 @@ def test_closed_form_and_mn_zero_exhaustive(seed):
         assert plan.stats.peak_paper == max(after)
         assert plan.stats.n_evict == 0 and plan.stats.d2h_bytes == 0
         assert plan.stats.h2d_bytes == sum(dag.size(u) for u in dag.used_leaves())
-        if count > 400:
-            break
-    assert count >= 1
+    assert count >= 1      # every order of the 10-node DAG (at most 6! of them)
 
 
 @pytest.mark.parametrize("seed", range(25))
 @pytest.mark.parametrize("policy", [M.LRU, M.NEXT_USE])
 def test_budgeted_replays_valid(seed, policy):
-    lt, leaves, contr = random_spec(100 + seed, n_leaves=5, n_contr=7)
-    dag = D.from_spec(lt, leaves, contr)
-    orders = []
-    for k, o in enumerate(topological_orders(dag)):
-        orders.append(o)
-        if k > 60:
-            break
-    for order in orders:
+    lt, leaves, contr = random_spec(100 + seed, n_leaves=4, n_contr=6)
+    dag = D.from_spec(lt, leaves, contr)       # 10 nodes: every order
+    for order in topological_orders(dag):
         free = M.replay(dag, order)
         need_max = max(sum(dag.size(x) for x in dag.nodes[c].children) + dag.size(c)
                        for c in order)

@@ -98,3 +98,52 @@ def test_orientation_larger_tensor_left():
         got = C.evaluate(dag, lambda u: mv if u == Mn else pv, roots)[roots[0]]
         want = np.einsum("tab,tsuba->tsu", mv, pv)
         assert np.allclose(got, want, rtol=1e-12, atol=0)
+
+
+def _ring4(w, x, y, z):
+    # Tr(W X Y Z) of matrices: W.1-X.0, X.1-Y.0, Y.1-Z.0, Z.1-W.0
+    return [w, x, y, z], [(0, 1, 1, 0), (1, 1, 2, 0), (2, 1, 3, 0), (3, 1, 0, 0)]
+
+
+# The contractions path selection must build for Tr(A B C D) and Tr(A B E F)
+# with extents a = b = c = e = 2 and d = 16 (A: a x b, B: b x c, C: c x d,
+# D: d x a, E: c x e, F: e x a), derived by hand (per slice, cost = M N K):
+#  1. candidates: A.B in both terms, cost 8, value 2 x 8 = 16; in the first
+#     term B.C, C.D, D.A cost 64 each (value 64); in the second every pair
+#     costs 8.  The largest value is 64; of the tied keys (left = the larger
+#     tensor, equal sizes -> smaller id) (C,B,(0,),(1,)) < (C,D,(1,),(0,)) <
+#     (D,A,(1,),(0,)), so C.B -> node 6 [d x b].  A selection by frequency
+#     alone would take A.B here.
+#  2. first term [A, 6, D]: 6.A, D.6, D.A all cost 64; smallest key
+#     (D,A,(1,),(0,)) -> node 7 [d x b].
+#  3. first term [7, 6]: both axes pair, equal sizes -> left 6:
+#     (6,7,(0,1),(0,1)) -> root 8 (cost 32 > 8).
+#  4. second term, every pair 8: smallest key (A,B,(1,),(0,)) -> node 9 [a x c].
+#  5. [9, E, F]: keys (E,9,(0,),(1,)), (F,9,(1,),(0,)), (E,F,(1,),(0,)):
+#     smallest (E,F,(1,),(0,)) -> node 10 [c x a].
+#  6. [9, 10]: 9.0-10.1 (a), 9.1-10.0 (c) -> root 11 (9,10,(0,1),(1,0)).
+COSTLY_PAIR_EXPECTED = [(2, 1, (0,), (1,)), (3, 0, (1,), (0,)), (6, 7, (0, 1), (0, 1)),
+                        (0, 1, (1,), (0,)), (4, 5, (1,), (0,)), (9, 10, (0, 1), (1, 0))]
+COSTLY_PAIR_SHAPES = [(2, 2), (2, 2), (2, 16), (16, 2), (2, 2), (2, 2)]
+
+
+def test_rarer_costlier_pair_beats_frequent_cheap_one():
+    """count x cost, not count: the once-occurring C.B (cost 64) is built
+    before the twice-occurring A.B (cost 8); the whole DAG as derived by
+    hand above, and both traces equal einsum."""
+    lt = 2
+    dag = D.Dag(lt)
+    A, B, Cm, Dm, E, F = (dag.add_leaf(s, leaf_index=i) for i, s in enumerate(COSTLY_PAIR_SHAPES))
+    roots = PS.select_paths(dag, [_ring4(A, B, Cm, Dm), _ring4(A, B, E, F)])
+    got = [(dag.nodes[u].left, dag.nodes[u].right, tuple(dag.nodes[u].la), tuple(dag.nodes[u].ra))
+           for u in dag.non_leaf()]
+    assert got == COSTLY_PAIR_EXPECTED
+    assert roots == [8, 11]
+    rng = np.random.default_rng(2)
+    data = [rng.standard_normal((lt,) + s) + 1j * rng.standard_normal((lt,) + s)
+            for s in COSTLY_PAIR_SHAPES]
+    vals = C.evaluate(dag, lambda u: data[u], roots)
+    want1 = np.einsum("tab,tbc,tcd,tda->t", data[0], data[1], data[2], data[3])
+    want2 = np.einsum("tab,tbc,tce,tea->t", data[0], data[1], data[4], data[5])
+    assert np.allclose(vals[8], want1, rtol=1e-12, atol=0)
+    assert np.allclose(vals[11], want2, rtol=1e-12, atol=0)

@@ -321,3 +321,16 @@ def test_paths_bit_exact_random_graphs_mixed_extents(seed):
     oroots = PS.select_paths(od, graphs)
     assert nd.add_graphs(graphs) == oroots
     assert _structure_native(nd) == _structure_oracle(od)
+
+
+def test_rarer_costlier_pair_native():
+    """The hand-derived count x cost example of test_oracle_paths: the
+    native selection builds the same six contractions, written out by hand
+    there (the once-occurring C.B of cost 64 before the twice-occurring A.B
+    of cost 8)."""
+    from test_oracle_paths import COSTLY_PAIR_EXPECTED, COSTLY_PAIR_SHAPES, _ring4
+    nd = L.Dag(2)
+    A, B, Cm, Dm, E, F = (nd.add_leaf(s) for s in COSTLY_PAIR_SHAPES)
+    roots = nd.add_graphs([_ring4(A, B, Cm, Dm), _ring4(A, B, E, F)])
+    assert roots == [8, 11]
+    assert [nd.node_operands(u) for u in range(6, nd.num_nodes())] == COSTLY_PAIR_EXPECTED

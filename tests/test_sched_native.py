@@ -93,9 +93,10 @@ def test_orders_and_plans_bit_exact_workloads(name):
             assert got == [(k, u, f) for (k, u, f) in plan.ops]
 
 
-@pytest.mark.parametrize("seed", range(20))
+@pytest.mark.parametrize("seed", range(40))
 def test_plans_bit_exact_exhaustive(seed):
-    lt, leaves, contr = random_spec(2000 + seed, n_leaves=5, n_contr=7, share=0.6)
+    # 10 nodes: every topological order of the contractions, no cap
+    lt, leaves, contr = random_spec(2000 + seed, n_leaves=4, n_contr=6, share=0.6)
     od = D.from_spec(lt, leaves, contr)
     nd = native_from_spec(lt, leaves, contr)
     n_orders = 0
@@ -115,8 +116,7 @@ def test_plans_bit_exact_exhaustive(seed):
         with pytest.raises(L.LqcError) as ei:
             nd.set_order(order, "lru", need - 1)
         assert ei.value.code == L.LQC_ERR_BUDGET
-        if n_orders >= 150:
-            break
+    assert n_orders == sum(1 for _ in topological_orders(od))
 
 
 def test_table1_schedules_native():
@@ -247,3 +247,18 @@ def test_bulk_contractions_errors_leave_dag_unchanged():
     ids = d.add_contractions([(a, b, [1], [0]), (a, b, [1], [0]), (-2, -1, [0], [0])])
     assert ids[0] == ids[1] == n0 and ids[2] == n0 + 1
     assert d.node_operands(ids[2]) == (n0, n0, (0,), (0,))
+
+
+def test_add_contractions_rejects_extreme_back_references():
+    """Operand ids below -(i) (no earlier request of the call), down to
+    INT64_MIN, are argument errors and leave the DAG unchanged."""
+    d = L.Dag(2)
+    a = d.add_leaf((3, 3))
+    n0 = d.num_nodes()
+    for bad in (-(2 ** 63), -(2 ** 63) + 1, -2, -1):
+        with pytest.raises(L.LqcError) as ei:
+            d.add_contractions([(a, bad, [1], [0])])
+        assert ei.value.code == L.LQC_ERR_ARG
+        assert d.num_nodes() == n0
+    ab = d.add_contractions([(a, a, [1], [0]), (-1, a, [1], [0])])
+    assert ab == [n0, n0 + 1]

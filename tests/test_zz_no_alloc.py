@@ -37,12 +37,14 @@ def _arr(xs, dt, pt):
     return a, a.ctypes.data_as(pt)
 
 
-@pytest.mark.parametrize("lt", [1, 64, 700])
-def test_noalloc_matches_regular_entry_point_twice(lt):
+@pytest.mark.parametrize("lt,shape", [(1, (4, 4, 20, 20)), (64, (4, 4, 20, 20)),
+                                      (700, (4, 4, 20, 20)), (4096, (4, 4, 6, 6))])
+def test_noalloc_matches_regular_entry_point_twice(lt, shape):
+    """lt = 4096 with one chunk per slice fills the array exactly."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     noalloc = _lib()
-    sa, sb, la, ra = (4, 4, 20, 20), (4, 4, 20, 20), (0, 1, 2, 3), (1, 0, 3, 2)
+    sa, sb, la, ra = shape, shape, (0, 1, 2, 3), (1, 0, 3, 2)
     ea, pa = _arr(sa, np.int64, P_i64)
     eb, pb = _arr(sb, np.int64, P_i64)
     xla, pla = _arr(la, np.intc, P_int)
@@ -65,14 +67,20 @@ def test_noalloc_matches_regular_entry_point_twice(lt):
         assert rc == 0
         torch.cuda.synchronize()
         r, g = ref.cpu().numpy(), got.cpu().numpy()
+        # same kernels, same chunking: bit-identical; the tolerance only
+        # words the failure message
+        assert np.array_equal(g.view(np.float64), r.view(np.float64)), \
+            np.linalg.norm(g - r) / np.linalg.norm(r)
         assert np.linalg.norm(g - r) <= TOL * np.linalg.norm(r)
 
 
-def test_noalloc_rejects_beyond_its_array():
+@pytest.mark.parametrize("lt", [4097, 5000])
+def test_noalloc_rejects_beyond_its_array(lt):
+    """One slot more than the fixed array holds is rejected (the accepted
+    side of the bound, lt = 4096, runs above)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     noalloc = _lib()
-    lt = 5000          # more partial sums than the fixed array holds
     ea, pa = _arr((8,), np.int64, P_i64)
     xla, pla = _arr((0,), np.intc, P_int)
     d = torch.zeros(lt * 8, dtype=torch.complex128, device="cuda")

@@ -526,6 +526,37 @@ int lqc_mixed_error(int reset);
  * of the FP64 path's roofline).  Errors: LQC_ERR_CUDA. */
 int lqc_measure_fp64_peak(double* tflops);
 
+/* ---------------------------------------------------------------------
+ * Test hooks (no counterpart in the paper): failures made on the host, so
+ * that error paths can be tested without faulting a GPU.
+ * --------------------------------------------------------------------- */
+
+/* Arm one injected failure: after `skip_calls` successful calls at `site`,
+ * the next one returns an error without calling CUDA (0 = the library's
+ * device allocations, cudaMalloc; 1 = its pinned host allocations,
+ * cudaHostAlloc -- a leaf store then falls back to pageable memory, a
+ * write-back arena fails; 2 = its asynchronous copies, cudaMemcpyAsync).
+ * The failing library call returns LQC_ERR_CUDA (a leaf store: nothing) and
+ * the DAG stays usable.  site = -1 disarms every site.  Process-wide.
+ * Errors: LQC_ERR_ARG (site or skip_calls out of range). */
+int lqc_test_inject_failure(int site, int64_t skip_calls);
+
+/* Launch one thread that waits on a shared-memory mbarrier nothing arrives
+ * on, through the bounded-wait routine of the tensor-core kernels but with
+ * a limit of limit_ns (1 .. 1e9) instead of their 2 s; synchronises with
+ * `stream`.  Returns LQC_ERR_TIMEOUT when the wait expired and set the
+ * device error word (which lqc_dag_wait reads after an execute; this call
+ * clears it again), LQC_OK if it did not expire, LQC_ERR_ARG, LQC_ERR_CUDA. */
+int lqc_test_expire_wait(int64_t limit_ns, void* stream);
+
+/* Change the stored op list of a DAG scheduled without a budget, keeping
+ * the planned figures, so that a test can tell figures the executor counts
+ * from figures it copies: what = 1 moves every FREE after all other ops
+ * (every tensor stays on the device to the end; results unchanged).
+ * Errors: LQC_ERR_STATE (not scheduled), LQC_ERR_ARG (other `what`, or a
+ * budgeted plan). */
+int lqc_test_tamper_plan(lqc_dag* dag, int what);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // C ABI: DAG construction with merging of identical requests (Sec. II-B),
 // scheduling + planning, and the thin wrappers around the executor.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -84,7 +85,49 @@ constexpr int64_t kMaxSliceElems = (int64_t)1 << 40;
 constexpr int64_t kMaxTensorElems = (int64_t)1 << 58;
 constexpr int64_t kMaxLt = ((int64_t)1 << 31) - 1;
 
+namespace lqc {
+namespace {
+// per site: successful calls still to pass before the armed failure (-1 = none)
+std::atomic<int64_t> g_inject_skip[INJ_SITES] = {{-1}, {-1}, {-1}};
+}  // namespace
+
+bool inject_fail(int site) {
+  std::atomic<int64_t>& k = g_inject_skip[site];
+  int64_t v = k.load();
+  while (v >= 0) {
+    if (k.compare_exchange_weak(v, v - 1)) return v == 0;  // 0 -> -1: this call fails
+  }
+  return false;
+}
+}  // namespace lqc
+
 extern "C" {
+
+int lqc_test_inject_failure(int site, int64_t skip_calls) {
+  if (site == -1) {
+    for (auto& k : lqc::g_inject_skip) k.store(-1);
+    return LQC_OK;
+  }
+  if (site < 0 || site >= lqc::INJ_SITES || skip_calls < 0) return LQC_ERR_ARG;
+  lqc::g_inject_skip[site].store(skip_calls);
+  return LQC_OK;
+}
+
+int lqc_test_tamper_plan(lqc_dag* h, int what) {
+  if (!h) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  Dag& g = h->d;
+  if (!g.scheduled) return fail(h, LQC_ERR_STATE, "tamper before schedule");
+  if (what != 1) return fail(h, LQC_ERR_ARG, "unknown plan change");
+  // every FREE after all other ops, in their order: tensors stay resident to
+  // the end (valid without a budget), the planned figures are kept
+  if (g.budget != 0) return fail(h, LQC_ERR_ARG, "plan change needs an unlimited budget");
+  std::stable_partition(g.ops.begin(), g.ops.end(),
+                        [](const lqc::Op& op) { return op.kind != lqc::OP_FREE; });
+  lqc::exec_invalidate_plan(g);
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
 
 int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
   if (!out || lt < 1 || lt > kMaxLt) return LQC_ERR_ARG;

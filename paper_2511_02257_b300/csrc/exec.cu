@@ -125,6 +125,19 @@ struct ExecState {
 
 namespace {
 
+// the library's allocations and copies, each open to a test's injected failure
+cudaError_t dev_alloc(void** p, size_t n) {
+  return inject_fail(INJ_DEVICE_ALLOC) ? cudaErrorMemoryAllocation : cudaMalloc(p, n);
+}
+cudaError_t pinned_alloc(void** p, size_t n) {
+  return inject_fail(INJ_PINNED_ALLOC) ? cudaErrorMemoryAllocation
+                                       : cudaHostAlloc(p, n, cudaHostAllocDefault);
+}
+cudaError_t copy_async(void* dst, const void* src, size_t n, cudaMemcpyKind kind,
+                       cudaStream_t s) {
+  return inject_fail(INJ_COPY) ? cudaErrorInvalidValue : cudaMemcpyAsync(dst, src, n, kind, s);
+}
+
 int cuda_fail(Dag& g, cudaError_t e, const char* what) {
   g.err = std::string(what) + ": " + cudaGetErrorString(e);
   return LQC_ERR_CUDA;
@@ -583,14 +596,14 @@ int build_program(Dag& g) {
     }
   }
   x.arena_bytes = pl.top;
-  if (x.arena_bytes > 0) CK(cudaMalloc((void**)&x.arena, (size_t)x.arena_bytes), "arena cudaMalloc");
+  if (x.arena_bytes > 0) CK(dev_alloc((void**)&x.arena, (size_t)x.arena_bytes), "arena cudaMalloc");
   if (x.n_results > 0)
-    CK(cudaMalloc((void**)&x.results, (size_t)(x.n_result_vals * 16)), "results cudaMalloc");
+    CK(dev_alloc((void**)&x.results, (size_t)(x.n_result_vals * 16)), "results cudaMalloc");
   x.scratch_bytes = scratch_need;
-  if (scratch_need > 0) CK(cudaMalloc((void**)&x.scratch, (size_t)scratch_need), "scratch cudaMalloc");
+  if (scratch_need > 0) CK(dev_alloc((void**)&x.scratch, (size_t)scratch_need), "scratch cudaMalloc");
   x.mscratch_bytes = mscratch_need;
   if (mscratch_need > 0)
-    CK(cudaMalloc((void**)&x.mscratch, (size_t)mscratch_need), "plane scratch cudaMalloc");
+    CK(dev_alloc((void**)&x.mscratch, (size_t)mscratch_need), "plane scratch cudaMalloc");
   // window levels: scratch sized by the largest level, task tables built with
   // the final device addresses
   for (const WinRec& r : x.wins)
@@ -600,7 +613,7 @@ int build_program(Dag& g) {
       x.wscratch_bytes = std::max(x.wscratch_bytes, sum);
     }
   if (x.wscratch_bytes > 0)
-    CK(cudaMalloc((void**)&x.wscratch, (size_t)x.wscratch_bytes), "window scratch cudaMalloc");
+    CK(dev_alloc((void**)&x.wscratch, (size_t)x.wscratch_bytes), "window scratch cudaMalloc");
   if (!x.wins.empty()) {
     std::vector<char> tbuf;
     auto operand = [&](const Instr& in, int k) -> const float* {
@@ -634,7 +647,7 @@ int build_program(Dag& g) {
         }
       }
     }
-    CK(cudaMalloc((void**)&x.taskbuf, tbuf.size() + 64), "task table cudaMalloc");
+    CK(dev_alloc((void**)&x.taskbuf, tbuf.size() + 64), "task table cudaMalloc");
     CK(cudaMemcpy(x.taskbuf, tbuf.data(), tbuf.size(), cudaMemcpyHostToDevice), "task tables");
     for (WinRec& r : x.wins)
       for (LevelDev& d : r.ldev) rebase_level(&d, x.taskbuf);
@@ -668,7 +681,7 @@ int build_program(Dag& g) {
   }
   x.host_arena_bytes = hpl.top;
   if (hpl.top > 0)
-    CK(cudaHostAlloc((void**)&x.host_arena, (size_t)hpl.top, cudaHostAllocDefault),
+    CK(pinned_alloc((void**)&x.host_arena, (size_t)hpl.top),
        "pinned write-back arena");
   x.prog_valid = true;
   x.tset = 0;
@@ -727,7 +740,7 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
     switch (in.kind) {
       case I_LOAD: {
         const void* src = n.is_leaf() ? n.host : (const void*)(x.host_arena + in.src[0]);
-        CK(cudaMemcpyAsync(x.arena + in.dst, src, (size_t)in.bytes, cudaMemcpyHostToDevice, s),
+        CK(copy_async(x.arena + in.dst, src, (size_t)in.bytes, cudaMemcpyHostToDevice, s),
            "H2D load");
         x.copy_h2d += in.bytes;
         c.n_h2d++;
@@ -735,7 +748,7 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
         break;
       }
       case I_WRITEBACK: {
-        CK(cudaMemcpyAsync(x.host_arena + in.dst, x.arena + in.src[0], (size_t)in.bytes,
+        CK(copy_async(x.host_arena + in.dst, x.arena + in.src[0], (size_t)in.bytes,
                            cudaMemcpyDeviceToHost, s),
            "D2H write-back");
         x.copy_d2h += in.bytes;
@@ -821,7 +834,7 @@ int host_store_alloc(Dag& g, int64_t leaf, std::string* err) {
   if (n.host) return LQC_OK;
   const size_t bytes = (size_t)(n.lt * n.elems * g.elem_bytes);
   void* p = nullptr;
-  if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) == cudaSuccess) {
+  if (pinned_alloc(&p, bytes) == cudaSuccess) {
     n.host = p;
     n.host_pinned = true;
     return LQC_OK;
@@ -973,6 +986,12 @@ int ensure_graph(Dag& g, cudaStream_t cs) {
   }
   CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = issue(g, cap, true);
+  if (rc != LQC_OK) {  // an issue that stopped early: join the forked side streams
+    for (int k = 1; k < 3; ++k) {  // so that the capture ends on every stream
+      cudaEventRecord(x.start_ev, x.side[k]);
+      cudaStreamWaitEvent(cap, x.start_ev, 0);
+    }
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cap, &graph);
   if (rc != LQC_OK) {
@@ -1174,8 +1193,8 @@ int exec_stage_leaves(Dag& g, void* stream) {
       return LQC_ERR_STATE;
     }
     size_t bytes = (size_t)g.size_bytes(u);
-    CK(cudaMalloc(&x.staged[u], bytes), "staged leaf cudaMalloc");
-    CK(cudaMemcpyAsync(x.staged[u], n.host, bytes, cudaMemcpyHostToDevice, s), "stage leaf");
+    CK(dev_alloc(&x.staged[u], bytes), "staged leaf cudaMalloc");
+    CK(copy_async(x.staged[u], n.host, bytes, cudaMemcpyHostToDevice, s), "stage leaf");
   }
   CK(cudaStreamSynchronize(s), "stage sync");
   x.staged_valid = true;

@@ -93,6 +93,12 @@ bool plan_replay(const Dag& g, const std::vector<int64_t>& order, uint64_t budge
                  lqc_evict evict, std::vector<Op>* ops, lqc_stats* st, std::string* err);
 int64_t model_peak(const Dag& g, const std::vector<int64_t>& order);
 
+// ---- failure injection for tests (api.cpp): the library's host-side CUDA
+// allocations and copies ask this before the real call; true = behave as if
+// the call had failed (one armed failure is consumed) ----
+enum InjectSite { INJ_DEVICE_ALLOC = 0, INJ_PINNED_ALLOC = 1, INJ_COPY = 2, INJ_SITES = 3 };
+bool inject_fail(int site);
+
 // ---- executor (exec.cu) ----
 int exec_run(Dag& g, void* stream);
 int exec_prepare(Dag& g, void* stream);

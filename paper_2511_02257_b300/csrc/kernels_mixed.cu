@@ -91,14 +91,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// bounded wait: false after kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: false after limit_ns (kWaitNs in every kernel but the
+// wait probe below)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity)) {
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
+}
+
+// Test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives on, for limit_ns; the expiry takes the GEMM's path (the device
+// error word) and the kernel returns.
+__global__ void k_wait_probe(unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, limit_ns)) atomicCAS(&g_mixed_error, 0, 1);
+  }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int c0, int c1, int c2) {
@@ -1962,5 +1976,17 @@ int64_t lqc_contract_all_c64_scratch_bytes(int rank_a, const int64_t* ext_a, int
 }
 
 int lqc_mixed_error(int reset) { return lqc::mixed_error_status(reset != 0); }
+
+int lqc_test_expire_wait(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1 || limit_ns > 1000000000) return LQC_ERR_ARG;
+  lqc::clear_pending_error();
+  if (lqc::mixed_error_status(true) < 0) return LQC_ERR_CUDA;  // start from a clear word
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lqc::k_wait_probe<<<1, 32, 0, s>>>((unsigned long long)limit_ns);
+  if (cudaGetLastError() != cudaSuccess) return LQC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LQC_ERR_CUDA;
+  const int st = lqc::mixed_error_status(true);
+  return st < 0 ? LQC_ERR_CUDA : (st ? LQC_ERR_TIMEOUT : LQC_OK);
+}
 
 }  // extern "C"

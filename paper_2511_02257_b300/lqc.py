@@ -106,6 +106,9 @@ _sig("lqc_dag_stage_leaves", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_unstage_leaves", ctypes.c_int, [c_vp])
 _sig("lqc_dag_execute", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_dag_prepare", ctypes.c_int, [c_vp, c_vp])
+_sig("lqc_test_inject_failure", ctypes.c_int, [ctypes.c_int, c_i64])
+_sig("lqc_test_expire_wait", ctypes.c_int, [c_i64, c_vp])
+_sig("lqc_test_tamper_plan", ctypes.c_int, [c_vp, ctypes.c_int])
 _sig("lqc_dag_wait", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_autotune", ctypes.c_int, [c_vp, c_vp, ctypes.c_int, ctypes.POINTER(lqc_tune_entry),
                                         c_i64, P_i64])
@@ -149,7 +152,9 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_ad
            "lqc_dag_get_kernel_times",
            "lqc_contract_fp64", "lqc_contract_all_fp64", "lqc_contract_all_scratch_bytes",
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
-           "lqc_contract_all_c64", "lqc_mixed_error", "lqc_contract_all_c64_scratch_bytes"):
+           "lqc_contract_all_c64", "lqc_mixed_error", "lqc_contract_all_c64_scratch_bytes",
+           "lqc_dag_prepare", "lqc_test_inject_failure", "lqc_test_expire_wait",
+           "lqc_test_tamper_plan"):
     globals()[_n] = getattr(_lib, _n)
 
 

@@ -9,13 +9,13 @@ leaves starting in pinned host memory.  Correlators of all policies are
 compared bit for bit (each node's arithmetic is fixed; an eviction is a
 copy), so a schedule can change the time but never a result.
 
-  python -m paper_2511_02257_b300.experiments [--workload memory_pressure]
+  python experiments.py [--workload memory_pressure]
          [--precision tf32x3] [--evict lru] [--steps 2] [--budget-gib 24[,8]] [--paths]
 
 Prints one JSON line per policy, then a summary line with ratios to the
 naive order.
 
-  python -m paper_2511_02257_b300.experiments kernel --shape pxp --n 64 --lt 64
+  python experiments.py kernel --shape pxp --n 64 --lt 64
          [--precision tf32x3|bf16x3|fp64] [--reps 20] [--fused-max-n F]
 
 times one contraction shape through the single-contraction C ABI, or, with
@@ -23,7 +23,7 @@ times one contraction shape through the single-contraction C ABI, or, with
 executor's options set; F = 0 forces the plane form, a large F the fused
 form of TF32X3).
 
-  python -m paper_2511_02257_b300.experiments batched [--workload batched|baryon|...]
+  python experiments.py batched [--workload batched|baryon|...]
          [--steps 2] [--window 64]
 
 runs a workload (default: the batched one, 50 independent DAGs of uneven N
@@ -33,7 +33,7 @@ FP64, with the leaves resident on the device and from pinned host memory;
 reports times, speedups and the TF32x3 error of every correlator against
 the FP64 path (whose parity with the oracle the test suite establishes).
 
-  python -m paper_2511_02257_b300.experiments paths [--workloads multi_meson,...]
+  python experiments.py paths [--workloads multi_meson,...]
          [--gpu] [--steps 3]
 
 builds each workload's terms twice -- as the generator brackets them and by
@@ -41,17 +41,17 @@ contraction-path selection (Sec. II-A) -- and reports distinct
 contractions, flops and every scheduler's peak; with --gpu also both DAGs'
 tuned TF32x3 time-to-solution and the largest difference of a term's value.
 
-  python -m paper_2511_02257_b300.experiments sched [--dags multi_meson:5000,...] [--reps 5]
+  python experiments.py sched [--dags multi_meson:5000,...] [--reps 5]
 
 times each scheduler's order on the host for synthetic DAGs of the vertex
 counts of the paper's Table 2, with their trees, vertices, edges, F_v, F_e.
 
-  python -m paper_2511_02257_b300.experiments optimal [--dags 200] [--max-contr 9]
+  python experiments.py optimal [--dags 200] [--max-contr 9]
 
 scores every scheduler's model peak against the optimal peak over all
 contraction orders of small synthetic DAGs (exhaustive enumeration).
 
-  python -m paper_2511_02257_b300.experiments model [--workloads ...] [--fractions 1,0.5,0.25]
+  python experiments.py model [--workloads ...] [--fractions 1,0.5,0.25]
 
 gives the memory model's peak, evictions and transfer bytes of every
 scheduler's plan at budgets relative to the tree order's peak, without
@@ -68,7 +68,7 @@ import time
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 SHAPES = {
@@ -97,6 +97,9 @@ def kernel_bench(argv):
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--fused-max-n", type=int, default=None)
+    ap.add_argument("--fused-kernel", type=int, default=1,
+                    help="with --fused-max-n: LQC_OPT_FUSED_KERNEL (0: A in shared memory, "
+                         "1: A in tensor memory)")
     args = ap.parse_args(argv)
     sa, sb, la, ra = SHAPES[args.shape](args.n)
     lt = args.lt
@@ -170,6 +173,7 @@ def kernel_bench_dag(args, sa, sb, la, ra):
     stream = torch.cuda.current_stream().cuda_stream
     d.set_option(L.LQC_OPT_WINDOW, 0)
     d.set_option(L.LQC_OPT_FUSED_MAX_N, args.fused_max_n)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, args.fused_kernel)
     d.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
     d.stage_leaves(stream)
     for _ in range(3):
@@ -186,9 +190,16 @@ def kernel_bench_dag(args, sa, sb, la, ra):
     M = int(np.prod(sa)) // K
     N = int(np.prod(sb)) // K
     flops = 8.0 * lt * M * N * K
+    from paper_2511_02257_b300.roofline import measured_peaks, precision_peak
+    eb, prod, peak, _, _ = precision_peak(args.precision)
+    bound_ms = 1e3 * max(prod * flops / (peak * 1e12),
+                         lt * (M * K + K * N + M * N) * eb / (measured_peaks()[0]["hbm_gbs"] * 1e9))
     print(json.dumps({"shape": args.shape, "n": args.n, "lt": lt, "M": M, "N": N, "K": K,
                       "precision": args.precision, "fused_max_n": args.fused_max_n,
+                      "fused_kernel": args.fused_kernel,
                       "ms_per_contraction": ms, "complex_tflops": flops / ms / 1e9,
+                      "tensor_tflops": prod * flops / ms / 1e9, "roofline_ms": bound_ms,
+                      "roofline_frac": bound_ms / ms,
                       "kernels": d.exec_info()["n_kernels"]}), flush=True)
 
 

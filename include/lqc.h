@@ -147,6 +147,11 @@ typedef struct {
    * windows taking effect at the window's end; the op-level figure with
    * frees at their op is lqc_stats.peak_exec of lqc_dag_get_stats          */
   int64_t resident_peak_bytes;
+  /* moves the executor adds to keep arena_bytes within the budget when the
+   * freed ranges of the arena are too fragmented for a tensor: tensors
+   * moved to the host (written back first when they had no host copy) and
+   * loaded again before their next use; not part of lqc_stats            */
+  int64_t extra_evictions, extra_h2d_bytes, extra_d2h_bytes;
 } lqc_exec_info;
 
 /* Option keys for lqc_dag_set_option. */
@@ -171,10 +176,18 @@ typedef enum {
                              read as raw complex64 and split inside the GEMM;
                              wider ones are split into hi/lo planes first.
                              Default 64; 0 = never fused                    */
-  LQC_OPT_SPLIT_POLICY = 6 /* mixed GEMM k splits: 0 (default) while the
+  LQC_OPT_SPLIT_POLICY = 6, /* mixed GEMM k splits: 0 (default) while the
                              output tiles cannot fill the GPU and for the
                              FP32 chunk bound (1024 real k), 1 for the chunk
                              bound only                                     */
+  LQC_OPT_FUSED_KERNEL = 7 /* TF32X3 fused form: 1 (default) = converter
+                             warps write A's hi/lo parts into tensor memory
+                             and the MMAs read A there, B from shared memory
+                             (correction products first into a fresh
+                             accumulator, drained every 128-byte k block);
+                             0 = both operands staged in shared memory, main
+                             and correction accumulators apart, drained every
+                             two k blocks                                    */
 } lqc_option;
 
 /* One autotuner candidate and its measured time per execute. */

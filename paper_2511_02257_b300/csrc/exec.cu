@@ -52,6 +52,7 @@ struct Instr {
   int32_t root_slot = -1;
   int32_t win = -1;    // I_WINDOW: index of its window record
   bool member = false; // issued through its window, not on its own
+  bool extra = false;  // LOAD / WRITEBACK made by placement within the budget, not by the plan
 };
 
 // A grouped window: up to W consecutive contractions of the plan whose frees
@@ -119,6 +120,8 @@ struct ExecState {
   std::vector<int64_t> kev_flops;
   // figures of the executor's own walk of the op list
   int64_t walk_evict = 0, walk_peak = 0, resident_peak = 0;
+  // moves made to keep the arena within the budget (not the plan's)
+  int64_t extra_evict = 0, extra_h2d = 0, extra_d2h = 0;
   bool timing_pending[2] = {false, false};
   int tset = 0;
 };
@@ -264,6 +267,8 @@ int build_program(Dag& g) {
   std::vector<uint8_t> holds(N, 0);
   int64_t held = 0, res = 0;
   x.walk_evict = x.walk_peak = x.resident_peak = 0;
+  x.extra_evict = x.extra_h2d = x.extra_d2h = 0;
+  std::map<int64_t, int64_t> live_at;        // arena offset -> resident node
   auto take_bytes = [&](int64_t u) {
     if (!holds[u]) { holds[u] = 1; held += g.size_bytes(u); }
   };
@@ -279,6 +284,7 @@ int build_program(Dag& g) {
   auto release = [&](int64_t u) {
     drop_bytes(u);
     if (off[u] < 0) return;
+    if (leaf_slot[u] < 0) live_at.erase(off[u]);
     int32_t dep[3] = {last_compute[u], last_h2d[u], last_d2h[u]};
     if (g.opt_poison) {
       Instr in{};
@@ -346,64 +352,151 @@ int build_program(Dag& g) {
     for (int64_t u : win_free) release(u);
     win_free.clear();
   };
+  // ---- placement within the budget.  The arena may not grow past the
+  // budget: when a tensor's bytes fit nowhere below it (the freed ranges are
+  // fragmented), live tensors the current contraction does not read move to
+  // the host (written back when they have no host copy yet) and are loaded
+  // again before their next use.  These moves are not the plan's: they are
+  // reported apart (extra_*), so the counted figures stay the plan's.
+  const int64_t limit = g.budget > 0 ? (int64_t)std::min<uint64_t>(g.budget, INT64_MAX) : 0;
+  std::vector<uint8_t> out_of_place(N, 0);  // moved out by placement: load before its next use
+  auto fits = [&](int64_t bytes) {
+    const int64_t b = Placer::rounded(bytes);
+    if (pl.by_size.lower_bound({b, INT64_MIN}) != pl.by_size.end()) return true;
+    int64_t start = pl.top;
+    if (!pl.free_.empty()) {
+      auto last = std::prev(pl.free_.end());
+      if (last->first + last->second.size == pl.top) start = last->first;
+    }
+    return start + b <= limit;
+  };
+  // the resident tensor (not p0 / p1, not in the leaf region) whose release
+  // opens the largest free range below the limit
+  auto pick_victim = [&](int64_t p0, int64_t p1) -> int64_t {
+    int64_t best = -1, best_hole = -1;
+    for (const auto& kv : live_at) {
+      const int64_t v = kv.second;
+      if (v == p0 || v == p1) continue;
+      const int64_t o = kv.first, e = o + Placer::rounded(g.size_bytes(v));
+      int64_t lo = o, hi = e;
+      auto nx = pl.free_.find(e);
+      if (nx != pl.free_.end()) hi = e + nx->second.size;
+      auto pv = pl.free_.lower_bound(o);
+      if (pv != pl.free_.begin()) {
+        --pv;
+        if (pv->first + pv->second.size == o) lo = pv->first;
+      }
+      if (hi == pl.top) hi = limit;
+      if (hi - lo > best_hole) {
+        best_hole = hi - lo;
+        best = v;
+      }
+    }
+    return best;
+  };
+  auto emit_writeback = [&](int64_t u, bool extra) {
+    Instr in{};
+    in.kind = I_WRITEBACK;
+    in.stream = S_D2H;
+    in.node = u;
+    in.bytes = g.size_bytes(u);
+    in.src[0] = off[u];
+    in.src[1] = -1;
+    in.extra = extra;
+    int32_t hdep[3];
+    in.dst = hpl.alloc(in.bytes, hdep);  // host offset
+    hoff[u] = in.dst;
+    add_wait(in, writer[u]);
+    add_wait(in, hdep[S_H2D]);  // the previous owner's reloads have read these bytes
+    P.push_back(in);
+    x.cdesc.emplace_back();
+    x.adesc.emplace_back();
+    x.mdesc.emplace_back();
+    last_d2h[u] = (int32_t)P.size() - 1;
+    wb_instr[u] = last_d2h[u];
+    if (extra) x.extra_d2h += in.bytes;
+  };
+  auto place = [&](int64_t u, int64_t bytes, int64_t p0, int64_t p1, int32_t dep[3]) {
+    if (limit > 0 && !fits(bytes)) {
+      flush();  // a window's members are issued before anything of theirs moves
+      while (!fits(bytes)) {
+        const int64_t v = pick_victim(p0, p1);
+        if (v < 0) break;  // only this contraction's tensors left: the arena grows
+        if (!g.nodes[v].is_leaf() && hoff[v] < 0) emit_writeback(v, true);
+        release(v);
+        out_of_place[v] = 1;
+        ++x.extra_evict;
+      }
+    }
+    const int64_t o = pl.alloc(bytes, dep);
+    live_at[o] = u;
+    return o;
+  };
+  // H2D load of u (a leaf on first use, or a reload of a written-back tensor)
+  auto emit_load = [&](int64_t u, bool extra, int64_t p0, int64_t p1) {
+    const Node& nu = g.nodes[u];
+    Instr in{};
+    in.kind = I_LOAD;
+    in.stream = S_H2D;
+    in.node = u;
+    in.bytes = g.size_bytes(u);
+    in.src[0] = in.src[1] = -1;
+    in.extra = extra;
+    int32_t dep[3];
+    if (leaf_slot[u] >= 0) {
+      in.dst = leaf_slot[u];  // own bytes: nothing to wait for
+    } else {
+      in.dst = place(u, in.bytes, p0, p1, dep);
+      add_wait(in, dep[S_COMPUTE]);
+      add_wait(in, dep[S_D2H]);
+    }
+    if (!nu.is_leaf()) {
+      add_wait(in, wb_instr[u]);  // reload after the write-back landed
+      in.src[0] = hoff[u];        // host offset of the copy
+    }
+    off[u] = in.dst;
+    P.push_back(in);
+    x.cdesc.emplace_back();
+    x.adesc.emplace_back();
+    x.mdesc.emplace_back();
+    last_h2d[u] = (int32_t)P.size() - 1;
+    last_compute[u] = -1;
+    last_d2h[u] = -1;
+    writer[u] = -1;
+    waited_for_load[u] = 0;
+    take_bytes(u);
+    if (extra) x.extra_h2d += in.bytes;
+  };
+  // the contraction each op serves (a LOAD's operands are protected)
+  std::vector<int64_t> serves(g.ops.size(), -1);
+  for (int64_t k = (int64_t)g.ops.size() - 1, nxt = -1; k >= 0; --k) {
+    if (g.ops[k].kind == OP_CONTRACT) nxt = g.ops[k].node;
+    serves[k] = nxt;
+  }
+  int64_t opi = -1;
   for (const Op& op : g.ops) {
+    ++opi;
     const int64_t u = op.node;
     const Node& n = g.nodes[u];
     if (op.kind == OP_LOAD) {
       take_bytes(u);
       res += g.size_bytes(u);
       if (staged && n.is_leaf()) continue;  // leaves already on the device
-      Instr in{};
-      in.kind = I_LOAD;
-      in.stream = S_H2D;
-      in.node = u;
-      in.bytes = g.size_bytes(u);
-      in.src[0] = in.src[1] = -1;
-      int32_t dep[3];
-      if (leaf_slot[u] >= 0) {
-        in.dst = leaf_slot[u];  // own bytes: nothing to wait for
-      } else {
-        in.dst = pl.alloc(in.bytes, dep);
-        add_wait(in, dep[S_COMPUTE]);
-        add_wait(in, dep[S_D2H]);
-      }
-      if (!n.is_leaf()) {
-        add_wait(in, wb_instr[u]);  // reload after the write-back landed
-        in.src[0] = hoff[u];        // host offset of the copy
-      }
-      off[u] = in.dst;
-      P.push_back(in);
-      x.cdesc.emplace_back();
-      x.adesc.emplace_back();
-      x.mdesc.emplace_back();
-      last_h2d[u] = (int32_t)P.size() - 1;
-      last_compute[u] = -1;
-      last_d2h[u] = -1;
-      writer[u] = -1;
-      waited_for_load[u] = 0;
+      const int64_t c = serves[opi];
+      emit_load(u, false, c >= 0 ? g.nodes[c].left : -1, c >= 0 ? g.nodes[c].right : -1);
     } else if (op.kind == OP_EVICT) {
       ++x.walk_evict;
       res -= g.size_bytes(u);
       if (op.flag) {
-        Instr in{};
-        in.kind = I_WRITEBACK;
-        in.stream = S_D2H;
-        in.node = u;
-        in.bytes = g.size_bytes(u);
-        in.src[0] = off[u];
-        in.src[1] = -1;
-        int32_t hdep[3];
-        in.dst = hpl.alloc(in.bytes, hdep);  // host offset
-        hoff[u] = in.dst;
-        add_wait(in, writer[u]);
-        add_wait(in, hdep[S_H2D]);  // the previous owner's reloads have read these bytes
-        P.push_back(in);
-        x.cdesc.emplace_back();
-        x.adesc.emplace_back();
-        x.mdesc.emplace_back();
-        last_d2h[u] = (int32_t)P.size() - 1;
-        wb_instr[u] = last_d2h[u];
+        if (wb_instr[u] >= 0 && hoff[u] >= 0 && P[wb_instr[u]].extra) {
+          // placement wrote it back already: that copy is the plan's write-back
+          P[wb_instr[u]].extra = false;
+          x.extra_d2h -= g.size_bytes(u);
+        } else {
+          emit_writeback(u, false);
+        }
       }
+      out_of_place[u] = 0;  // off the device in the plan too: the plan reloads it
       release(u);
     } else if (op.kind == OP_FREE && W > 0 && !win.empty()) {
       res -= g.size_bytes(u);
@@ -424,6 +517,14 @@ int build_program(Dag& g) {
            (g.budget > 0 && n.rank != 0 &&
             pl.top + ((g.size_bytes(u) + 255) & ~int64_t(255)) > (int64_t)g.budget)))
         flush();
+      // operands that placement moved out come back first
+      for (int k = 0; k < n.n_children(); ++k) {
+        const int64_t c = n.child(k);
+        if (out_of_place[c]) {
+          emit_load(c, true, n.left, n.right);
+          out_of_place[c] = 0;
+        }
+      }
       Instr in{};
       in.stream = S_COMPUTE;
       in.node = u;
@@ -466,7 +567,7 @@ int build_program(Dag& g) {
           return LQC_ERR_ARG;
         }
         int32_t dep[3];
-        in.dst = pl.alloc(in.bytes, dep);
+        in.dst = place(u, in.bytes, n.left, n.right, dep);
         add_wait(in, dep[S_H2D]);
         add_wait(in, dep[S_D2H]);
         off[u] = in.dst;
@@ -476,6 +577,7 @@ int build_program(Dag& g) {
         MixedTune tune;
         tune.fused_max_n = g.opt_fused_max_n;
         tune.split_policy = (int)g.opt_split_policy;
+        tune.fused_kernel = (int)g.opt_fused_kernel;
         if (!make_mixed_desc(cd, g.prec == LQC_PREC_BF16X3, &md, tune)) {
           g.err = "contraction too large for the mixed-precision kernels";
           return LQC_ERR_ARG;
@@ -743,8 +845,10 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
         CK(copy_async(x.arena + in.dst, src, (size_t)in.bytes, cudaMemcpyHostToDevice, s),
            "H2D load");
         x.copy_h2d += in.bytes;
-        c.n_h2d++;
-        c.h2d_bytes += in.bytes;
+        if (!in.extra) {  // the plan's loads (placement's are reported apart)
+          c.n_h2d++;
+          c.h2d_bytes += in.bytes;
+        }
         break;
       }
       case I_WRITEBACK: {
@@ -752,8 +856,10 @@ int issue(Dag& g, cudaStream_t cs, bool capturing) {
                            cudaMemcpyDeviceToHost, s),
            "D2H write-back");
         x.copy_d2h += in.bytes;
-        c.n_d2h++;
-        c.d2h_bytes += in.bytes;
+        if (!in.extra) {
+          c.n_d2h++;
+          c.d2h_bytes += in.bytes;
+        }
         break;
       }
       case I_POISON: {
@@ -1067,6 +1173,9 @@ int exec_run(Dag& g, void* stream) {
   g.info.copied_d2h = x.copy_d2h;
   g.info.n_ops = (int64_t)g.ops.size();
   g.info.resident_peak_bytes = x.resident_peak;
+  g.info.extra_evictions = x.extra_evict;
+  g.info.extra_h2d_bytes = x.extra_h2d;
+  g.info.extra_d2h_bytes = x.extra_d2h;
   g.executed = true;
   return LQC_OK;
 }

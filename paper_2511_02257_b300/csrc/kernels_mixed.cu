@@ -238,6 +238,12 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   int b_nk, b_no;       // 2: k axes in the map (innermost first), outer n axis present
   int b_kext[3];        // 2: extents of the k axes, innermost first
   long long tile_start;
+  // fused form, A read by the converters themselves (A in tensor memory):
+  // complex64 rows [lt][M][kc] with row stride a_rs and slice stride a_ts
+  // (complex elements, both even), 16-byte aligned
+  const float2* a_raw;
+  long long a_ts, a_rs;
+  int kc;
 };
 
 struct GemmParams {
@@ -671,6 +677,444 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols));
+}
+
+// ------------------------------------------------------------ K4t: A in TMEM
+// Fused TF32 split-3 GEMM whose A operand never passes through shared
+// memory.  Four A-converter warps (one per TMEM lane quarter, one A' row per
+// thread) load the raw complex64 row segment of a k-block from global memory
+// one k-block ahead, split it into hi/lo and write both into tensor memory
+// with tcgen05.st; tcgen05.mma reads A from there and only B' from shared
+// memory.  B arrives as raw complex64 tiles by TMA (the maps of the fused
+// form) and two B-converter warps build its hi/lo B' tiles.  Per k-block the
+// MMA thread issues the two correction products (lo*hi, hi*lo) first, into a
+// fresh accumulator, then hi*hi, and the drain warps add the finished
+// accumulator into FP32 registers: four accumulations at full magnitude per
+// drain.  Shared-memory traffic per k-block: raw B written and read (16 KB),
+// B' hi/lo written (32 KB), B' read by the MMAs (48 KB) -- against 208 KB
+// when A is staged in shared memory too.
+struct TaCfg {
+  static constexpr int kStages = 4;                 // raw B ring = B' operand ring
+  static constexpr int kBTile = kBN * 128;          // one B' plane tile: kBN rows x 128 B
+  static constexpr int kBStage = 2 * kBTile;        // hi + lo
+  static constexpr int kRawB = (kBN / 2) * 128;     // raw complex64 B tile
+  static constexpr int kAConv = 4, kBConv = 2;      // converter warps
+  static constexpr int kThreads = 64 + 32 * (kDrainWarps + kAConv + kBConv);
+  static constexpr int kStgPitch = 20;
+  static constexpr int kStgBytes = kDrainWarps * 32 * kStgPitch * 4;
+  static constexpr int kSmem = kStages * (kBStage + kRawB) + 1024 + 256 + kStgBytes;
+  static constexpr int kACol = 2 * kBN;             // TMEM: [0, 2 kBN) accumulators, then A
+  static constexpr int kTmemCols = 512;
+};
+static_assert(TaCfg::kACol + 2 * 64 <= TaCfg::kTmemCols, "A stages must fit in TMEM");
+static_assert(TaCfg::kThreads == 512, "warp roles: 2 + 8 drain + 4 A + 2 B converters");
+
+__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                        uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+// raw A row segment (16 complex = 8 float4) of k-block i of a tile for row r
+// of the tile; zero beyond the matrix
+__device__ __forceinline__ void a_row_load(const GemmTask* tk, int local, int i, int r,
+                                           float4 (&v)[8]) {
+  const int tm = (local / tk->ntn) % tk->ntm;
+  const int z = local / (tk->ntn * tk->ntm);
+  const int t = z % tk->lt, split = z / tk->lt;
+  const int m = tm * kBM + r;
+  const int kc0 = (split * tk->kblocks + i) * 16;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool row_ok = m < tk->M;
+  const float4* p = reinterpret_cast<const float4*>(
+      tk->a_raw + (long long)t * tk->a_ts + (long long)(row_ok ? m : 0) * tk->a_rs + kc0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = (row_ok && kc0 + 2 * c < tk->kc) ? __ldg(p + c) : zero;
+}
+
+__global__ void __launch_bounds__(TaCfg::kThreads, 1)
+k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
+  using C = TaCfg;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* raw = smem + S * C::kBStage;  // raw complex64 B ring
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(raw + S * C::kRawB);  // [S] B' stage built
+  uint64_t* bempty = bfull + S;        // [S] B' stage read by its MMAs
+  uint64_t* rfull = bempty + S;        // [S] raw B landed
+  uint64_t* rempty = rfull + S;        // [S] raw B converted
+  uint64_t* afull = rempty + S;        // [2] A stage written to TMEM
+  uint64_t* aempty = afull + 2;        // [2] A stage read by its MMAs
+  uint64_t* tfull = aempty + 2;        // [2] accumulator ready to drain
+  uint64_t* tempty = tfull + 2;        // [2] accumulator drained
+  uint64_t* done = tempty + 2;         // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* stage_out = reinterpret_cast<float*>(raw + S * C::kRawB + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kAWarp0 = 2 + kDrainWarps, kBWarp0 = kAWarp0 + C::kAConv;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&bfull[i], C::kBConv);
+      mbar_init(&bempty[i], 1);
+      mbar_init(&rfull[i], 1);
+      mbar_init(&rempty[i], C::kBConv);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], C::kAConv);
+      mbar_init(&aempty[b], 1);
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kDrainWarps);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer: raw B tiles
+      int g = 0, issued = 0, k = 0, local = 0;
+      bool stop = false;
+      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+        const GemmTask* tk = tile_task(gp, tile, k, local);
+        const int tn = local % tk->ntn;
+        const int z = local / (tk->ntn * tk->ntm);
+        const int t = z % tk->lt, split = z / tk->lt;
+        const int n0 = tn * kBN, kb0 = split * tk->kblocks;
+        for (int i = 0; i < tk->kblocks; ++i, ++g) {
+          const int st = g % S;
+          if (!mbar_wait(&rempty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          const int k0 = (kb0 + i) * 32;  // floats
+          uint8_t* rp = raw + st * C::kRawB;
+          mbar_expect_tx(&rfull[st], C::kRawB);
+          if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
+            int c[5], nd = 0, kk = k0 / 2;
+            c[nd++] = n0 % (2 * tk->b_ni);
+            for (int a = 0; a < tk->b_nk; ++a) {
+              c[nd++] = kk % tk->b_kext[a];
+              kk /= tk->b_kext[a];
+            }
+            if (tk->b_no) c[nd++] = n0 / (2 * tk->b_ni);
+            c[nd++] = t;
+            if (nd == 3) tma_load_3d(rp, &tk->map[2], &rfull[st], c[0], c[1], c[2]);
+            else if (nd == 4)
+              tma_load_4d(rp, &tk->map[2], &rfull[st], c[0], c[1], c[2], c[3]);
+            else
+              tma_load_5d(rp, &tk->map[2], &rfull[st], c[0], c[1], c[2], c[3], c[4]);
+          } else if (tk->b_mn) {  // [16 complex k rows][kBN/2 complex n], unswizzled
+            tma_load_3d(rp, &tk->map[2], &rfull[st], n0, k0 / 2, t);
+          } else {
+            tma_load_3d(rp, &tk->map[2], &rfull[st], k0, n0 / 2, t);
+          }
+          issued = g + 1;
+        }
+      }
+      // every issued load must have landed before the CTA exits
+      for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
+        if (!mbar_wait(&rfull[i % S], (uint32_t)(i / S) & 1u)) break;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: A from TMEM, B' from shared memory
+      constexpr uint32_t idesc = make_idesc<false>();
+      int g = 0, k = 0, local = 0;
+      bool stop = false;
+      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+        const GemmTask* tk = tile_task(gp, tile, k, local);
+        for (int i = 0; i < tk->kblocks; ++i, ++g) {
+          const int b = g & 1, st = g % S;
+          const uint32_t ph2 = (uint32_t)(g >> 1) & 1u;
+          if (!mbar_wait(&tempty[b], ph2 ^ 1u) || !mbar_wait(&afull[b], ph2) ||
+              !mbar_wait(&bfull[st], (uint32_t)(g / S) & 1u) || *abort_flag) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t bhi = smem_u32(smem + st * C::kBStage), blo = bhi + C::kBTile;
+          const uint32_t d = tmem + (uint32_t)(b * kBN);
+          const uint32_t ahi = tmem + (uint32_t)(C::kACol + b * 64), alo = ahi + 32;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)  // corrections first, into a fresh accumulator
+            umma_ta(d, alo + kk * 8, sdesc_sw128(bhi + kk * 32), idesc, kk > 0 ? 1u : 0u);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            umma_ta(d, ahi + kk * 8, sdesc_sw128(blo + kk * 32), idesc, 1u);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            umma_ta(d, ahi + kk * 8, sdesc_sw128(bhi + kk * 32), idesc, 1u);
+          umma_commit(&bempty[st]);
+          umma_commit(&aempty[b]);
+          umma_commit(&tfull[b]);
+        }
+      }
+      umma_commit(done);
+    }
+  } else if (warp < 2 + kDrainWarps) {
+    // ---- drain / epilogue warps: one accumulator per k-block
+    constexpr int kHalf = kBN / 2;
+    const int q = warp & 3;
+    const int c0 = ((warp - 2) >> 2) * kHalf;
+    const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+    int g = 0, ok = 1, k = 0, local = 0;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+      const GemmTask* tk = tile_task(gp, tile, k, local);
+      const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
+      const int z = local / (tk->ntn * tk->ntm);
+      const int t = z % tk->lt, split = z / tk->lt;
+      const int M = tk->M, Nr = tk->Nr;
+      float acc[kHalf];
+#pragma unroll
+      for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
+      for (int i = 0; i < tk->kblocks; ++i, ++g) {
+        const int b = g & 1;
+        if (lane == 0) {
+          if (!mbar_wait(&tfull[b], (uint32_t)(g >> 1) & 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tb = tmem + tlane + (uint32_t)(b * kBN);
+#pragma unroll
+        for (int j = 0; j < kHalf; j += 16) {
+          uint32_t r[16];
+          tmem_ld16(tb + j, r);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[j + u] += __uint_as_float(r[u]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (ok) {  // warp-uniform: the staging below is collective
+        float* stg = stage_out + (warp - 2) * (32 * C::kStgPitch);
+        float* base = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr;
+        const int row0 = tm * kBM + q * 32, col0 = tn * kBN + c0;
+        const bool vec = (Nr & 3) == 0;
+#pragma unroll
+        for (int j = 0; j < kHalf; j += 16) {
+          float4* w = reinterpret_cast<float4*>(stg + lane * C::kStgPitch);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            w[u] = make_float4(acc[j + 4 * u], acc[j + 4 * u + 1], acc[j + 4 * u + 2],
+                               acc[j + 4 * u + 3]);
+          __syncwarp();
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int rr = (lane >> 2) + 8 * p, cc = (lane & 3) * 4;
+            const float4 v = *reinterpret_cast<const float4*>(stg + rr * C::kStgPitch + cc);
+            const int orow = row0 + rr, col = col0 + j + cc;
+            if (orow < M) {
+              float* dst = base + (size_t)orow * Nr + col;
+              if (vec && col + 4 <= Nr) {
+                *reinterpret_cast<float4*>(dst) = v;
+              } else {
+                if (col < Nr) dst[0] = v.x;
+                if (col + 1 < Nr) dst[1] = v.y;
+                if (col + 2 < Nr) dst[2] = v.z;
+                if (col + 3 < Nr) dst[3] = v.w;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+  } else if (warp < kBWarp0) {
+    // ---- A converters: global complex64 rows -> hi/lo A' rows in TMEM
+    const int q = warp & 3, r = q * 32 + lane;  // this thread's row of the tile
+    const uint32_t ta0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)C::kACol;
+    int k = 0, local = 0, ok = 1, g = 0, i = 0;
+    long long tile = blockIdx.x;
+    const GemmTask* tk = tile < gp.total_tiles ? tile_task(gp, tile, k, local) : nullptr;
+    int nk = k, nlocal = local;  // look-ahead cursor of the next k-block
+    float4 cur[8], nxt[8];
+    if (tk) a_row_load(tk, local, 0, r, cur);
+    while (tk) {
+      // the next k-block (of this tile or the next one): its loads fly while
+      // this one is split and stored
+      int ni = i + 1;
+      long long ntile = tile;
+      const GemmTask* ntk = tk;
+      nlocal = local;
+      if (ni >= tk->kblocks) {
+        ni = 0;
+        ntile = tile + gridDim.x;
+        ntk = ntile < gp.total_tiles ? tile_task(gp, ntile, nk, nlocal) : nullptr;
+      }
+      if (ntk) a_row_load(ntk, nlocal, ni, r, nxt);
+      const int s = g & 1;
+      if (lane == 0) {
+        if (!mbar_wait(&aempty[s], ((uint32_t)(g >> 1) & 1u) ^ 1u) || *abort_flag) {
+          *abort_flag = 1;
+          ok = 0;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      const uint32_t ta = ta0 + (uint32_t)(s * 64);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float h[16], l[16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 v = cur[half * 4 + u];
+          Split<false>::split(v.x, h[4 * u], l[4 * u]);
+          Split<false>::split(v.y, h[4 * u + 1], l[4 * u + 1]);
+          Split<false>::split(v.z, h[4 * u + 2], l[4 * u + 2]);
+          Split<false>::split(v.w, h[4 * u + 3], l[4 * u + 3]);
+        }
+        tmem_st16(ta + (uint32_t)(half * 16), h);
+        tmem_st16(ta + 32u + (uint32_t)(half * 16), l);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&afull[s]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
+      tile = ntile;
+      tk = ntk;
+      local = nlocal;
+      k = nk;
+      i = ni;
+      ++g;
+    }
+  } else {
+    // ---- B converters: raw complex64 B tiles -> hi/lo B' tiles in shared memory
+    const int ct = threadIdx.x - 32 * kBWarp0;  // 0 .. 32*kBConv-1
+    constexpr int kCT = 32 * C::kBConv;
+    constexpr int kUB = ((kBN / 2) * 8 + kCT - 1) / kCT;  // B units per thread
+    static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
+    int g = 0, k = 0, local = 0, ok = 1;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+      const GemmTask* tk = tile_task(gp, tile, k, local);
+      const bool bmn = tk->b_mn != 0;  // [k][n] raw tile (3-d, 4-d or 5-d map alike)
+      for (int i = 0; i < tk->kblocks; ++i, ++g) {
+        const int st = g % S;
+        const uint32_t ph = (uint32_t)(g / S) & 1u;
+        if (lane == 0) {
+          if (!mbar_wait(&rfull[st], ph) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const uint8_t* rp = raw + st * C::kRawB;
+        const float2* rb = reinterpret_cast<const float2*>(rp);
+        float4 vb[kUB];
+        // unit it -> (column n, chunk c): [k][n] tiles: a warp takes 16
+        // consecutive n at two chunks c, c ^ 1; K-major tiles: n = it / 8
+#pragma unroll
+        for (int j = 0; j < kUB; ++j) {
+          const int it = ct + j * kCT;
+          if (it < (kBN / 2) * 8) {
+            int n, c;
+            if (bmn) {
+              n = (it & 15) + 16 * ((it >> 5) & 3);
+              c = 2 * (it >> 7) + ((it >> 4) & 1);
+              const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
+              vb[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
+            } else {
+              n = it >> 3;
+              c = it & 7;
+              vb[j] = *reinterpret_cast<const float4*>(rp + n * 128 + 16 * (c ^ (n & 7)));
+            }
+          }
+        }
+        if (lane == 0) {
+          if (!mbar_wait(&bempty[st], ph ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        uint8_t* bh = smem + st * C::kBStage;
+        uint8_t* bl = bh + C::kBTile;
+#pragma unroll
+        for (int j = 0; j < kUB; ++j) {
+          const int it = ct + j * kCT;
+          if (it >= (kBN / 2) * 8) continue;
+          int n, c;
+          if (bmn) {
+            n = (it & 15) + 16 * ((it >> 5) & 3);
+            c = 2 * (it >> 7) + ((it >> 4) & 1);
+          } else {
+            n = it >> 3;
+            c = it & 7;
+          }
+          // complex column n -> B' rows 2n (re, -im) and 2n+1 (im, re); the
+          // 16-byte chunk c of row r sits at chunk c ^ (r & 7) (128-byte swizzle)
+          const float4 v = vb[j];
+          const int r0 = 2 * n, r1 = 2 * n + 1;
+          const int o0 = r0 * 128 + 16 * (c ^ (r0 & 7)), o1 = r1 * 128 + 16 * (c ^ (r1 & 7));
+          float h[4], l[4];
+          Split<false>::split(v.x, h[0], l[0]);
+          Split<false>::split(-v.y, h[1], l[1]);
+          Split<false>::split(v.z, h[2], l[2]);
+          Split<false>::split(-v.w, h[3], l[3]);
+          *reinterpret_cast<float4*>(bh + o0) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(bl + o0) = make_float4(l[0], l[1], l[2], l[3]);
+          *reinterpret_cast<float4*>(bh + o1) = make_float4(-h[1], h[0], -h[3], h[2]);
+          *reinterpret_cast<float4*>(bl + o1) = make_float4(-l[1], l[0], -l[3], l[2]);
+        }
+        // generic-proxy writes -> visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&bfull[st]);
+          mbar_arrive(&rempty[st]);
+        }
+      }
+    }
+  }
+  // teardown: no MMA may still write TMEM when it is released
+  if (warp == 1 && lane == 0) {
+    if (!mbar_wait(done, 0)) *abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicCAS(&g_mixed_error, 0, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::kTmemCols));
 }
 
 // K4r: out c64 [lt][M][N] = sum over splits of the FP32 partials, in FP64
@@ -1280,6 +1724,7 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const Mixe
   // memory by TMA alone, while the converter warps add shared-memory traffic
   // next to the three MMAs per k-step).
   d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= tune.fused_max_n;
+  d->tmem_a = tune.fused_kernel == 1;
   if (d->fused && make_fused_desc(cd, d, tune.split_policy)) return true;
   d->fused = false;
   const int es = bf16 ? 2 : 4;
@@ -1424,6 +1869,10 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
       return false;
     }
     t->b_mn = d.b_mn2 ? 2 : (d.b_mn ? 1 : 0);
+    t->a_raw = static_cast<const float2*>(a);
+    t->a_ts = ats;
+    t->a_rs = d.a_rowstride;
+    t->kc = (int)cd.K;
   } else if (!make_map(&t->map[0], as, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[1], as + d.plane_a, d.bf16, d.kp, cd.M, cd.lt) ||
              !make_map(&t->map[2], bs, d.bf16, d.kp, 2 * cd.N, cd.lt) ||
@@ -1465,10 +1914,15 @@ void launch_gemm_t(const GemmParams& gp, dim3 grid, cudaStream_t s) {
   k_gemm_split3<BF16, FUSED><<<grid, C::kThreads, C::kSmem, s>>>(gp);
 }
 
-int launch_gemm(const GemmParams& gp, bool bf16, bool fused, cudaStream_t s) {
+int launch_gemm(const GemmParams& gp, bool bf16, bool fused, cudaStream_t s,
+                bool tmem_a = false) {
   if (gp.total_tiles <= 0) return 0;
   dim3 grid((unsigned)std::min<long long>(gp.total_tiles, num_sms()));
-  if (fused) launch_gemm_t<false, true>(gp, grid, s);
+  if (fused && tmem_a) {
+    cudaFuncSetAttribute(k_gemm_tf32_tmem_a, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TaCfg::kSmem);
+    k_gemm_tf32_tmem_a<<<grid, TaCfg::kThreads, TaCfg::kSmem, s>>>(gp);
+  } else if (fused) launch_gemm_t<false, true>(gp, grid, s);
   else if (bf16) launch_gemm_t<true, false>(gp, grid, s);
   else launch_gemm_t<false, false>(gp, grid, s);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
@@ -1484,7 +1938,7 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
     std::memset(&gp, 0, sizeof(gp));
     if (!fill_gemm_task(d, A, B, scratch, C, &gp.single, nullptr, nullptr)) return -2;
     gp.total_tiles = gp.single.tiles;
-    if (launch_gemm(gp, false, true, s) < 0) return -1;
+    if (launch_gemm(gp, false, true, s, d.tmem_a) < 0) return -1;
     ++nk;
     if (d.splits > 1) {
       const long long per = cd.lt * cd.M * 2 * cd.N;
@@ -1683,6 +2137,7 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   std::vector<PermTask> pm;
   std::vector<GemmTask> gf;  // fused-form GEMM tasks
   long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0, ftiles = 0;
+  bool lvl_tmem_a = false;
   auto add_perm = [&](const PermDesc& pd, const void* src, void* dst) {
     PermTask t;
     std::memset(&t, 0, sizeof(t));
@@ -1740,6 +2195,7 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
       }
       GemmTask g;
       if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g, as, bs)) return false;
+      lvl_tmem_a = d.tmem_a;  // one DAG option: every fused task of a level alike
       g.tile_start = ftiles;
       ftiles += g.tiles;
       gf.push_back(g);
@@ -1806,6 +2262,7 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->gemm_fused = reinterpret_cast<const void*>(append(buf, gf, 64));
   lvl->ngemm_fused = (int)gf.size();
   lvl->gemm_fused_tiles = ftiles;
+  lvl->fused_tmem_a = lvl_tmem_a;
   lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
   lvl->nred = (int)rd.size();
   lvl->red_blocks = rb;
@@ -1889,7 +2346,7 @@ int launch_level(const LevelDev& L, cudaStream_t s, cudaEvent_t* marks, unsigned
     gp.ntasks = L.ngemm_fused;
     gp.total_tiles = L.gemm_fused_tiles;
     mark();
-    if (launch_gemm(gp, false, true, s) < 0) return -1;
+    if (launch_gemm(gp, false, true, s, L.fused_tmem_a) < 0) return -1;
     ++nk;
   }
   if (L.nred > 0) {

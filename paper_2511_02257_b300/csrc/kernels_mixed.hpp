@@ -52,6 +52,7 @@ struct MixedDesc {
   bool b_mn2;               // ... as [k][outer n][inner n] blocks (4-d map)
   int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
   PermDesc a_perm, b_perm;
+  bool tmem_a;              // fused form: A split by converter warps into tensor memory
 };
 bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 
@@ -62,6 +63,7 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 struct MixedTune {
   int64_t fused_max_n = 64;
   int split_policy = 0;
+  int fused_kernel = 1;     // fused form: 0 = A staged in shared memory, 1 = A in TMEM
 };
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d,
                      const MixedTune& tune = MixedTune());
@@ -115,6 +117,7 @@ struct LevelDev {
   const void* gemm_fused;
   int ngemm_fused;
   long long gemm_fused_tiles;
+  bool fused_tmem_a;        // the fused tasks run the A-in-tensor-memory kernel
   const void* red;
   const long long* red_starts;
   int nred;

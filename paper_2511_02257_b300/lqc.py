@@ -34,7 +34,7 @@ LQC_SCHED_NODE, LQC_SCHED_RSGS = 3, 4
 LQC_EVICT_LRU, LQC_EVICT_NEXT_USE = 0, 1
 LQC_PREC_FP64, LQC_PREC_TF32X3, LQC_PREC_BF16X3 = 0, 1, 2
 LQC_OPT_CUDA_GRAPH, LQC_OPT_POISON, LQC_OPT_TIMING, LQC_OPT_WINDOW = 1, 2, 3, 4
-LQC_OPT_FUSED_MAX_N, LQC_OPT_SPLIT_POLICY = 5, 6
+LQC_OPT_FUSED_MAX_N, LQC_OPT_SPLIT_POLICY, LQC_OPT_FUSED_KERNEL = 5, 6, 7
 OP_NAMES = {0: "LOAD", 1: "EVICT", 2: "CONTRACT", 3: "FREE"}
 LQC_NUM_KINDS = 8
 KIND_NAMES = {0: "reorder", 1: "pack", 2: "gemm_planes", 3: "gemm_fused", 4: "reduce",
@@ -62,7 +62,8 @@ class lqc_exec_info(ctypes.Structure):
         [("ms_contract", ctypes.c_double), ("ms_contract_all", ctypes.c_double),
          ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64),
          ("n_kind", c_i64 * LQC_NUM_KINDS), ("ms_kind", ctypes.c_double * LQC_NUM_KINDS),
-         ("flops_gemm", c_i64), ("resident_peak_bytes", c_i64)]
+         ("flops_gemm", c_i64), ("resident_peak_bytes", c_i64),
+         ("extra_evictions", c_i64), ("extra_h2d_bytes", c_i64), ("extra_d2h_bytes", c_i64)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}

@@ -210,8 +210,10 @@ def test_budgeted_eviction_matches_oracle(evict):
         assert tuple(planned[k] for k in planned) == oplan.stats.as_tuple()
         assert nd.stats() == planned
         info = nd.exec_info()
-        assert info["copied_h2d"] == planned["h2d_bytes"]
-        assert info["copied_d2h"] == planned["d2h_bytes"]
+        # copies = the plan's + those placement adds to keep the arena in the budget
+        assert info["copied_h2d"] == planned["h2d_bytes"] + info["extra_h2d_bytes"]
+        assert info["copied_d2h"] == planned["d2h_bytes"] + info["extra_d2h_bytes"]
+        assert info["arena_bytes"] <= budget
         for r in ref:
             assert rel_err(vals[r], ref[r]) < TOL, (pol, r)
         if base is None:

@@ -67,3 +67,42 @@ def test_memory_pressure_full_size_fp64_with_evictions():
     errs = {r: float(np.linalg.norm(nd.read_correlator(r) - ref[r]) / np.linalg.norm(ref[r]))
             for r in pick}
     assert max(errs.values()) < 1e-12, errs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("budget_gib", [24, 8])
+def test_arena_within_budget_all_schedulers(budget_gib):
+    """The full memory-pressure workload (TF32x3 storage) under 24 and 8 GiB:
+    for every scheduler the physical arena stays within the budget (the
+    best-fit placement fragments; placement moves tensors to the host where
+    it must), the counted figures equal the plan's, copies = plan + the
+    reported extra moves, and every correlator is bit-identical to the tree
+    order's at 24 GiB."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = synth.make_workload("memory_pressure")
+    cache = {}
+
+    def leaf(li):
+        if li not in cache:
+            cache[li] = synth.leaf_data(wl, li)
+        return cache[li]
+    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=leaf)
+    budget = budget_gib << 30
+    stream = torch.cuda.current_stream().cuda_stream
+    base = None
+    for pol in ("tree", "naive", "sibling", "rsgs", "node"):
+        planned = nd.schedule(pol, "lru", budget)
+        nd.execute(stream)
+        vals = nd.read_all_correlators()
+        info = nd.exec_info()
+        assert info["arena_bytes"] <= budget, (pol, info["arena_bytes"])
+        assert nd.stats() == planned, pol
+        assert info["copied_h2d"] == planned["h2d_bytes"] + info["extra_h2d_bytes"]
+        assert info["copied_d2h"] == planned["d2h_bytes"] + info["extra_d2h_bytes"]
+        assert L.lqc_mixed_error(1) == 0
+        if base is None:
+            base = vals
+        assert np.array_equal(vals.view(np.float64), base.view(np.float64)), pol
+    nd.close()

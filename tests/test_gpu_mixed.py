@@ -240,7 +240,8 @@ def test_contract_all_c64_vs_oracle(case, lt):
                                  (128, 1100, 96)])
 @pytest.mark.parametrize("fused", [0, 1 << 30])
 @pytest.mark.parametrize("window", [0, 64])
-def test_matrix_product_forms_vs_oracle(mkn, fused, window):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_matrix_product_forms_vs_oracle(mkn, fused, window, kernel):
     """C = A.B with B stored [k][n] (read in place and transposed inside the
     fused GEMM when n is even), then Tr(C.D): every form against the oracle."""
     M, K, N = mkn
@@ -258,13 +259,16 @@ def test_matrix_product_forms_vs_oracle(mkn, fused, window):
     d.schedule("tree")
     d.set_option(L.LQC_OPT_FUSED_MAX_N, fused)
     d.set_option(L.LQC_OPT_WINDOW, window)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
     d.execute(torch.cuda.current_stream().cuda_stream)
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
+    assert L.lqc_mixed_error(1) == 0
 
 
 @pytest.mark.parametrize("n", [64, 128])
 @pytest.mark.parametrize("window", [0, 64])
-def test_propagator_right_operand_in_place_vs_oracle(n, window):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_propagator_right_operand_in_place_vs_oracle(n, window, kernel):
     """M . P over P's first distillation axis: P is read in place as [k][spin
     block][n] by the fused GEMM (one 4-d TMA box per tile), then a correlator
     of the result; against the oracle."""
@@ -282,12 +286,14 @@ def test_propagator_right_operand_in_place_vs_oracle(n, window):
     d.schedule("tree")
     d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
     d.set_option(L.LQC_OPT_WINDOW, window)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
     d.execute(torch.cuda.current_stream().cuda_stream)
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
 
 
 @pytest.mark.parametrize("n", [32, 128])
-def test_propagator_left_operand_in_place_vs_oracle(n):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_propagator_left_operand_in_place_vs_oracle(n, kernel):
     """P x P over (spin out, distillation out) and a P x M over three axes:
     left operands whose contracted axes are several groups (and whose rows are
     two groups at n = 128) are read in place; against the oracle."""
@@ -306,5 +312,62 @@ def test_propagator_left_operand_in_place_vs_oracle(n):
     r = d.add_contraction(y, m, [0, 1], [0, 1])
     d.schedule("tree")
     d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
     d.execute(torch.cuda.current_stream().cuda_stream)
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("mkn,bmn", [((40, 70, 24), True), ((130, 44, 200), True),
+                                     ((129, 1100, 64), True), ((64, 48, 64), False),
+                                     ((300, 34, 70), False)])
+@pytest.mark.parametrize("window", [0, 64])
+def test_fused_kernels_exact_on_integers(kernel, mkn, bmn, window):
+    """Both fused GEMMs on small-integer operands, where the split is exact
+    and every partial sum is an integer below 2^24: the correlator
+    Tr(A.B.D) equals the oracle bit for bit.  Rows and k are not multiples
+    of the tiles (a ragged last tile, k blocks partly beyond K), K > 512
+    splits over k, and B is stored [k][n] (read in place) or [n][k]."""
+    M, K, N = mkn
+    lt = 3
+    rng = np.random.default_rng(M + 7 * K + 13 * N + kernel)
+
+    def ints(*s):
+        return rng.integers(-3, 4, (lt,) + s) + 1j * rng.integers(-3, 4, (lt,) + s)
+    A, Dm = ints(M, K), ints(N, M)
+    B = ints(K, N) if bmn else ints(N, K)
+    ref = C.contract_pair(C.contract_pair(A, B, (1,), (0,) if bmn else (1,)), Dm, (0, 1), (1, 0))
+    d = L.Dag(lt, "tf32x3")
+    a = d.add_leaf((M, K), A)
+    b = d.add_leaf((K, N) if bmn else (N, K), B)
+    dd = d.add_leaf((N, M), Dm)
+    c = d.add_contraction(a, b, [1], [0] if bmn else [1])
+    r = d.add_contraction(c, dd, [0, 1], [1, 0])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+    d.set_option(L.LQC_OPT_WINDOW, window)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    got = d.read_correlator(r)
+    assert L.lqc_mixed_error(1) == 0
+    assert np.array_equal(got, ref), rel_err(got, ref)
+
+
+def test_fused_kernels_agree_on_a_dag():
+    """The two fused GEMMs on the same DAG (multi-meson terms, every width
+    fused): both within the mixed bar of the oracle on every root."""
+    wl = synth.make_workload("multi_meson", n_functions=30)
+    od, _ = D.build_from_workload(wl)
+    ref = C.evaluate(od, lambda u: synth.leaf_data(wl, od.nodes[u].leaf_index))
+    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd.schedule("tree", "lru", 0)
+    nd.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    stream = torch.cuda.current_stream().cuda_stream
+    worst = {}
+    for kernel in (0, 1):
+        nd.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+        nd.execute(stream)
+        vals = {r: nd.read_correlator(r) for r in nd.roots()}
+        assert L.lqc_mixed_error(1) == 0
+        worst[kernel] = max(rel_err(vals[r], ref[r]) for r in ref)
+    assert max(worst.values()) < TOL_TF32X3, worst

@@ -11,7 +11,7 @@ from oracle import memory as M
 from oracle.enumerate import topological_orders
 
 L = pytest.importorskip("paper_2511_02257_b300")
-from paper_2511_02257_b300 import experiments as E  # noqa: E402
+import experiments as E  # noqa: E402
 
 
 @pytest.mark.parametrize("name,kw,seed", [

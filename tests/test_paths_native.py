@@ -184,7 +184,7 @@ def test_add_graphs_argument_errors():
 @pytest.mark.parametrize("name,kw", [("multi_meson", dict(n_functions=12, nvec=6, lt=3)),
                                      ("baryon", dict(n_functions=10, nvec=5, lt=2))])
 def test_dag_flops_from_sizes(name, kw):
-    from paper_2511_02257_b300.experiments import dag_contraction_flops
+    from experiments import dag_contraction_flops
     from paper_2511_02257_b300.roofline import contraction_shapes
     wl = synth.make_workload(name, **kw)
     nd, ids = L.build_dag(wl, with_data=False)

@@ -557,12 +557,16 @@ def sub_record(L, name, args, stream, link):
         ms = timed_executes(nn, stream, 1, 0)
         tn = ms / 1e3
         cnt = nn.stats()
+        ninfo = nn.exec_info()
         v = nn.read_all_correlators().reshape(-1)
         rec["naive_order"] = {
             "time_to_solution_s": tn, "n_evict": cnt["n_evict"],
             "peak_paper_bytes": pl["peak_paper"], "peak_exec_bytes": pl["peak_exec"],
             "h2d_bytes": cnt["h2d_bytes"], "d2h_bytes": cnt["d2h_bytes"],
             "stats_equal_plan": cnt == pl,
+            "arena_bytes": ninfo["arena_bytes"], "budget_bytes": wl.budget_bytes,
+            "extra_placement_moves": {k: ninfo[k] for k in ("extra_evictions", "extra_h2d_bytes",
+                                                            "extra_d2h_bytes")},
             "correlators_bit_identical_to_tree_order": bool(np.array_equal(
                 v.view(np.float64), mixed.view(np.float64))),
             "link": link_record(cnt["h2d_bytes"], cnt["d2h_bytes"], tn, link),
@@ -684,6 +688,7 @@ def main():
 
     # ---- end to end: leaves from pinned host memory, correlators back to the host
     e2e = None
+    counted_equal = None
     if not args.no_e2e:
         nd.set_option(L.LQC_OPT_TIMING, 0)
         nd.unstage_leaves()
@@ -704,6 +709,7 @@ def main():
         t_e2e = time.perf_counter() - t0
         t_e2e = max_over_ranks(t_e2e, ws)
         st = nd.stats()
+        counted_equal = st == planned   # leaves from the host: every plan copy is issued
         e2e = {"value": job_flops * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": st["h2d_bytes"],
                "d2h_bytes_per_step": st["d2h_bytes"] + out.nbytes,
@@ -715,7 +721,7 @@ def main():
     arena = info1["arena_bytes"]
     resident_peak = info1["resident_peak_bytes"]
     leaf_bytes = sum(nd.node_info(i)["size"] for i in range(len(wl.leaves)))
-    measured_stats = nd.stats()
+    ex_info = nd.exec_info()
     n_contr = len(nd.order())
     nd.close()
     del nd
@@ -786,7 +792,9 @@ def main():
             "peak_paper_bytes": planned["peak_paper"], "peak_exec_bytes": planned["peak_exec"],
             "n_evict": planned["n_evict"], "h2d_gb_per_step": planned["h2d_bytes"] / 1e9,
             "d2h_gb_per_step": planned["d2h_bytes"] / 1e9,
-            "stats_counted_equal_planned": measured_stats == planned,
+            "stats_counted_equal_planned": counted_equal,
+            "extra_placement_moves": {k: ex_info[k] for k in ("extra_evictions", "extra_h2d_bytes",
+                                                               "extra_d2h_bytes")},
             "arena_bytes": arena, "resident_peak_bytes": resident_peak,
             "schedule_ms": 1e3 * t_sched, "dag_build_s": t_build, "leaf_generation_s": t_gen,
             "roofline": roofline,

@@ -180,14 +180,14 @@ typedef enum {
                              output tiles cannot fill the GPU and for the
                              FP32 chunk bound (1024 real k), 1 for the chunk
                              bound only                                     */
-  LQC_OPT_FUSED_KERNEL = 7 /* TF32X3 fused form: 1 (default) = converter
-                             warps write A's hi/lo parts into tensor memory
-                             and the MMAs read A there, B from shared memory
-                             (correction products first into a fresh
-                             accumulator, drained every 128-byte k block);
-                             0 = both operands staged in shared memory, main
-                             and correction accumulators apart, drained every
-                             two k blocks                                    */
+  LQC_OPT_FUSED_KERNEL = 7 /* TF32X3 fused form: 0 (default) = both operands'
+                             hi/lo tiles built in shared memory, main and
+                             correction accumulators apart, drained every two
+                             128-byte k blocks; 1 = converter warps write A's
+                             hi/lo parts into tensor memory and the MMAs read
+                             A there (B from shared memory): the correction
+                             products of a k block go first into a fresh
+                             accumulator, then hi*hi, drained every k block */
 } lqc_option;
 
 /* One autotuner candidate and its measured time per execute. */
@@ -561,6 +561,14 @@ int lqc_test_inject_failure(int site, int64_t skip_calls);
  * device error word (which lqc_dag_wait reads after an execute; this call
  * clears it again), LQC_OK if it did not expire, LQC_ERR_ARG, LQC_ERR_CUDA. */
 int lqc_test_expire_wait(int64_t limit_ns, void* stream);
+
+/* Check the TF32 rounding the converter warps use (an integer form of
+ * round-to-nearest, ties away from zero) against the hardware conversion
+ * cvt.rna.tf32.f32 on n finite float bit patterns drawn from a hash of
+ * (seed, index), the first 4096 of them exact ties; *mismatches receives
+ * the count of differing results (0 expected).  Synchronous.  Errors:
+ * LQC_ERR_ARG, LQC_ERR_CUDA. */
+int lqc_test_tf32_rounding(int64_t n, uint32_t seed, int64_t* mismatches);
 
 /* Change the stored op list of a DAG scheduled without a budget, keeping
  * the planned figures, so that a test can tell figures the executor counts

@@ -68,7 +68,7 @@ struct Dag {
   ExecState* ex = nullptr;
   int64_t opt_graph = 0, opt_poison = 0, opt_timing = 0, opt_window = 64;
   int64_t opt_fused_max_n = 64, opt_split_policy = 0;  // mixed GEMM choices
-  int64_t opt_fused_kernel = 1;
+  int64_t opt_fused_kernel = 0;
   lqc_stats measured{};
   lqc_exec_info info{};
   bool executed = false;

@@ -73,6 +73,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// Rounding to TF32 (10 stored mantissa bits) to nearest, ties away from
+// zero: add half a unit of the last kept bit to the magnitude bits and clear
+// the 13 dropped bits (a carry into the exponent is the correct round-up).
+// Two full-rate integer operations instead of a conversion instruction; the
+// converter warps issue two per split value.  Equal to cvt.rna.tf32.f32 for
+// finite inputs (checked on the device by lqc_test_tf32_rounding).
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
@@ -101,6 +110,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
     if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
+}
+
+// Test of the TF32 rounding: n values x_i spread over every binade and
+// mantissa pattern (x_i = bit pattern hash(seed, i), finite values only),
+// each rounded by round_tf32 and by the hardware conversion cvt.rna; counts
+// the values where the two differ.
+__global__ void k_tf32_rounding_check(long long n, unsigned seed, unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    if ((h & 0x7F800000u) == 0x7F800000u) h &= 0xBF7FFFFFu;  // Inf / NaN patterns -> finite
+    if (i < 4096) h = (h & 0xFFFFE000u) | 0x1000u;           // exact ties first
+    const float x = __uint_as_float(h);
+    uint32_t hw;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hw) : "f"(x));
+    if (__float_as_uint(round_tf32(x)) != hw) ++local;
+  }
+  if (local) atomicAdd(bad, local);
 }
 
 // Test of the bounded wait: one thread waits on an mbarrier that nothing
@@ -182,18 +215,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// two 16-column TMEM loads in flight before one wait
+__device__ __forceinline__ void tmem_ld16_pair(uint32_t ta, uint32_t tb, uint32_t* r,
+                                               uint32_t* s) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]),
+        "=r"(s[7]), "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]),
+        "=r"(s[14]), "=r"(s[15])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 template <bool BF16>
 struct Split;
 template <>
 struct Split<false> {
   typedef float T;
   __device__ static void split(float x, float& hi, float& lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
-    lo = __uint_as_float(l);
+    hi = round_tf32(x);
+    lo = round_tf32(x - hi);  // x - hi is exact
   }
   __device__ static void store2(float* p, float a, float b) {
     *reinterpret_cast<float2*>(p) = make_float2(a, b);
@@ -499,8 +548,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
 #pragma unroll
         for (int j = 0; j < kHalf; j += 16) {
           uint32_t r[16], rc[16];
-          tmem_ld16(tb + j, r);      // collective: every lane loads, in-range or not
-          tmem_ld16(tb + kBN + j, rc);
+          tmem_ld16_pair(tb + j, tb + kBN + j, r, rc);  // collective: every lane loads
 #pragma unroll
           for (int u = 0; u < 16; ++u)
             acc[j + u] += __uint_as_float(r[u]) + __uint_as_float(rc[u]);
@@ -680,29 +728,33 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
 }
 
 // ------------------------------------------------------------ K4t: A in TMEM
-// Fused TF32 split-3 GEMM whose A operand never passes through shared
-// memory.  Four A-converter warps (one per TMEM lane quarter, one A' row per
-// thread) load the raw complex64 row segment of a k-block from global memory
-// one k-block ahead, split it into hi/lo and write both into tensor memory
+// Fused TF32 split-3 GEMM whose A' hi/lo operands live in tensor memory.
+// TMA brings raw complex64 tiles of A (128 rows) and B (64 complex columns)
+// into a shared-memory ring (the maps of the fused form).  Four A-converter
+// warps (one per TMEM lane quarter, one A' row per thread) read their row
+// of the raw A tile, split it into hi/lo and write both into tensor memory
 // with tcgen05.st; tcgen05.mma reads A from there and only B' from shared
-// memory.  B arrives as raw complex64 tiles by TMA (the maps of the fused
-// form) and two B-converter warps build its hi/lo B' tiles.  Per k-block the
-// MMA thread issues the two correction products (lo*hi, hi*lo) first, into a
-// fresh accumulator, then hi*hi, and the drain warps add the finished
-// accumulator into FP32 registers: four accumulations at full magnitude per
-// drain.  Shared-memory traffic per k-block: raw B written and read (16 KB),
-// B' hi/lo written (32 KB), B' read by the MMAs (48 KB) -- against 208 KB
-// when A is staged in shared memory too.
+// memory, where two B-converter warps build the hi/lo B' tiles.  Per k-block
+// the MMA thread issues the two correction products (lo*hi, hi*lo) first,
+// into a fresh accumulator, then hi*hi, and the drain warps add the
+// finished accumulator into FP32 registers: four accumulations at full
+// magnitude per drain.  Shared-memory traffic per k-block: raw A and B
+// written and read (48 KB), B' hi/lo written (32 KB), B' read by the MMAs
+// (48 KB) -- 128 KB against 208 KB when the A' planes are staged in shared
+// memory as well (three MMAs read each of them).
 struct TaCfg {
-  static constexpr int kStages = 4;                 // raw B ring = B' operand ring
+  static constexpr int kRawStages = 4;              // raw A + B ring
+  static constexpr int kStages = 3;                 // B' operand ring
   static constexpr int kBTile = kBN * 128;          // one B' plane tile: kBN rows x 128 B
   static constexpr int kBStage = 2 * kBTile;        // hi + lo
+  static constexpr int kRawA = kBM * 128;           // raw complex64 A tile (128-byte swizzle)
   static constexpr int kRawB = (kBN / 2) * 128;     // raw complex64 B tile
+  static constexpr int kRaw = kRawA + kRawB;
   static constexpr int kAConv = 4, kBConv = 2;      // converter warps
   static constexpr int kThreads = 64 + 32 * (kDrainWarps + kAConv + kBConv);
   static constexpr int kStgPitch = 20;
   static constexpr int kStgBytes = kDrainWarps * 32 * kStgPitch * 4;
-  static constexpr int kSmem = kStages * (kBStage + kRawB) + 1024 + 256 + kStgBytes;
+  static constexpr int kSmem = kStages * kBStage + kRawStages * kRaw + 1024 + 256 + kStgBytes;
   static constexpr int kACol = 2 * kBN;             // TMEM: [0, 2 kBN) accumulators, then A
   static constexpr int kTmemCols = 512;
 };
@@ -729,43 +781,26 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
       : "memory");
 }
 
-// raw A row segment (16 complex = 8 float4) of k-block i of a tile for row r
-// of the tile; zero beyond the matrix
-__device__ __forceinline__ void a_row_load(const GemmTask* tk, int local, int i, int r,
-                                           float4 (&v)[8]) {
-  const int tm = (local / tk->ntn) % tk->ntm;
-  const int z = local / (tk->ntn * tk->ntm);
-  const int t = z % tk->lt, split = z / tk->lt;
-  const int m = tm * kBM + r;
-  const int kc0 = (split * tk->kblocks + i) * 16;
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  const bool row_ok = m < tk->M;
-  const float4* p = reinterpret_cast<const float4*>(
-      tk->a_raw + (long long)t * tk->a_ts + (long long)(row_ok ? m : 0) * tk->a_rs + kc0);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = (row_ok && kc0 + 2 * c < tk->kc) ? __ldg(p + c) : zero;
-}
-
 __global__ void __launch_bounds__(TaCfg::kThreads, 1)
 k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
   using C = TaCfg;
-  constexpr int S = C::kStages;
+  constexpr int S = C::kStages, R = C::kRawStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint8_t* raw = smem + S * C::kBStage;  // raw complex64 B ring
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(raw + S * C::kRawB);  // [S] B' stage built
+  uint8_t* raw = smem + S * C::kBStage;  // raw complex64 ring: A tile, then B tile
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(raw + R * C::kRaw);  // [S] B' stage built
   uint64_t* bempty = bfull + S;        // [S] B' stage read by its MMAs
-  uint64_t* rfull = bempty + S;        // [S] raw B landed
-  uint64_t* rempty = rfull + S;        // [S] raw B converted
-  uint64_t* afull = rempty + S;        // [2] A stage written to TMEM
+  uint64_t* rfull = bempty + S;        // [R] raw A + B landed
+  uint64_t* rempty = rfull + R;        // [R] raw A and B read by the converters
+  uint64_t* afull = rempty + R;        // [2] A stage written to TMEM
   uint64_t* aempty = afull + 2;        // [2] A stage read by its MMAs
   uint64_t* tfull = aempty + 2;        // [2] accumulator ready to drain
   uint64_t* tempty = tfull + 2;        // [2] accumulator drained
   uint64_t* done = tempty + 2;         // every MMA issued has completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* stage_out = reinterpret_cast<float*>(raw + S * C::kRawB + 256);
+  float* stage_out = reinterpret_cast<float*>(raw + R * C::kRaw + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kAWarp0 = 2 + kDrainWarps, kBWarp0 = kAWarp0 + C::kAConv;
@@ -774,8 +809,10 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&bfull[i], C::kBConv);
       mbar_init(&bempty[i], 1);
+    }
+    for (int i = 0; i < R; ++i) {
       mbar_init(&rfull[i], 1);
-      mbar_init(&rempty[i], C::kBConv);
+      mbar_init(&rempty[i], C::kAConv + C::kBConv);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&afull[b], C::kAConv);
@@ -800,25 +837,27 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---- TMA producer: raw B tiles
+      // ---- TMA producer: raw A and B tiles
       int g = 0, issued = 0, k = 0, local = 0;
       bool stop = false;
       for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
         const GemmTask* tk = tile_task(gp, tile, k, local);
-        const int tn = local % tk->ntn;
+        const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
         const int z = local / (tk->ntn * tk->ntm);
         const int t = z % tk->lt, split = z / tk->lt;
-        const int n0 = tn * kBN, kb0 = split * tk->kblocks;
+        const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * tk->kblocks;
         for (int i = 0; i < tk->kblocks; ++i, ++g) {
-          const int st = g % S;
-          if (!mbar_wait(&rempty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
+          const int st = g % R;
+          if (!mbar_wait(&rempty[st], ((uint32_t)(g / R) & 1u) ^ 1u) || *abort_flag) {
             *abort_flag = 1;
             stop = true;
             break;
           }
           const int k0 = (kb0 + i) * 32;  // floats
-          uint8_t* rp = raw + st * C::kRawB;
-          mbar_expect_tx(&rfull[st], C::kRawB);
+          uint8_t* ra = raw + st * C::kRaw;
+          uint8_t* rp = ra + C::kRawA;
+          mbar_expect_tx(&rfull[st], C::kRaw);
+          tma_load_3d(ra, &tk->map[0], &rfull[st], k0, m0, t);
           if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
             int c[5], nd = 0, kk = k0 / 2;
             c[nd++] = n0 % (2 * tk->b_ni);
@@ -842,8 +881,8 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
         }
       }
       // every issued load must have landed before the CTA exits
-      for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
-        if (!mbar_wait(&rfull[i % S], (uint32_t)(i / S) & 1u)) break;
+      for (int i = (issued > R ? issued - R : 0); i < issued; ++i)
+        if (!mbar_wait(&rfull[i % R], (uint32_t)(i / R) & 1u)) break;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -911,11 +950,14 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t tb = tmem + tlane + (uint32_t)(b * kBN);
 #pragma unroll
-        for (int j = 0; j < kHalf; j += 16) {
-          uint32_t r[16];
-          tmem_ld16(tb + j, r);
+        for (int j = 0; j < kHalf; j += 32) {
+          uint32_t r[16], r2[16];
+          tmem_ld16_pair(tb + j, tb + j + 16, r, r2);
 #pragma unroll
-          for (int u = 0; u < 16; ++u) acc[j + u] += __uint_as_float(r[u]);
+          for (int u = 0; u < 16; ++u) {
+            acc[j + u] += __uint_as_float(r[u]);
+            acc[j + 16 + u] += __uint_as_float(r2[u]);
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -956,64 +998,58 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
       }
     }
   } else if (warp < kBWarp0) {
-    // ---- A converters: global complex64 rows -> hi/lo A' rows in TMEM
-    const int q = warp & 3, r = q * 32 + lane;  // this thread's row of the tile
+    // ---- A converters: this thread's row of the raw A tile -> hi/lo A' row in TMEM
+    const int q = warp & 3, r = q * 32 + lane;  // the row = the TMEM lane it writes
     const uint32_t ta0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)C::kACol;
-    int k = 0, local = 0, ok = 1, g = 0, i = 0;
-    long long tile = blockIdx.x;
-    const GemmTask* tk = tile < gp.total_tiles ? tile_task(gp, tile, k, local) : nullptr;
-    int nk = k, nlocal = local;  // look-ahead cursor of the next k-block
-    float4 cur[8], nxt[8];
-    if (tk) a_row_load(tk, local, 0, r, cur);
-    while (tk) {
-      // the next k-block (of this tile or the next one): its loads fly while
-      // this one is split and stored
-      int ni = i + 1;
-      long long ntile = tile;
-      const GemmTask* ntk = tk;
-      nlocal = local;
-      if (ni >= tk->kblocks) {
-        ni = 0;
-        ntile = tile + gridDim.x;
-        ntk = ntile < gp.total_tiles ? tile_task(gp, ntile, nk, nlocal) : nullptr;
-      }
-      if (ntk) a_row_load(ntk, nlocal, ni, r, nxt);
-      const int s = g & 1;
-      if (lane == 0) {
-        if (!mbar_wait(&aempty[s], ((uint32_t)(g >> 1) & 1u) ^ 1u) || *abort_flag) {
-          *abort_flag = 1;
-          ok = 0;
+    int g = 0, k = 0, local = 0, ok = 1;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+      const GemmTask* tk = tile_task(gp, tile, k, local);
+      for (int i = 0; i < tk->kblocks; ++i, ++g) {
+        const int st = g % R, s = g & 1;
+        if (lane == 0) {
+          if (!mbar_wait(&rfull[st], (uint32_t)(g / R) & 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
         }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      const uint32_t ta = ta0 + (uint32_t)(s * 64);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        // chunk c of row r sits at chunk c ^ (r & 7): a quarter-warp's 16-byte
+        // reads (8 rows) cover all 32 banks
+        const uint8_t* ra = raw + st * C::kRaw + r * 128;
+        float4 v[8];
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float h[16], l[16];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 v = cur[half * 4 + u];
-          Split<false>::split(v.x, h[4 * u], l[4 * u]);
-          Split<false>::split(v.y, h[4 * u + 1], l[4 * u + 1]);
-          Split<false>::split(v.z, h[4 * u + 2], l[4 * u + 2]);
-          Split<false>::split(v.w, h[4 * u + 3], l[4 * u + 3]);
+        for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(ra + 16 * (c ^ (r & 7)));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rempty[st]);
+        if (lane == 0) {
+          if (!mbar_wait(&aempty[s], ((uint32_t)(g >> 1) & 1u) ^ 1u) || *abort_flag) {
+            *abort_flag = 1;
+            ok = 0;
+          }
         }
-        tmem_st16(ta + (uint32_t)(half * 16), h);
-        tmem_st16(ta + 32u + (uint32_t)(half * 16), l);
-      }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&afull[s]);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const uint32_t ta = ta0 + (uint32_t)(s * 64);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
-      tile = ntile;
-      tk = ntk;
-      local = nlocal;
-      k = nk;
-      i = ni;
-      ++g;
+        for (int half = 0; half < 2; ++half) {
+          float h[16], l[16];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 x = v[half * 4 + u];
+            Split<false>::split(x.x, h[4 * u], l[4 * u]);
+            Split<false>::split(x.y, h[4 * u + 1], l[4 * u + 1]);
+            Split<false>::split(x.z, h[4 * u + 2], l[4 * u + 2]);
+            Split<false>::split(x.w, h[4 * u + 3], l[4 * u + 3]);
+          }
+          tmem_st16(ta + (uint32_t)(half * 16), h);
+          tmem_st16(ta + 32u + (uint32_t)(half * 16), l);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&afull[s]);
+      }
     }
   } else {
     // ---- B converters: raw complex64 B tiles -> hi/lo B' tiles in shared memory
@@ -1026,17 +1062,17 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
       const GemmTask* tk = tile_task(gp, tile, k, local);
       const bool bmn = tk->b_mn != 0;  // [k][n] raw tile (3-d, 4-d or 5-d map alike)
       for (int i = 0; i < tk->kblocks; ++i, ++g) {
-        const int st = g % S;
+        const int st = g % S, rs = g % R;
         const uint32_t ph = (uint32_t)(g / S) & 1u;
         if (lane == 0) {
-          if (!mbar_wait(&rfull[st], ph) || *abort_flag) {
+          if (!mbar_wait(&rfull[rs], (uint32_t)(g / R) & 1u) || *abort_flag) {
             *abort_flag = 1;
             ok = 0;
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
-        const uint8_t* rp = raw + st * C::kRawB;
+        const uint8_t* rp = raw + rs * C::kRaw + C::kRawA;
         const float2* rb = reinterpret_cast<const float2*>(rp);
         float4 vb[kUB];
         // unit it -> (column n, chunk c): [k][n] tiles: a warp takes 16
@@ -1100,7 +1136,7 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&bfull[st]);
-          mbar_arrive(&rempty[st]);
+          mbar_arrive(&rempty[rs]);
         }
       }
     }
@@ -2433,6 +2469,25 @@ int64_t lqc_contract_all_c64_scratch_bytes(int rank_a, const int64_t* ext_a, int
 }
 
 int lqc_mixed_error(int reset) { return lqc::mixed_error_status(reset != 0); }
+
+int lqc_test_tf32_rounding(int64_t n, uint32_t seed, int64_t* mismatches) {
+  if (n < 1 || !mismatches) return LQC_ERR_ARG;
+  lqc::clear_pending_error();
+  unsigned long long* bad = nullptr;
+  if (cudaMalloc(&bad, sizeof(unsigned long long)) != cudaSuccess) return LQC_ERR_CUDA;
+  unsigned long long h = 0;
+  int rc = LQC_OK;
+  if (cudaMemset(bad, 0, sizeof(h)) != cudaSuccess) rc = LQC_ERR_CUDA;
+  if (rc == LQC_OK) {
+    lqc::k_tf32_rounding_check<<<4 * 148, 256>>>((long long)n, seed, bad);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = LQC_ERR_CUDA;
+  }
+  cudaFree(bad);
+  if (rc == LQC_OK) *mismatches = (int64_t)h;
+  return rc;
+}
 
 int lqc_test_expire_wait(int64_t limit_ns, void* stream) {
   if (limit_ns < 1 || limit_ns > 1000000000) return LQC_ERR_ARG;

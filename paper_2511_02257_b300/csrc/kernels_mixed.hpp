@@ -63,7 +63,7 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 struct MixedTune {
   int64_t fused_max_n = 64;
   int split_policy = 0;
-  int fused_kernel = 1;     // fused form: 0 = A staged in shared memory, 1 = A in TMEM
+  int fused_kernel = 0;     // fused form: 0 = A staged in shared memory, 1 = A in TMEM
 };
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d,
                      const MixedTune& tune = MixedTune());

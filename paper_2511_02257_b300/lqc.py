@@ -110,6 +110,7 @@ _sig("lqc_dag_prepare", ctypes.c_int, [c_vp, c_vp])
 _sig("lqc_test_inject_failure", ctypes.c_int, [ctypes.c_int, c_i64])
 _sig("lqc_test_expire_wait", ctypes.c_int, [c_i64, c_vp])
 _sig("lqc_test_tamper_plan", ctypes.c_int, [c_vp, ctypes.c_int])
+_sig("lqc_test_tf32_rounding", ctypes.c_int, [c_i64, ctypes.c_uint32, P_i64])
 _sig("lqc_dag_wait", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_autotune", ctypes.c_int, [c_vp, c_vp, ctypes.c_int, ctypes.POINTER(lqc_tune_entry),
                                         c_i64, P_i64])
@@ -155,7 +156,7 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_ad
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
            "lqc_contract_all_c64", "lqc_mixed_error", "lqc_contract_all_c64_scratch_bytes",
            "lqc_dag_prepare", "lqc_test_inject_failure", "lqc_test_expire_wait",
-           "lqc_test_tamper_plan"):
+           "lqc_test_tamper_plan", "lqc_test_tf32_rounding"):
     globals()[_n] = getattr(_lib, _n)
 
 

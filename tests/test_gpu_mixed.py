@@ -371,3 +371,11 @@ def test_fused_kernels_agree_on_a_dag():
         assert L.lqc_mixed_error(1) == 0
         worst[kernel] = max(rel_err(vals[r], ref[r]) for r in ref)
     assert max(worst.values()) < TOL_TF32X3, worst
+
+
+def test_tf32_rounding_equals_the_hardware_conversion():
+    """The converters' integer TF32 rounding against cvt.rna.tf32.f32 on
+    2^26 hashed float patterns (every binade, exact ties first)."""
+    bad = ctypes.c_int64(-1)
+    assert L.lqc_test_tf32_rounding(1 << 26, 12345, ctypes.byref(bad)) == 0
+    assert bad.value == 0

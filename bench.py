@@ -57,10 +57,19 @@ sys.path.insert(0, HERE)
 # DRAM bytes per launch of the fused split-3 GEMM from an ncu capture, with
 # the hash of the kernel source it was taken on (None until captured: the
 # figure is reported only while the source is unchanged).
-GEMM_TRAFFIC = None   # {"bytes_per_flop": x, "source_sha16": "...", "note": "..."}
+GEMM_TRAFFIC = {
+    "bytes_per_flop": 62.40e9 / 5.099e12, "source_sha16": "66ee201e860bd7df",
+    "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 24 grouped fused-GEMM "
+            "launches of one step of the batched workload with 8 parts (39.35 + 23.05 GB for "
+            "5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + output bytes), "
+            "scaled by the flops of a launch of this run"}
 # DRAM bytes per launch of the dominant FP64 kernel (k_contract_fp64<4,4>),
 # same convention.
-FP64_TRAFFIC = None
+FP64_TRAFFIC = {
+    "bytes_per_launch": 97.88e6, "source_sha16": "fffc41101ef2c194",
+    "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 239 launches of "
+            "k_contract_fp64<4,4> (the instantiation with the largest share of K1 time) in "
+            "one step of the multi-meson workload"}
 
 
 def parse():
@@ -72,6 +81,8 @@ def parse():
     ap.add_argument("--ref-seconds", type=float, default=8.0,
                     help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--workload", default="batched")
+    ap.add_argument("--workload-kw", default="{}",
+                    help="JSON overrides of the workload generator (smaller cases for profiling)")
     ap.add_argument("--policy", default="tree")
     ap.add_argument("--evict", default="lru")
     ap.add_argument("--precision", default="tf32x3")
@@ -604,7 +615,8 @@ def main():
     from paper_2511_02257_b300.roofline import FP64_NOMINAL_TFLOPS, dag_roofline_for
     sharded = args.shard == "lt" and ws > 1
     shard = (rank, ws) if sharded else None
-    wl = synth.make_workload(args.workload, seed=0 if sharded else rank)
+    wl = synth.make_workload(args.workload, seed=0 if sharded else rank,
+                             **json.loads(args.workload_kw))
     t_lo, t_hi = SH.lt_slices(wl.lt, ws)[rank] if sharded else (0, wl.lt)
     lt_share = (t_hi - t_lo) / wl.lt
     budget = SH.shard_budget(wl.budget_bytes, wl.lt, t_hi - t_lo) if sharded else \
@@ -681,7 +693,9 @@ def main():
                                    "chains, this run); nominal %.2f" % FP64_NOMINAL_TFLOPS,
                     "frac_of_nominal": ach / FP64_NOMINAL_TFLOPS if ach else None,
                     "launches": n_c, "kernel_ms_per_step": ms_c / args.steps,
-                    "traffic": traffic}
+                    "traffic": traffic,
+                    "traffic_note": FP64_TRAFFIC["note"] if traffic else
+                    "no ncu DRAM capture of this kernel source"}
 
     # ---- host link
     link = link_bandwidth()

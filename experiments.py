@@ -637,6 +637,9 @@ def main():
     del leaves
     stream = torch.cuda.current_stream().cuda_stream
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, args.graph)
+    from bench import link_bandwidth
+    args.link = link_bandwidth()
+    print(json.dumps({"host_link": args.link}), flush=True)
     for budget in budgets:
         _compare_policies(args, wl, nd, budget, stream, t_gen)
 
@@ -683,6 +686,15 @@ def _compare_policies(args, wl, nd, budget, stream, t_gen):
             "host_arena_gib": info["host_arena_bytes"] / 2 ** 30,
             "time_to_solution_s": min(times), "tflops": info["flops"] / min(times) / 1e12,
             "correlators_bit_identical_to_first_policy": same,
+            "arena_within_budget": info["arena_bytes"] <= budget,
+            "extra_placement_moves": {k: info[k] for k in ("extra_evictions", "extra_h2d_bytes",
+                                                            "extra_d2h_bytes")},
+            # host link: copies of both directions overlap (full duplex), so the
+            # bound is the slower direction's copy time at the measured bandwidth
+            "link_bound_s": max(info["copied_h2d"] / (args.link["h2d_gbs"] * 1e9),
+                                info["copied_d2h"] / (args.link["d2h_gbs"] * 1e9)),
+            "link_frac": max(info["copied_h2d"] / (args.link["h2d_gbs"] * 1e9),
+                             info["copied_d2h"] / (args.link["d2h_gbs"] * 1e9)) / min(times),
             "leaf_generation_s": t_gen,
         }
         rows.append(row)

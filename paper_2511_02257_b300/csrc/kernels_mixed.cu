@@ -54,7 +54,7 @@ namespace {
 constexpr int kBM = 128;        // UMMA M (rows of A' per CTA)
 constexpr int kBN = 128;        // UMMA N (real columns of D' per CTA)
 constexpr int kStages = 3;
-constexpr int kTmemCols = 4 * kBN;  // 2 buffers x (main + correction accumulator)
+constexpr int kTmemCols = 4 * kBN;  // 2 main accumulators (per chunk) + 2 correction (per tile)
 constexpr int64_t kMaxChunk = 1024;  // real k summed in FP32 registers before an FP64 sum
 constexpr int kDrainWarps = 8;  // two per TMEM lane quarter, one per column half
 constexpr int kConvWarps = 6;   // fused form: raw complex64 tiles -> hi/lo operand tiles
@@ -361,7 +361,8 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
   uint64_t* done = tempty + 2;         // every MMA issued has completed
   uint64_t* rfull = done + 1;          // FUSED [R] raw stage landed
   uint64_t* rempty = rfull + R;        // FUSED [R] raw stage converted
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + R);
+  uint64_t* cempty = rempty + R;       // [2] correction accumulator of a tile drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* stage_out = reinterpret_cast<float*>(raw + R * C::kRawBytes + 256);
 
@@ -379,6 +380,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kDrainWarps);
+      mbar_init(&cempty[b], kDrainWarps);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -459,11 +461,18 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     if (lane == 0) {
       // ---- MMA issuer
       constexpr uint32_t idesc = make_idesc<BF16>();
-      int g = 0, cc = 0, k = 0, local = 0;  // k-blocks and accumulation chunks walked
+      int g = 0, cc = 0, tt = 0, k = 0, local = 0;  // k-blocks, chunks, tiles walked
       bool stop = false;
-      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x, ++tt) {
         const GemmTask* tk = tile_task(gp, tile, k, local);
         const int kblocks = tk->kblocks;
+        // the tile's correction accumulator: free once the drain warps have
+        // read the one of tile tt - 2
+        if (!mbar_wait(&cempty[tt & 1], ((uint32_t)(tt >> 1) & 1u) ^ 1u) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t dcorr = tmem + (uint32_t)((2 + (tt & 1)) * kBN);
         for (int i = 0; i < kblocks; ++i, ++g) {
           const int b = cc & 1;
           const bool first = (i % kChunkBlocks) == 0;
@@ -487,12 +496,13 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           const uint32_t base = smem_u32(smem + st * C::kStageBytes);
           const uint32_t ahi = base, alo = base + C::kATile;
           const uint32_t bhi = base + 2 * C::kATile, blo = bhi + C::kBTile;
-          const uint32_t dmain = tmem + (uint32_t)(b * 2 * kBN), dcorr = dmain + kBN;
+          const uint32_t dmain = tmem + (uint32_t)(b * kBN);
 #pragma unroll
           for (int kk = 0; kk < 128 / 32; ++kk) {  // 32-byte k-steps inside the 128-byte row
             const uint32_t off = kk * 32;
-            const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
-            umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, acc0);
+            const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;     // main: fresh per chunk
+            const uint32_t accc = (i > 0 || kk > 0) ? 1u : 0u;      // correction: per tile
+            umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, accc);
             umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
             umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
           }
@@ -511,8 +521,8 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     const int q = warp & 3;          // TMEM lane quarter of this warp
     const int c0 = ((warp - 2) >> 2) * kHalf;  // first column of this warp's half
     const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-    int cc = 0, ok = 1, k = 0, local = 0;
-    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+    int cc = 0, tt = 0, ok = 1, k = 0, local = 0;
+    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x, ++tt) {
       const GemmTask* tk = tile_task(gp, tile, k, local);
       const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
       const int z = local / (tk->ntn * tk->ntm);
@@ -534,18 +544,37 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tb = tmem + tlane + (uint32_t)(b * 2 * kBN);
+        // the chunk's main accumulator; after the tile's last chunk (whose
+        // commit covers every MMA of the tile) also its correction accumulator,
+        // which stays in TMEM for the whole tile: its values are about 2^-11
+        // of the main ones, so its in-TMEM rounding is negligible
+        const bool last = c == chunks - 1;
+        const uint32_t tb = tmem + tlane + (uint32_t)(b * kBN);
+        const uint32_t tc = tmem + tlane + (uint32_t)((2 + (tt & 1)) * kBN);
 #pragma unroll
-        for (int j = 0; j < kHalf; j += 16) {
-          uint32_t r[16], rc[16];
-          tmem_ld16_pair(tb + j, tb + kBN + j, r, rc);  // collective: every lane loads
+        for (int j = 0; j < kHalf; j += 32) {
+          uint32_t r[16], r2[16];
+          tmem_ld16_pair(tb + j, tb + j + 16, r, r2);  // collective: every lane loads
 #pragma unroll
-          for (int u = 0; u < 16; ++u)
-            acc[j + u] += __uint_as_float(r[u]) + __uint_as_float(rc[u]);
+          for (int u = 0; u < 16; ++u) {
+            acc[j + u] += __uint_as_float(r[u]);
+            acc[j + 16 + u] += __uint_as_float(r2[u]);
+          }
+          if (last) {
+            tmem_ld16_pair(tc + j, tc + j + 16, r, r2);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              acc[j + u] += __uint_as_float(r[u]);
+              acc[j + 16 + u] += __uint_as_float(r2[u]);
+            }
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[b]);
+        if (lane == 0) {
+          mbar_arrive(&tempty[b]);
+          if (last) mbar_arrive(&cempty[tt & 1]);
+        }
       }
       if (ok) {  // warp-uniform: the staging below is collective
         // each thread holds one row of the tile; 16 columns at a time go

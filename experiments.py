@@ -81,6 +81,14 @@ SHAPES = {
     # both operand orders (M = N_dist, N = 16 N_dist and the transpose)
     "mxp": lambda n: ((n, n), (4, 4, n, n), (1,), (2,)),
     "pxm2": lambda n: ((4, 4, n, n), (n, n), (2,), (1,)),
+    # meson x baryon over one baryon leg (last, first, middle): M = N_dist rows
+    "mxb_t": lambda n: ((n, n), (n, n, n), (1,), (2,)),
+    "mxb_h": lambda n: ((n, n), (n, n, n), (1,), (0,)),
+    "mxb_m": lambda n: ((n, n), (n, n, n), (1,), (1,)),
+    # baryon x meson over one baryon leg (first, middle, last): M = N_dist^2 rows
+    "bxm_h": lambda n: ((n, n, n), (n, n), (0,), (0,)),
+    "bxm_m": lambda n: ((n, n, n), (n, n), (1,), (0,)),
+    "bxm_t": lambda n: ((n, n, n), (n, n), (2,), (0,)),
 }
 
 

@@ -283,6 +283,10 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   const float2* a_raw;
   long long a_ts, a_rs;
   int kc;
+  int a_mn;             // fused form: A's raw tile is [16 complex k][128 rows] (rows
+                        // unit-stride), transposed by the converters
+  int out_t;            // D' row r, real column c -> out[((c / 2) * M + r) * 2 + (c & 1)]
+                        // of each slice: the transposed product of exchanged operands
 };
 
 struct GemmParams {
@@ -344,8 +348,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // two TMEM accumulator buffers (each 2*kBN columns: main + correction) keep
 // cycling across tiles and tasks, so a tile's store overlaps the next tile's
 // MMAs.  The drain warps empty a buffer every kChunkBlocks k-blocks into FP32
-// registers.
-template <bool BF16, bool FUSED>
+// registers.  AMN: the launch may hold [k][rows] A tiles (a second copy of the
+// converters' A loops, taken per task; without it the default loops alone).
+template <bool BF16, bool FUSED, bool AMN = false>
 __global__ void __launch_bounds__(GemmCfg<BF16, FUSED>::kThreads, 1)
 k_gemm_split3(const __grid_constant__ GemmParams gp) {
   using C = GemmCfg<BF16, FUSED>;
@@ -423,7 +428,10 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           if (FUSED) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
-            tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
+            if (tk->a_mn)  // [16 complex k rows][128 complex rows], unswizzled
+              tma_load_3d(rp, &tk->map[0], &rf[st], 2 * m0, k0 / 2, t);
+            else
+              tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
             if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
               int c[5], nd = 0, kk = k0 / 2;
               c[nd++] = n0 % (2 * tk->b_ni);
@@ -576,7 +584,22 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           if (last) mbar_arrive(&cempty[tt & 1]);
         }
       }
-      if (ok) {  // warp-uniform: the staging below is collective
+      if (ok && tk->out_t) {
+        // transposed store: this thread's row r is an output column, its
+        // column pairs (re, im) are output rows: for each pair the warp
+        // writes 32 consecutive complex values
+        if (row < M) {
+          float* base = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr;
+          const int col0 = tn * kBN + c0;
+#pragma unroll
+          for (int j = 0; j < kHalf; j += 2) {
+            const int col = col0 + j;
+            if (col < Nr)
+              *reinterpret_cast<float2*>(base + ((size_t)(col >> 1) * M + row) * 2) =
+                  make_float2(acc[j], acc[j + 1]);
+          }
+        }
+      } else if (ok) {  // warp-uniform: the staging below is collective
         // each thread holds one row of the tile; 16 columns at a time go
         // through this warp's shared-memory pitch so that a store covers 8 rows
         // x 64 contiguous bytes instead of 32 rows x 16 bytes
@@ -642,10 +665,28 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         constexpr int kUB = ((kBN / 2) * 8 + kCT - 1) / kCT;  // B units per thread
         static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
         float4 va[kUA], vb[kUB];
+        // A unit c: K-major tiles: the 16-byte chunk c, written to the same
+        // place; [k][rows] tiles: row c % 128, complex k pair c / 128 (lanes
+        // on consecutive rows: contiguous loads, and the swizzled stores of a
+        // quarter warp fall on 8 distinct chunk positions)
+        const bool amn = AMN && tk->a_mn != 0;
+        const float2* ra = reinterpret_cast<const float2*>(rp);
+        if (amn) {  // warp-uniform (one task per tile): two copies of the loop
 #pragma unroll
-        for (int j = 0; j < kUA; ++j) {
-          const int c = ct + j * kCT;
-          if (c < C::kRawA / 16) va[j] = *reinterpret_cast<const float4*>(rp + 16 * c);
+          for (int j = 0; j < kUA; ++j) {
+            const int c = ct + j * kCT;
+            if (c < C::kRawA / 16) {
+              const int n = c & (kBM - 1), kc2 = c / kBM;
+              const float2 v0 = ra[(2 * kc2) * kBM + n], v1 = ra[(2 * kc2 + 1) * kBM + n];
+              va[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < kUA; ++j) {
+            const int c = ct + j * kCT;
+            if (c < C::kRawA / 16) va[j] = *reinterpret_cast<const float4*>(rp + 16 * c);
+          }
         }
         // B unit it -> (column n, chunk c).  [k][n] tiles: a warp takes 16
         // consecutive n at two chunks c, c ^ 1 (each half-warp reads 128
@@ -685,19 +726,33 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
-        // A: same 128-byte-swizzled layout in and out, element by element
-#pragma unroll
-        for (int j = 0; j < kUA; ++j) {
-          const int c = ct + j * kCT;
-          if (c >= C::kRawA / 16) continue;
+        // A: K-major tiles keep their 128-byte-swizzled layout, element by
+        // element; [k][rows] tiles go to row n, chunk kc2 ^ (n & 7)
+        auto split_a = [&](int j, int o) {
           const float4 v = va[j];
           float h0, l0, h1, l1, h2, l2, h3, l3;
           Split<false>::split(v.x, h0, l0);
           Split<false>::split(v.y, h1, l1);
           Split<false>::split(v.z, h2, l2);
           Split<false>::split(v.w, h3, l3);
-          *reinterpret_cast<float4*>(sp + 16 * c) = make_float4(h0, h1, h2, h3);
-          *reinterpret_cast<float4*>(sp + C::kATile + 16 * c) = make_float4(l0, l1, l2, l3);
+          *reinterpret_cast<float4*>(sp + o) = make_float4(h0, h1, h2, h3);
+          *reinterpret_cast<float4*>(sp + C::kATile + o) = make_float4(l0, l1, l2, l3);
+        };
+        if (amn) {
+#pragma unroll
+          for (int j = 0; j < kUA; ++j) {
+            const int c = ct + j * kCT;
+            if (c >= C::kRawA / 16) continue;
+            const int n = c & (kBM - 1), kc2 = c / kBM;
+            split_a(j, n * 128 + 16 * (kc2 ^ (n & 7)));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < kUA; ++j) {
+            const int c = ct + j * kCT;
+            if (c >= C::kRawA / 16) continue;
+            split_a(j, 16 * c);
+          }
         }
         // B: complex column n -> B' rows 2n (re, -im) and 2n+1 (im, re); the
         // 16-byte chunk c (complex k 2c, 2c+1) of row r sits at chunk
@@ -1296,6 +1351,15 @@ __device__ __forceinline__ void df_acc_prod(float& sh, float& sl, float a, float
   sh = t;
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
+// (h, l) += (h2, l2) for double-float values: Knuth's TwoSum of the high
+// parts, the low parts and the rounding error added to the low part
+__device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
+  const float t = __fadd_rn(h, h2);
+  const float bp = __fsub_rn(t, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(h2, bp));
+  h = t;
+  l = __fadd_rn(l, __fadd_rn(err, l2));
+}
 // ------------------------------------------------------------ permute
 // A PermDesc maps every element e of a destination order (row-major over its
 // axes) to a source offset.  Two block shapes move it with coalesced reads
@@ -1483,19 +1547,33 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
       }
     }
   }
-  double re = (double)rh + (double)rl, im = (double)ih + (double)il;
+  // block sum in double-float as well (FP32 shuffles and TwoSum adds; B300
+  // issues FP64 at a small fraction of the FP32 rate), FP64 once per block
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_down_sync(0xffffffffu, re, o);
-    im += __shfl_down_sync(0xffffffffu, im, o);
+    const float h1 = __shfl_down_sync(0xffffffffu, rh, o), l1 = __shfl_down_sync(0xffffffffu, rl, o);
+    const float h2 = __shfl_down_sync(0xffffffffu, ih, o), l2 = __shfl_down_sync(0xffffffffu, il, o);
+    df_add(rh, rl, h1, l1);
+    df_add(ih, il, h2, l2);
   }
-  __shared__ double2 w[8];
-  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_double2(re, im);
+  __shared__ float4 w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_float4(rh, rl, ih, il);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 s = w[0];
-    for (int k = 1; k < 8; ++k) { s.x += w[k].x; s.y += w[k].y; }
-    part[t * d.blocks + b] = s;
+  if (threadIdx.x < 32) {
+    const float4 v = threadIdx.x < 8 ? w[threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+    rh = v.x;
+    rl = v.y;
+    ih = v.z;
+    il = v.w;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const float h1 = __shfl_down_sync(0xffffffffu, rh, o), l1 = __shfl_down_sync(0xffffffffu, rl, o);
+      const float h2 = __shfl_down_sync(0xffffffffu, ih, o), l2 = __shfl_down_sync(0xffffffffu, il, o);
+      df_add(rh, rl, h1, l1);
+      df_add(ih, il, h2, l2);
+    }
+    if (threadIdx.x == 0)
+      part[t * d.blocks + b] = make_double2((double)rh + (double)rl, (double)ih + (double)il);
   }
 }
 
@@ -1676,13 +1754,15 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // [lt][K rows][n2 floats] (n unit-stride), boxes of kBN floats (kBN/2
 // complex n) x 16 rows (complex k), unswizzled: the raw tile of a right
 // operand stored [k][n]
+// operand stored [k][n] (box_w = kBN), or of a left operand stored [k][rows]
+// (box_w = 2 * kBM floats: 128 complex rows)
 bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows, int64_t lt,
-                     int64_t row_stride, int64_t slice_stride) {
+                     int64_t row_stride, int64_t slice_stride, int box_w = kBN) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)n2, (cuuint64_t)krows, (cuuint64_t)lt};
   cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 8), (cuuint64_t)(slice_stride * 8)};
-  cuuint32_t box[3] = {(cuuint32_t)kBN, 16u, 1u};
+  cuuint32_t box[3] = {(cuuint32_t)box_w, 16u, 1u};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1768,8 +1848,58 @@ int64_t choose_splits(const ContractDesc& cd, int64_t kblocks, int64_t bk, int p
 }
 }  // namespace
 
+namespace {
+// the same contraction with the operands exchanged: C^T[n][m] = sum_k
+// B[k][n] A[m][k] (pairs keep their order, so k runs alike)
+ContractDesc exchanged(const ContractDesc& cd) {
+  ContractDesc x = cd;
+  x.M = cd.N;
+  x.N = cd.M;
+  x.a_ts = cd.b_ts;
+  x.b_ts = cd.a_ts;
+  x.am = cd.bn;
+  x.ak = cd.bk;
+  x.bk = cd.ak;
+  x.bn = cd.am;
+  x.a_kfast = cd.b_kfast;
+  x.b_kfast = cd.a_kfast;
+  return x;
+}
+int64_t gemm_tiles(const ContractDesc& cd) {
+  return ((cd.M + kBM - 1) / kBM) * ((2 * cd.N + kBN - 1) / kBN) * cd.lt;
+}
+// fused form of cd with both operands read in place (no reorder)?
+bool fused_in_place(const ContractDesc& cd, int split_policy, MixedDesc* x) {
+  std::memset(x, 0, sizeof(*x));
+  x->cd = cd;
+  x->fused = true;
+  return make_fused_desc(cd, x, split_policy) && x->a_direct && x->b_direct;
+}
+}  // namespace
+
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const MixedTune& tune) {
   std::memset(d, 0, sizeof(*d));
+  // Orientation: a product with fewer rows than a tile (M < 128, e.g. a meson
+  // times a baryon over one leg: 64 x 4096) fills half of every 128-row MMA;
+  // its transpose (4096 x 64) does not.  The exchanged product is taken when
+  // it needs at least a quarter fewer 128 x 64-complex tiles, or no more
+  // tiles and no operand reorder where the given orientation needs one; it
+  // is stored transposed by the GEMM's epilogue (shared-memory-A kernel).
+  if (!bf16 && cd.K % 2 == 0 && tune.fused_kernel == 0 && cd.M <= tune.fused_max_n) {
+    MixedDesc x, y;
+    const ContractDesc sw = exchanged(cd);
+    if (fused_in_place(sw, tune.split_policy, &x)) {
+      const int64_t t0 = gemm_tiles(cd), t1 = gemm_tiles(sw);
+      const bool normal_in_place =
+          cd.N <= tune.fused_max_n && fused_in_place(cd, tune.split_policy, &y);
+      if (4 * t1 <= 3 * t0 || (t1 <= t0 && !normal_in_place)) {
+        *d = x;
+        d->swap = true;
+        return true;
+      }
+    }
+    std::memset(d, 0, sizeof(*d));
+  }
   d->bf16 = bf16;
   d->cd = cd;
   // fused form: TF32 with an even paired extent (16-byte complex64 rows) and
@@ -1859,6 +1989,16 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
     d->b_direct = true;
     d->b_rowstride = cd.bk.stride[0];
   }
+  // A stored [k][rows] with the rows unit-stride (a tensor contracted over
+  // its leading axis): read in place, k rows of 16-byte multiples, transposed
+  // by the converters (the shared-memory-A kernel only)
+  d->a_mn = !d->tmem_a && !d->a_direct && !cd.a_kfast && cd.am.n == 1 &&
+            cd.am.stride[0] == 1 && cd.ak.n == 1 && cd.ak.stride[0] % 2 == 0 &&
+            cd.a_ts % 2 == 0;
+  if (d->a_mn) {
+    d->a_direct = true;
+    d->a_rowstride = cd.ak.stride[0];
+  }
   int64_t off = 0;
   d->a_off = off;
   if (!d->a_direct) {
@@ -1915,7 +2055,10 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const void* b = d.b_direct ? (const void*)B : (const void*)bs;
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
-    if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) return false;
+    if (d.a_mn ? !make_raw_map_mn(&t->map[0], a, 2 * cd.M, cd.K, cd.lt, d.a_rowstride, ats, 2 * kBM)
+               : !make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM))
+      return false;
+    t->a_mn = d.a_mn ? 1 : 0;
     if (d.b_mn2) {
       if (!make_raw_map_mnx(&t->map[2], b, cd.bn, cd.bk, cd.lt, bts, t)) return false;
     } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
@@ -1942,6 +2085,7 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
   t->ntm = (t->M + kBM - 1) / kBM;
   t->tiles = t->ntn * t->ntm * t->lt * t->splits;
   t->out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
+  t->out_t = d.swap ? 1 : 0;
   return true;
 }
 
@@ -1961,23 +2105,25 @@ int launch_fused_copies(const MixedDesc& d, const float* A, const float* B, void
   return nk;
 }
 
-template <bool BF16, bool FUSED>
+template <bool BF16, bool FUSED, bool AMN = false>
 void launch_gemm_t(const GemmParams& gp, dim3 grid, cudaStream_t s) {
   using C = GemmCfg<BF16, FUSED>;
-  cudaFuncSetAttribute(k_gemm_split3<BF16, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       C::kSmem);
-  k_gemm_split3<BF16, FUSED><<<grid, C::kThreads, C::kSmem, s>>>(gp);
+  cudaFuncSetAttribute(k_gemm_split3<BF16, FUSED, AMN>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  k_gemm_split3<BF16, FUSED, AMN><<<grid, C::kThreads, C::kSmem, s>>>(gp);
 }
 
+// amn: some fused task of the launch reads A as [k][rows] tiles
 int launch_gemm(const GemmParams& gp, bool bf16, bool fused, cudaStream_t s,
-                bool tmem_a = false) {
+                bool tmem_a = false, bool amn = false) {
   if (gp.total_tiles <= 0) return 0;
   dim3 grid((unsigned)std::min<long long>(gp.total_tiles, num_sms()));
   if (fused && tmem_a) {
     cudaFuncSetAttribute(k_gemm_tf32_tmem_a, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TaCfg::kSmem);
     k_gemm_tf32_tmem_a<<<grid, TaCfg::kThreads, TaCfg::kSmem, s>>>(gp);
-  } else if (fused) launch_gemm_t<false, true>(gp, grid, s);
+  } else if (fused && amn) launch_gemm_t<false, true, true>(gp, grid, s);
+  else if (fused) launch_gemm_t<false, true>(gp, grid, s);
   else if (bf16) launch_gemm_t<true, false>(gp, grid, s);
   else launch_gemm_t<false, false>(gp, grid, s);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
@@ -1987,13 +2133,14 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
                           void* scratch, cudaStream_t s) {
   const ContractDesc& cd = d.cd;
   if (d.fused) {
+    if (d.swap) std::swap(A, B);  // the GEMM's left operand is the contraction's right one
     int nk = launch_fused_copies(d, A, B, scratch, s);
     if (nk < 0) return -1;
     GemmParams gp;
     std::memset(&gp, 0, sizeof(gp));
     if (!fill_gemm_task(d, A, B, scratch, C, &gp.single, nullptr, nullptr)) return -2;
     gp.total_tiles = gp.single.tiles;
-    if (launch_gemm(gp, false, true, s, d.tmem_a) < 0) return -1;
+    if (launch_gemm(gp, false, true, s, d.tmem_a, d.a_mn) < 0) return -1;
     ++nk;
     if (d.splits > 1) {
       const long long per = cd.lt * cd.M * 2 * cd.N;
@@ -2192,7 +2339,7 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   std::vector<PermTask> pm;
   std::vector<GemmTask> gf;  // fused-form GEMM tasks
   long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0, ftiles = 0;
-  bool lvl_tmem_a = false;
+  bool lvl_tmem_a = false, lvl_amn = false;
   auto add_perm = [&](const PermDesc& pd, const void* src, void* dst) {
     PermTask t;
     std::memset(&t, 0, sizeof(t));
@@ -2240,17 +2387,21 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     const char* bs = nullptr;
     bool fresh = false;
     if (d.fused) {
+      // operands in the GEMM's roles (exchanged for a transposed product)
+      const float* EA = d.swap ? e.B : e.A;
+      const float* EB = d.swap ? e.A : e.B;
       if (!d.a_direct) {
-        as = stage(key_of(e.A, &d.a_perm, sizeof(PermDesc), 0), sc + d.a_off, &fresh);
-        if (fresh) add_perm(d.a_perm, e.A, sc + d.a_off);
+        as = stage(key_of(EA, &d.a_perm, sizeof(PermDesc), 0), sc + d.a_off, &fresh);
+        if (fresh) add_perm(d.a_perm, EA, sc + d.a_off);
       }
       if (!d.b_direct) {
-        bs = stage(key_of(e.B, &d.b_perm, sizeof(PermDesc), 0), sc + d.b_off, &fresh);
-        if (fresh) add_perm(d.b_perm, e.B, sc + d.b_off);
+        bs = stage(key_of(EB, &d.b_perm, sizeof(PermDesc), 0), sc + d.b_off, &fresh);
+        if (fresh) add_perm(d.b_perm, EB, sc + d.b_off);
       }
       GemmTask g;
-      if (!fill_gemm_task(d, e.A, e.B, e.scratch, e.C, &g, as, bs)) return false;
+      if (!fill_gemm_task(d, EA, EB, e.scratch, e.C, &g, as, bs)) return false;
       lvl_tmem_a = d.tmem_a;  // one DAG option: every fused task of a level alike
+      lvl_amn = lvl_amn || d.a_mn;
       g.tile_start = ftiles;
       ftiles += g.tiles;
       gf.push_back(g);
@@ -2318,6 +2469,7 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->ngemm_fused = (int)gf.size();
   lvl->gemm_fused_tiles = ftiles;
   lvl->fused_tmem_a = lvl_tmem_a;
+  lvl->fused_amn = lvl_amn;
   lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
   lvl->nred = (int)rd.size();
   lvl->red_blocks = rb;
@@ -2401,7 +2553,7 @@ int launch_level(const LevelDev& L, cudaStream_t s, cudaEvent_t* marks, unsigned
     gp.ntasks = L.ngemm_fused;
     gp.total_tiles = L.gemm_fused_tiles;
     mark();
-    if (launch_gemm(gp, false, true, s, L.fused_tmem_a) < 0) return -1;
+    if (launch_gemm(gp, false, true, s, L.fused_tmem_a, L.fused_amn) < 0) return -1;
     ++nk;
   }
   if (L.nred > 0) {

@@ -50,7 +50,12 @@ struct MixedDesc {
   bool a_direct, b_direct;
   bool b_mn;                // B read in place as [k][n]; the GEMM's converters transpose it
   bool b_mn2;               // ... as [k][outer n][inner n] blocks (4-d map)
-  int64_t a_rowstride, b_rowstride;  // complex elements between operand rows
+  bool a_mn;                // A read in place as [k][rows] (rows unit-stride); transposed by
+                            // the converters
+  bool swap;                // operands exchanged: the GEMM computes C^T = B^T A^T (its rows
+                            // are C's columns) and stores it transposed; cd describes the
+                            // exchanged roles
+  int64_t a_rowstride, b_rowstride;  // complex elements between operand rows (a_mn: k rows)
   PermDesc a_perm, b_perm;
   bool tmem_a;              // fused form: A split by converter warps into tensor memory
 };
@@ -118,6 +123,7 @@ struct LevelDev {
   int ngemm_fused;
   long long gemm_fused_tiles;
   bool fused_tmem_a;        // the fused tasks run the A-in-tensor-memory kernel
+  bool fused_amn;           // ... and some reads A as [k][rows] tiles
   const void* red;
   const long long* red_starts;
   int nred;

@@ -89,6 +89,15 @@ CASES = [
     ((200, 300), (300, 150), (1,), (0,)),
     ((16, 16, 16), (16, 16, 16), (1, 2), (0, 1)),   # long k: split over k
     ((40, 1100), (1100, 40), (1,), (0,)),              # k not a multiple of the tile
+    # fewer rows than a tile: the exchanged product, stored transposed, with
+    # the right operand K-major, or [k][n] (transposed by the converters),
+    # or [k][n] with k split over partial sums
+    ((13, 18), (10, 14, 18), (1,), (2,)),
+    ((13, 18), (18, 10, 14), (1,), (0,)),
+    ((8, 1100), (1100, 300), (1,), (0,)),
+    # left operand [k][rows] read in place (a baryon over its first leg)
+    ((24, 24, 24), (24, 24), (0,), (0,)),
+    ((18, 130), (18, 40), (0,), (0,)),
 ]
 
 

@@ -689,16 +689,18 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           }
         }
         // B unit it -> (column n, chunk c).  [k][n] tiles: a warp takes 16
-        // consecutive n at two chunks c, c ^ 1 (each half-warp reads 128
-        // contiguous bytes; the B' rows' swizzled writes cover all 8 chunk
-        // positions): n = [3:0] + 16*[6:5], c = 2*[8:7] + [4].  K-major tiles:
+        // consecutive n at two chunks c, c ^ 1, a quarter warp four n at one
+        // chunk and the next four at the other, so that a half warp's loads
+        // fall on 16 distinct bank pairs and a quarter warp's swizzled B'
+        // stores on 8 distinct chunk positions (no bank conflicts):
+        // n = [3:0] + 16*[6:5], c = 2*[8:7] + ([2] ^ [4]).  K-major tiles:
         // n = it / 8, c = it % 8.
         const bool bmn = tk->b_mn != 0;  // [k][n] raw tile (3-d or 4-d map alike)
         const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
         auto unit = [&](int it, int& n, int& c) {
           if (bmn) {
             n = (it & 15) + 16 * ((it >> 5) & 3);
-            c = 2 * (it >> 7) + ((it >> 4) & 1);
+            c = 2 * (it >> 7) + (((it >> 2) ^ (it >> 4)) & 1);
           } else {
             n = it >> 3;
             c = it & 7;
@@ -1150,7 +1152,8 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
         const float2* rb = reinterpret_cast<const float2*>(rp);
         float4 vb[kUB];
         // unit it -> (column n, chunk c): [k][n] tiles: a warp takes 16
-        // consecutive n at two chunks c, c ^ 1; K-major tiles: n = it / 8
+        // consecutive n at two chunks c, c ^ 1, alternating every four lanes
+        // (conflict-free loads and stores); K-major tiles: n = it / 8
 #pragma unroll
         for (int j = 0; j < kUB; ++j) {
           const int it = ct + j * kCT;
@@ -1158,7 +1161,7 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
             int n, c;
             if (bmn) {
               n = (it & 15) + 16 * ((it >> 5) & 3);
-              c = 2 * (it >> 7) + ((it >> 4) & 1);
+              c = 2 * (it >> 7) + (((it >> 2) ^ (it >> 4)) & 1);
               const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
               vb[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
             } else {
@@ -1185,7 +1188,7 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
           int n, c;
           if (bmn) {
             n = (it & 15) + 16 * ((it >> 5) & 3);
-            c = 2 * (it >> 7) + ((it >> 4) & 1);
+            c = 2 * (it >> 7) + (((it >> 2) ^ (it >> 4)) & 1);
           } else {
             n = it >> 3;
             c = it & 7;

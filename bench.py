@@ -97,6 +97,9 @@ def parse():
                     help="with --autotune 0: LQC_OPT_FUSED_MAX_N of the mixed path")
     ap.add_argument("--split-policy", type=int, default=1,
                     help="with --autotune 0: LQC_OPT_SPLIT_POLICY of the mixed path")
+    ap.add_argument("--fused-kernel", type=int, default=2,
+                    help="LQC_OPT_FUSED_KERNEL of the mixed path (0: one CTA per tile, "
+                         "1: A in tensor memory, 2: CTA pairs on 256-row tiles)")
     ap.add_argument("--fp64-arm", type=int, default=1,
                     help="executions of the FP64 path on the same DAG (0: skip)")
     ap.add_argument("--sub", default="memory_pressure,baryon",
@@ -365,6 +368,7 @@ def set_mixed_options(L, nd, args):
     nd.set_option(L.LQC_OPT_WINDOW, args.window)
     nd.set_option(L.LQC_OPT_FUSED_MAX_N, args.fused_max_n)
     nd.set_option(L.LQC_OPT_SPLIT_POLICY, args.split_policy)
+    nd.set_option(L.LQC_OPT_FUSED_KERNEL, args.fused_kernel)
 
 
 def autotune(nd, stream, reps=1):
@@ -501,7 +505,8 @@ def mixed_form(L, wl, leaves, args, precision, policy, budget, stream, steps, wa
            "options": {"window": tuned["best"]["window"] if tuned else args.window,
                        "fused_max_n": tuned["best"]["fused_max_n"] if tuned else args.fused_max_n,
                        "split_policy": tuned["best"]["split_policy"] if tuned
-                       else args.split_policy, "cuda_graph": bool(args.graph)},
+                       else args.split_policy, "cuda_graph": bool(args.graph),
+                       "fused_kernel": args.fused_kernel},
            "peak_paper_bytes": planned["peak_paper"], "peak_exec_bytes": planned["peak_exec"],
            "n_evict": planned["n_evict"], "h2d_bytes_planned": planned["h2d_bytes"],
            "d2h_bytes_planned": planned["d2h_bytes"],
@@ -796,6 +801,7 @@ def main():
                                        else args.fused_max_n) if mixed else None,
                        "split_policy": (tuned["best"]["split_policy"] if tuned
                                         else args.split_policy) if mixed else None,
+                       "fused_kernel": args.fused_kernel if mixed else None,
                        "autotune": tuned,
                        "parallelism": ("lt-shard" if sharded else "replicas") if ws > 1
                                       else "single",

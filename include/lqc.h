@@ -187,7 +187,12 @@ typedef enum {
                              hi/lo parts into tensor memory and the MMAs read
                              A there (B from shared memory): the correction
                              products of a k block go first into a fresh
-                             accumulator, then hi*hi, drained every k block */
+                             accumulator, then hi*hi, drained every k block;
+                             2 = as 0, and products of more than 128 rows run
+                             on CTA pairs (clusters of 2, cta_group::2 MMAs on
+                             256-row tiles, each CTA converting half of the B
+                             tile): the same arithmetic per output element,
+                             so the same bits as 0                          */
 } lqc_option;
 
 /* One autotuner candidate and its measured time per execute. */

@@ -387,7 +387,7 @@ int lqc_dag_set_option(lqc_dag* h, int option, int64_t value) {
       h->d.opt_split_policy = value;
       break;
     case LQC_OPT_FUSED_KERNEL:
-      if (value != 0 && value != 1) return fail(h, LQC_ERR_ARG, "fused kernel must be 0 or 1");
+      if (value < 0 || value > 2) return fail(h, LQC_ERR_ARG, "fused kernel must be 0, 1 or 2");
       h->d.opt_fused_kernel = value;
       break;
     default: return fail(h, LQC_ERR_ARG, "unknown option");

@@ -205,6 +205,44 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// ---- CTA pairs (cluster of 2, cta_group::2)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// arrive on the mbarrier at the same shared-memory offset in CTA 0 of the
+// pair.  The default (CTA-scope release) form: the converters' stores are
+// ordered for the tensor core by their fence.proxy.async before it; the
+// cluster-scope release form measured 26 % slower on 256^3 products.
+__device__ __forceinline__ void mbar_arrive_leader(uint64_t* bar) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(smem_u32(bar)));
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+// 2-SM MMA issued by CTA 0: A rows 0..127 from CTA 0's shared memory and
+// 128..255 from CTA 1's (same offsets), B' rows (output columns) split the
+// same way; D rows land in each CTA's own tensor memory
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+// arrive on the mbarrier at this offset in both CTAs once the pair's MMAs
+// issued so far have completed
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"((unsigned short)3)
+      : "memory");
+}
+
 // two 16-column TMEM loads in flight before one wait
 __device__ __forceinline__ void tmem_ld16_pair(uint32_t ta, uint32_t tb, uint32_t* r,
                                                uint32_t* s) {
@@ -315,16 +353,23 @@ __device__ __forceinline__ const GemmTask* tile_task(const GemmParams& gp, long 
 // converter warps write the hi/lo operand tiles (B' rows 2n / 2n+1 built from
 // complex row n) into the operand ring; otherwise the producer loads the
 // four precomputed planes directly into the operand ring.
-template <bool BF16, bool FUSED = false>
+// PAIR (fused form only): a CTA pair (cluster of 2) computes 256-row tiles
+// with cta_group::2 MMAs (M = 256, N = kBN): each CTA stages its own 128 A'
+// rows and half of the tile's B' rows (kBN / 2), so each B' tile is
+// converted once per pair instead of once per CTA, and the smaller stage
+// leaves room for a third operand stage.
+template <bool BF16, bool FUSED = false, bool PAIR = false>
 struct GemmCfg {
   static constexpr int kElem = BF16 ? 2 : 4;
   static constexpr int kBK = 128 / kElem;           // elements per 128-byte row
   static constexpr int kATile = kBM * 128;          // bytes of one A plane tile
-  static constexpr int kBTile = kBN * 128;
+  static constexpr int kBRows = PAIR ? kBN / 2 : kBN;  // B' rows staged by one CTA
+  static constexpr int kBTile = kBRows * 128;
+  static constexpr int kBCols = kBRows / 2;         // complex columns of B per CTA
   static constexpr int kStageBytes = 2 * kATile + 2 * kBTile;
-  static constexpr int kOpStages = FUSED ? 2 : kStages;
+  static constexpr int kOpStages = FUSED ? (PAIR ? 3 : 2) : kStages;
   static constexpr int kRawStages = FUSED ? 3 : 0;
-  static constexpr int kRawA = kBM * 128, kRawB = (kBN / 2) * 128;
+  static constexpr int kRawA = kBM * 128, kRawB = kBCols * 128;
   static constexpr int kRawBytes = kRawA + kRawB;
   static constexpr int kThreads = kGemmThreads + (FUSED ? 32 * kConvWarps : 0);
   // epilogue staging: per drain warp 32 rows x 16 columns, pitch 20 floats
@@ -350,10 +395,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // MMAs.  The drain warps empty a buffer every kChunkBlocks k-blocks into FP32
 // registers.  AMN: the launch may hold [k][rows] A tiles (a second copy of the
 // converters' A loops, taken per task; without it the default loops alone).
-template <bool BF16, bool FUSED, bool AMN = false>
+// PAIR: launched in clusters of 2; the pair walks 256-row tiles (pair p takes
+// tiles p, p + gridDim.x / 2, ...), CTA 0's thread issues the cta_group::2
+// MMAs, and the converter and drain warps of CTA 1 arrive on CTA 0's
+// barriers; the commits arrive in both CTAs.
+template <bool BF16, bool FUSED, bool AMN = false, bool PAIR = false>
 __global__ void __launch_bounds__(GemmCfg<BF16, FUSED>::kThreads, 1)
 k_gemm_split3(const __grid_constant__ GemmParams gp) {
-  using C = GemmCfg<BF16, FUSED>;
+  using C = GemmCfg<BF16, FUSED, PAIR>;
+  static_assert(!PAIR || (FUSED && !BF16), "CTA pairs: fused TF32 form only");
   constexpr int S = C::kOpStages, R = C::kRawStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -372,10 +422,16 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
   float* stage_out = reinterpret_cast<float*>(raw + R * C::kRawBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // tile walk: this CTA's (or pair's) first tile and stride; rank in the pair
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const long long tile0 = PAIR ? (long long)(blockIdx.x >> 1) : (long long)blockIdx.x;
+  const long long tstep = PAIR ? (long long)(gridDim.x >> 1) : (long long)gridDim.x;
+  constexpr int kTileRows = PAIR ? 2 * kBM : kBM;  // rows of a (pair) tile
+  constexpr int kPeers = PAIR ? 2 : 1;             // CTAs arriving on CTA 0's barriers
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
-      mbar_init(&full[i], FUSED ? kConvWarps : 1);
+      mbar_init(&full[i], FUSED ? kConvWarps * kPeers : 1);
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < R; ++i) {
@@ -384,21 +440,29 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kDrainWarps);
-      mbar_init(&cempty[b], kDrainWarps);
+      mbar_init(&tempty[b], kDrainWarps * kPeers);
+      mbar_init(&cempty[b], kDrainWarps * kPeers);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (PAIR) {  // one warp of each CTA of the pair, collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();  // both CTAs' barriers initialised
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -410,12 +474,15 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
       uint64_t* re = FUSED ? rempty : empty;
       int g = 0, issued = 0, k = 0, local = 0;
       bool stop = false;
-      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x) {
+      for (long long tile = tile0; tile < gp.total_tiles && !stop; tile += tstep) {
         const GemmTask* tk = tile_task(gp, tile, k, local);
         const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
         const int z = local / (tk->ntn * tk->ntm);
         const int t = z % tk->lt, split = z / tk->lt;
-        const int n0 = tn * kBN, m0 = tm * kBM, kb0 = split * tk->kblocks;
+        // this CTA's rows and B' columns (a pair: CTA r takes rows 128 r.. of
+        // the 256-row tile and B' columns kBN / 2 * r .. of its kBN)
+        const int n0 = tn * kBN + (int)rank * (kBN / 2), m0 = tm * kTileRows + (int)rank * kBM;
+        const int kb0 = split * tk->kblocks;
         for (int i = 0; i < tk->kblocks; ++i, ++g) {
           const int st = g % RS;
           const uint32_t ph = (uint32_t)(g / RS) & 1u;
@@ -466,12 +533,13 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         if (!mbar_wait(&rf[i % RS], (uint32_t)(i / RS) & 1u)) break;
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---- MMA issuer
-      constexpr uint32_t idesc = make_idesc<BF16>();
+    if (lane == 0 && rank == 0) {
+      // ---- MMA issuer (a pair: CTA 0's)
+      constexpr uint32_t idesc =
+          make_idesc<BF16>() + (PAIR ? ((uint32_t)(kBM >> 4) << 24) : 0u);  // M = 256
       int g = 0, cc = 0, tt = 0, k = 0, local = 0;  // k-blocks, chunks, tiles walked
       bool stop = false;
-      for (long long tile = blockIdx.x; tile < gp.total_tiles && !stop; tile += gridDim.x, ++tt) {
+      for (long long tile = tile0; tile < gp.total_tiles && !stop; tile += tstep, ++tt) {
         const GemmTask* tk = tile_task(gp, tile, k, local);
         const int kblocks = tk->kblocks;
         // the tile's correction accumulator: free once the drain warps have
@@ -510,18 +578,29 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             const uint32_t off = kk * 32;
             const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;     // main: fresh per chunk
             const uint32_t accc = (i > 0 || kk > 0) ? 1u : 0u;      // correction: per tile
-            umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, accc);
-            umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
-            umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+            if constexpr (PAIR) {
+              umma_pair(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, accc);
+              umma_pair(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+              umma_pair(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+            } else {
+              umma<BF16>(dcorr, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, accc);
+              umma<BF16>(dcorr, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+              umma<BF16>(dmain, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+            }
           }
-          umma_commit(&empty[st]);   // stage reusable once these MMAs have read it
+          // stage reusable once these MMAs have read it (a pair: in both CTAs)
+          if constexpr (PAIR) umma_commit_pair(&empty[st]);
+          else umma_commit(&empty[st]);
           if (last) {
-            umma_commit(&tfull[b]);
+            if constexpr (PAIR) umma_commit_pair(&tfull[b]);
+            else umma_commit(&tfull[b]);
             ++cc;
           }
         }
       }
-      umma_commit(done);             // all issued MMAs complete (or abandoned)
+      // all issued MMAs complete (or abandoned)
+      if constexpr (PAIR) umma_commit_pair(done);
+      else umma_commit(done);
     }
   } else if (warp < 2 + kDrainWarps) {
     // ---- drain / epilogue warps
@@ -530,14 +609,15 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     const int c0 = ((warp - 2) >> 2) * kHalf;  // first column of this warp's half
     const uint32_t tlane = ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
     int cc = 0, tt = 0, ok = 1, k = 0, local = 0;
-    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x, ++tt) {
+    for (long long tile = tile0; tile < gp.total_tiles && ok; tile += tstep, ++tt) {
       const GemmTask* tk = tile_task(gp, tile, k, local);
       const int tn = local % tk->ntn, tm = (local / tk->ntn) % tk->ntm;
       const int z = local / (tk->ntn * tk->ntm);
       const int t = z % tk->lt, split = z / tk->lt;
       const int M = tk->M, Nr = tk->Nr;
       const int chunks = (tk->kblocks + kChunkBlocks - 1) / kChunkBlocks;
-      const int row = tm * kBM + q * 32 + lane;
+      const int mrow0 = tm * kTileRows + (int)rank * kBM;  // this CTA's first row
+      const int row = mrow0 + q * 32 + lane;
       float acc[kHalf];
 #pragma unroll
       for (int j = 0; j < kHalf; ++j) acc[j] = 0.f;
@@ -580,8 +660,13 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&tempty[b]);
-          if (last) mbar_arrive(&cempty[tt & 1]);
+          if (PAIR && rank != 0) {  // the MMA thread of CTA 0 waits on its own barriers
+            mbar_arrive_leader(&tempty[b]);
+            if (last) mbar_arrive_leader(&cempty[tt & 1]);
+          } else {
+            mbar_arrive(&tempty[b]);
+            if (last) mbar_arrive(&cempty[tt & 1]);
+          }
         }
       }
       if (ok && tk->out_t) {
@@ -605,7 +690,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         // x 64 contiguous bytes instead of 32 rows x 16 bytes
         float* stg = stage_out + (warp - 2) * (32 * C::kStgPitch);
         float* base = tk->out + ((size_t)split * tk->lt + t) * (size_t)M * Nr;
-        const int row0 = tm * kBM + q * 32, col0 = tn * kBN + c0;
+        const int row0 = mrow0 + q * 32, col0 = tn * kBN + c0;
         const bool vec = (Nr & 3) == 0;
         (void)row;
 #pragma unroll
@@ -642,7 +727,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
     const int ct = threadIdx.x - 32 * (2 + kDrainWarps);  // 0 .. 32*kConvWarps-1
     constexpr int kCT = 32 * kConvWarps;
     int g = 0, k = 0, local = 0, ok = 1;
-    for (long long tile = blockIdx.x; tile < gp.total_tiles && ok; tile += gridDim.x) {
+    for (long long tile = tile0; tile < gp.total_tiles && ok; tile += tstep) {
       const GemmTask* tk = tile_task(gp, tile, k, local);
       for (int i = 0; i < tk->kblocks; ++i, ++g) {
         const int r = g % R, st = g % S;
@@ -661,9 +746,11 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         // chunks, B: one complex k pair of one column each), then the splits
         // and stores: the loads overlap instead of one unit's round trip after
         // another.
+        constexpr int NB = C::kBCols;                         // complex B columns staged
         constexpr int kUA = (C::kRawA / 16 + kCT - 1) / kCT;  // A units per thread
-        constexpr int kUB = ((kBN / 2) * 8 + kCT - 1) / kCT;  // B units per thread
-        static_assert(kBN / 2 == 64, "unit decode assumes 64 complex columns per tile");
+        constexpr int kUB = (NB * 8 + kCT - 1) / kCT;         // B units per thread
+        static_assert(NB == 64 || NB == 32, "unit decode: 32 or 64 complex columns");
+        constexpr int kNBlk = NB / 16, kCShift = NB == 64 ? 7 : 6;
         float4 va[kUA], vb[kUB];
         // A unit c: K-major tiles: the 16-byte chunk c, written to the same
         // place; [k][rows] tiles: row c % 128, complex k pair c / 128 (lanes
@@ -693,14 +780,15 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         // chunk and the next four at the other, so that a half warp's loads
         // fall on 16 distinct bank pairs and a quarter warp's swizzled B'
         // stores on 8 distinct chunk positions (no bank conflicts):
-        // n = [3:0] + 16*[6:5], c = 2*[8:7] + ([2] ^ [4]).  K-major tiles:
+        // n = [3:0] + 16*[6:5], c = 2*[8:7] + ([2] ^ [4]) (32 columns, CTA
+        // pairs: n = [3:0] + 16*[5], c = 2*[7:6] + ([2] ^ [4])).  K-major tiles:
         // n = it / 8, c = it % 8.
         const bool bmn = tk->b_mn != 0;  // [k][n] raw tile (3-d or 4-d map alike)
         const float2* rb = reinterpret_cast<const float2*>(rp + C::kRawA);
         auto unit = [&](int it, int& n, int& c) {
           if (bmn) {
-            n = (it & 15) + 16 * ((it >> 5) & 3);
-            c = 2 * (it >> 7) + (((it >> 2) ^ (it >> 4)) & 1);
+            n = (it & 15) + 16 * ((it >> 5) & (kNBlk - 1));
+            c = 2 * (it >> kCShift) + (((it >> 2) ^ (it >> 4)) & 1);
           } else {
             n = it >> 3;
             c = it & 7;
@@ -709,11 +797,11 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
 #pragma unroll
         for (int j = 0; j < kUB; ++j) {
           const int it = ct + j * kCT;
-          if (it < (kBN / 2) * 8) {
+          if (it < NB * 8) {
             int n, c;
             unit(it, n, c);
             if (bmn) {  // complex (k, n) at k = 2c and 2c + 1
-              const float2 v0 = rb[(2 * c) * (kBN / 2) + n], v1 = rb[(2 * c + 1) * (kBN / 2) + n];
+              const float2 v0 = rb[(2 * c) * NB + n], v1 = rb[(2 * c + 1) * NB + n];
               vb[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
             } else {
               vb[j] = *reinterpret_cast<const float4*>(rp + C::kRawA + n * 128 + 16 * (c ^ (n & 7)));
@@ -762,7 +850,7 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
 #pragma unroll
         for (int j = 0; j < kUB; ++j) {
           const int it = ct + j * kCT;
-          if (it >= (kBN / 2) * 8) continue;
+          if (it >= NB * 8) continue;
           int n, c;
           unit(it, n, c);
           const float4 v = vb[j];
@@ -785,22 +873,31 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&full[st]);
+          if (PAIR && rank != 0) mbar_arrive_leader(&full[st]);  // CTA 0 issues the MMAs
+          else mbar_arrive(&full[st]);
           mbar_arrive(&rempty[r]);
         }
       }
     }
   }
-  // teardown: no MMA may still write TMEM when it is released
+  // teardown: no MMA may still write TMEM when it is released (a pair: the
+  // commit of CTA 0's last MMA arrives in both CTAs; neither CTA leaves while
+  // the other may still arrive on its barriers or its MMAs read the peer)
   if (warp == 1 && lane == 0) {
     if (!mbar_wait(done, 0)) *abort_flag = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();
   if (*abort_flag && threadIdx.x == 0) atomicCAS(&g_mixed_error, 0, 1);
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols));
+  if (warp == 0) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
+  }
 }
 
 // ------------------------------------------------------------ K4t: A in TMEM
@@ -1777,14 +1874,14 @@ bool make_raw_map_mn(CUtensorMap* m, const void* base, int64_t n2, int64_t krows
 // floats, the k axes innermost first, the outer n axis if any, batch), boxes
 // of kBN floats x 16 k rows x 1 ...; fills the task's coordinate fields
 bool make_raw_map_mnx(CUtensorMap* m, const void* base, const Group& bn, const Group& bk,
-                      int64_t lt, int64_t slice_stride, GemmTask* t) {
+                      int64_t lt, int64_t slice_stride, GemmTask* t, int box_w = kBN) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5], estr[5];
   int nd = 0;
   dims[nd] = (cuuint64_t)(2 * bn.ext[bn.n - 1]);
-  box[nd++] = (cuuint32_t)kBN;
+  box[nd++] = (cuuint32_t)box_w;
   t->b_nk = bk.n;
   for (int a = bk.n - 1; a >= 0; --a) {
     t->b_kext[bk.n - 1 - a] = bk.ext[a];
@@ -1888,7 +1985,7 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const Mixe
   // it needs at least a quarter fewer 128 x 64-complex tiles, or no more
   // tiles and no operand reorder where the given orientation needs one; it
   // is stored transposed by the GEMM's epilogue (shared-memory-A kernel).
-  if (!bf16 && cd.K % 2 == 0 && tune.fused_kernel == 0 && cd.M <= tune.fused_max_n) {
+  if (!bf16 && cd.K % 2 == 0 && tune.fused_kernel != 1 && cd.M <= tune.fused_max_n) {
     MixedDesc x, y;
     const ContractDesc sw = exchanged(cd);
     if (fused_in_place(sw, tune.split_policy, &x)) {
@@ -1898,6 +1995,7 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const Mixe
       if (4 * t1 <= 3 * t0 || (t1 <= t0 && !normal_in_place)) {
         *d = x;
         d->swap = true;
+        d->pair = tune.fused_kernel == 2 && sw.M > kBM;
         return true;
       }
     }
@@ -1913,7 +2011,10 @@ bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d, const Mixe
   // next to the three MMAs per k-step).
   d->fused = !bf16 && (cd.K % 2 == 0) && cd.N <= tune.fused_max_n;
   d->tmem_a = tune.fused_kernel == 1;
-  if (d->fused && make_fused_desc(cd, d, tune.split_policy)) return true;
+  if (d->fused && make_fused_desc(cd, d, tune.split_policy)) {
+    d->pair = tune.fused_kernel == 2 && cd.M > kBM;
+    return true;
+  }
   d->fused = false;
   const int es = bf16 ? 2 : 4;
   d->kp = round_up(2 * cd.K, 16 / es);          // 16-byte rows for TMA
@@ -2062,11 +2163,14 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
                : !make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM))
       return false;
     t->a_mn = d.a_mn ? 1 : 0;
+    // raw B boxes: kBN / 2 complex columns, or half that for a CTA of a pair
+    const int bcols = d.pair ? kBN / 4 : kBN / 2;
     if (d.b_mn2) {
-      if (!make_raw_map_mnx(&t->map[2], b, cd.bn, cd.bk, cd.lt, bts, t)) return false;
-    } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts)
+      if (!make_raw_map_mnx(&t->map[2], b, cd.bn, cd.bk, cd.lt, bts, t, 2 * bcols)) return false;
+    } else if (d.b_mn ? !make_raw_map_mn(&t->map[2], b, 2 * cd.N, cd.K, cd.lt, d.b_rowstride, bts,
+                                         2 * bcols)
                       : !make_raw_map(&t->map[2], b, d.kp, cd.N, cd.lt, d.b_rowstride, bts,
-                                      kBN / 2)) {
+                                      bcols)) {
       return false;
     }
     t->b_mn = d.b_mn2 ? 2 : (d.b_mn ? 1 : 0);
@@ -2085,7 +2189,8 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
   t->splits = d.splits;
   t->lt = (int)cd.lt;
   t->ntn = (t->Nr + kBN - 1) / kBN;
-  t->ntm = (t->M + kBM - 1) / kBM;
+  const int rows = d.pair ? 2 * kBM : kBM;  // a pair's tile: 256 rows
+  t->ntm = (t->M + rows - 1) / rows;
   t->tiles = t->ntn * t->ntm * t->lt * t->splits;
   t->out = d.splits > 1 ? reinterpret_cast<float*>(sc + d.part_off) : C;
   t->out_t = d.swap ? 1 : 0;
@@ -2116,10 +2221,46 @@ void launch_gemm_t(const GemmParams& gp, dim3 grid, cudaStream_t s) {
   k_gemm_split3<BF16, FUSED, AMN><<<grid, C::kThreads, C::kSmem, s>>>(gp);
 }
 
-// amn: some fused task of the launch reads A as [k][rows] tiles
+// CTA-pair form: clusters of 2, as many pairs as can be resident at once
+// (one CTA per SM), at most one per pair tile
+template <bool AMN>
+int launch_gemm_pair_t(const GemmParams& gp, cudaStream_t s) {
+  using C = GemmCfg<false, true, true>;
+  auto kern = k_gemm_split3<false, true, AMN, true>;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(C::kThreads);
+  cfg.dynamicSmemBytes = C::kSmem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  static int pairs[2] = {0, 0};  // resident pairs per kernel form (device 0 sized)
+  int& np = pairs[AMN ? 1 : 0];
+  if (!np) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    cfg.gridDim = dim3(2 * (num_sms() / 2));
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = num_sms() / 2;
+    }
+    np = n;
+  }
+  cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(gp.total_tiles, np)));
+  return cudaLaunchKernelEx(&cfg, kern, gp) == cudaSuccess ? 1 : -1;
+}
+
+// amn: some fused task of the launch reads A as [k][rows] tiles; pair: the
+// launch's tasks are tiled for CTA pairs
 int launch_gemm(const GemmParams& gp, bool bf16, bool fused, cudaStream_t s,
-                bool tmem_a = false, bool amn = false) {
+                bool tmem_a = false, bool amn = false, bool pair = false) {
   if (gp.total_tiles <= 0) return 0;
+  if (fused && pair) return amn ? launch_gemm_pair_t<true>(gp, s) : launch_gemm_pair_t<false>(gp, s);
   dim3 grid((unsigned)std::min<long long>(gp.total_tiles, num_sms()));
   if (fused && tmem_a) {
     cudaFuncSetAttribute(k_gemm_tf32_tmem_a, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2143,7 +2284,7 @@ int launch_contract_mixed(const MixedDesc& d, const float* A, const float* B, fl
     std::memset(&gp, 0, sizeof(gp));
     if (!fill_gemm_task(d, A, B, scratch, C, &gp.single, nullptr, nullptr)) return -2;
     gp.total_tiles = gp.single.tiles;
-    if (launch_gemm(gp, false, true, s, d.tmem_a, d.a_mn) < 0) return -1;
+    if (launch_gemm(gp, false, true, s, d.tmem_a, d.a_mn, d.pair) < 0) return -1;
     ++nk;
     if (d.splits > 1) {
       const long long per = cd.lt * cd.M * 2 * cd.N;
@@ -2341,7 +2482,9 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   std::vector<CATask> ca;
   std::vector<PermTask> pm;
   std::vector<GemmTask> gf;  // fused-form GEMM tasks
-  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0, ftiles = 0;
+  std::vector<GemmTask> gq;  // ... run by CTA pairs
+  long long pb = 0, tiles = 0, rb = 0, cb = 0, ct = 0, mb = 0, ftiles = 0, qtiles = 0;
+  bool lvl_pair_amn = false;
   bool lvl_tmem_a = false, lvl_amn = false;
   auto add_perm = [&](const PermDesc& pd, const void* src, void* dst) {
     PermTask t;
@@ -2404,10 +2547,17 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
       GemmTask g;
       if (!fill_gemm_task(d, EA, EB, e.scratch, e.C, &g, as, bs)) return false;
       lvl_tmem_a = d.tmem_a;  // one DAG option: every fused task of a level alike
-      lvl_amn = lvl_amn || d.a_mn;
-      g.tile_start = ftiles;
-      ftiles += g.tiles;
-      gf.push_back(g);
+      if (d.pair) {
+        lvl_pair_amn = lvl_pair_amn || d.a_mn;
+        g.tile_start = qtiles;
+        qtiles += g.tiles;
+        gq.push_back(g);
+      } else {
+        lvl_amn = lvl_amn || d.a_mn;
+        g.tile_start = ftiles;
+        ftiles += g.tiles;
+        gf.push_back(g);
+      }
       if (d.splits > 1) add_reduce(d, g, e.C);
       continue;
     }
@@ -2473,6 +2623,10 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->gemm_fused_tiles = ftiles;
   lvl->fused_tmem_a = lvl_tmem_a;
   lvl->fused_amn = lvl_amn;
+  lvl->gemm_pair = reinterpret_cast<const void*>(append(buf, gq, 64));
+  lvl->ngemm_pair = (int)gq.size();
+  lvl->gemm_pair_tiles = qtiles;
+  lvl->pair_amn = lvl_pair_amn;
   lvl->red = reinterpret_cast<const void*>(append(buf, rd, 64));
   lvl->nred = (int)rd.size();
   lvl->red_blocks = rb;
@@ -2493,6 +2647,7 @@ void rebase_level(LevelDev* lvl, const char* base) {
   lvl->red = base + reinterpret_cast<uintptr_t>(lvl->red);
   lvl->perm = base + reinterpret_cast<uintptr_t>(lvl->perm);
   lvl->gemm_fused = base + reinterpret_cast<uintptr_t>(lvl->gemm_fused);
+  lvl->gemm_pair = base + reinterpret_cast<uintptr_t>(lvl->gemm_pair);
   lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
   auto rb = [&](const long long*& p) {
     p = reinterpret_cast<const long long*>(base + reinterpret_cast<uintptr_t>(p));
@@ -2510,6 +2665,7 @@ int level_launch_kinds(const LevelDev& L, int kinds[LQC_NUM_KINDS]) {
     kinds[n++] = LQC_KIND_PACK;
     kinds[n++] = LQC_KIND_GEMM_PLANES;
   }
+  if (L.ngemm_pair > 0) kinds[n++] = LQC_KIND_GEMM_FUSED;
   if (L.ngemm_fused > 0) kinds[n++] = LQC_KIND_GEMM_FUSED;
   if (L.nred > 0) kinds[n++] = LQC_KIND_REDUCE;
   if (L.nca > 0) {
@@ -2547,6 +2703,16 @@ int launch_level(const LevelDev& L, cudaStream_t s, cudaEvent_t* marks, unsigned
     gp.total_tiles = L.gemm_tiles;
     mark();
     if (launch_gemm(gp, L.bf16, false, s) < 0) return -1;
+    ++nk;
+  }
+  if (L.ngemm_pair > 0) {  // the wide products first, by CTA pairs
+    GemmParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.tasks = static_cast<const GemmTask*>(L.gemm_pair);
+    gp.ntasks = L.ngemm_pair;
+    gp.total_tiles = L.gemm_pair_tiles;
+    mark();
+    if (launch_gemm(gp, false, true, s, false, L.pair_amn, true) < 0) return -1;
     ++nk;
   }
   if (L.ngemm_fused > 0) {

@@ -58,6 +58,7 @@ struct MixedDesc {
   int64_t a_rowstride, b_rowstride;  // complex elements between operand rows (a_mn: k rows)
   PermDesc a_perm, b_perm;
   bool tmem_a;              // fused form: A split by converter warps into tensor memory
+  bool pair;                // fused form: CTA pairs (cta_group::2) on 256-row tiles
 };
 bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 
@@ -68,7 +69,8 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy);
 struct MixedTune {
   int64_t fused_max_n = 64;
   int split_policy = 0;
-  int fused_kernel = 0;     // fused form: 0 = A staged in shared memory, 1 = A in TMEM
+  int fused_kernel = 0;     // fused form: 0 = A staged in shared memory, 1 = A in TMEM,
+                            // 2 = as 0 with CTA pairs for products of more than 128 rows
 };
 bool make_mixed_desc(const ContractDesc& cd, bool bf16, MixedDesc* d,
                      const MixedTune& tune = MixedTune());
@@ -124,6 +126,10 @@ struct LevelDev {
   long long gemm_fused_tiles;
   bool fused_tmem_a;        // the fused tasks run the A-in-tensor-memory kernel
   bool fused_amn;           // ... and some reads A as [k][rows] tiles
+  const void* gemm_pair;    // fused tasks run by CTA pairs (one more launch)
+  int ngemm_pair;
+  long long gemm_pair_tiles;
+  bool pair_amn;
   const void* red;
   const long long* red_starts;
   int nred;

@@ -249,7 +249,7 @@ def test_contract_all_c64_vs_oracle(case, lt):
                                  (128, 1100, 96)])
 @pytest.mark.parametrize("fused", [0, 1 << 30])
 @pytest.mark.parametrize("window", [0, 64])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_matrix_product_forms_vs_oracle(mkn, fused, window, kernel):
     """C = A.B with B stored [k][n] (read in place and transposed inside the
     fused GEMM when n is even), then Tr(C.D): every form against the oracle."""
@@ -276,7 +276,7 @@ def test_matrix_product_forms_vs_oracle(mkn, fused, window, kernel):
 
 @pytest.mark.parametrize("n", [64, 128])
 @pytest.mark.parametrize("window", [0, 64])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_propagator_right_operand_in_place_vs_oracle(n, window, kernel):
     """M . P over P's first distillation axis: P is read in place as [k][spin
     block][n] by the fused GEMM (one 4-d TMA box per tile), then a correlator
@@ -301,7 +301,7 @@ def test_propagator_right_operand_in_place_vs_oracle(n, window, kernel):
 
 
 @pytest.mark.parametrize("n", [32, 128])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_propagator_left_operand_in_place_vs_oracle(n, kernel):
     """P x P over (spin out, distillation out) and a P x M over three axes:
     left operands whose contracted axes are several groups (and whose rows are
@@ -326,7 +326,7 @@ def test_propagator_left_operand_in_place_vs_oracle(n, kernel):
     assert rel_err(d.read_correlator(r), ref) < TOL_TF32X3
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("mkn,bmn", [((40, 70, 24), True), ((130, 44, 200), True),
                                      ((129, 1100, 64), True), ((64, 48, 64), False),
                                      ((300, 34, 70), False)])
@@ -363,8 +363,11 @@ def test_fused_kernels_exact_on_integers(kernel, mkn, bmn, window):
 
 
 def test_fused_kernels_agree_on_a_dag():
-    """The two fused GEMMs on the same DAG (multi-meson terms, every width
-    fused): both within the mixed bar of the oracle on every root."""
+    """The fused GEMMs on the same DAG (multi-meson terms, every width
+    fused): each within the mixed bar of the oracle on every root, and the
+    CTA-pair form (kernel 2: cta_group::2 MMAs on 256-row tiles, each CTA
+    converting half of the B' tile) bit-identical to the one-CTA form, whose
+    per-element arithmetic it repeats."""
     wl = synth.make_workload("multi_meson", n_functions=30)
     od, _ = D.build_from_workload(wl)
     ref = C.evaluate(od, lambda u: synth.leaf_data(wl, od.nodes[u].leaf_index))
@@ -372,14 +375,48 @@ def test_fused_kernels_agree_on_a_dag():
     nd.schedule("tree", "lru", 0)
     nd.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
     stream = torch.cuda.current_stream().cuda_stream
-    worst = {}
-    for kernel in (0, 1):
+    worst, vals = {}, {}
+    for kernel in (0, 1, 2):
         nd.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
         nd.execute(stream)
-        vals = {r: nd.read_correlator(r) for r in nd.roots()}
+        vals[kernel] = {r: nd.read_correlator(r) for r in nd.roots()}
         assert L.lqc_mixed_error(1) == 0
-        worst[kernel] = max(rel_err(vals[r], ref[r]) for r in ref)
+        worst[kernel] = max(rel_err(vals[kernel][r], ref[r]) for r in ref)
     assert max(worst.values()) < TOL_TF32X3, worst
+    for r in ref:
+        assert np.array_equal(vals[2][r].view(np.float64), vals[0][r].view(np.float64)), r
+
+
+@pytest.mark.parametrize("rows", [192, 256])
+@pytest.mark.parametrize("window", [0, 64])
+def test_pair_tiles_right_operand_in_place_vs_oracle(rows, window):
+    """CTA pairs on a product of more than 128 rows whose right operand is a
+    propagator read in place as [k][spin block][n] blocks (half-width boxes
+    per CTA), then a correlator; against the oracle, and bit for bit against
+    the one-CTA kernel."""
+    n, lt = 64, 2
+    rng = np.random.default_rng(rows + window)
+
+    def rnd(*s):
+        return (rng.standard_normal((lt,) + s) + 1j * rng.standard_normal((lt,) + s)) / np.sqrt(n)
+    Mm, Pp, Dd = rnd(rows, n), rnd(4, 4, n, n), rnd(rows, 4, 4, n)
+    ref = C.contract_pair(C.contract_pair(Mm, Pp, (1,), (2,)), Dd, (0, 1, 2, 3), (0, 1, 2, 3))
+    got = {}
+    for kernel in (0, 2):
+        d = L.Dag(lt, "tf32x3")
+        a, b, dd = d.add_leaf((rows, n), Mm), d.add_leaf((4, 4, n, n), Pp), \
+            d.add_leaf((rows, 4, 4, n), Dd)
+        c = d.add_contraction(a, b, [1], [2])
+        r = d.add_contraction(c, dd, [0, 1, 2, 3], [0, 1, 2, 3])
+        d.schedule("tree")
+        d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+        d.set_option(L.LQC_OPT_WINDOW, window)
+        d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+        d.execute(torch.cuda.current_stream().cuda_stream)
+        got[kernel] = d.read_correlator(r)
+        assert L.lqc_mixed_error(1) == 0
+    assert rel_err(got[2], ref) < TOL_TF32X3
+    assert np.array_equal(got[2].view(np.float64), got[0].view(np.float64))
 
 
 def test_tf32_rounding_equals_the_hardware_conversion():

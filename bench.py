@@ -58,11 +58,11 @@ sys.path.insert(0, HERE)
 # the hash of the kernel source it was taken on (None until captured: the
 # figure is reported only while the source is unchanged).
 GEMM_TRAFFIC = {
-    "bytes_per_flop": 62.40e9 / 5.099e12, "source_sha16": "66ee201e860bd7df",
-    "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 24 grouped fused-GEMM "
-            "launches of one step of the batched workload with 8 parts (39.35 + 23.05 GB for "
-            "5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + output bytes), "
-            "scaled by the flops of a launch of this run"}
+    "bytes_per_flop": 62.80e9 / 5.099e12, "source_sha16": "a5ace22f78a7e64c",
+    "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 39 grouped fused-GEMM "
+            "launches (CTA-pair and one-CTA) of one step of the batched workload with 8 parts "
+            "(40.28 + 22.52 GB for 5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + "
+            "output bytes), scaled by the flops of a launch of this run"}
 # DRAM bytes per launch of the dominant FP64 kernel (k_contract_fp64<4,4>),
 # same convention.
 FP64_TRAFFIC = {

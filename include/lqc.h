@@ -501,7 +501,8 @@ int lqc_contract_all_fp64_noalloc(const double* A, int rank_a, const int64_t* ex
  * shapes / semantics as lqc_contract_fp64: each operand is split into hi and
  * lo parts of the tensor-core type, the products lo*hi + hi*lo + hi*hi are
  * accumulated in FP32 on the tensor cores (tcgen05), and long contractions are
- * split over the paired indices into FP32 partials summed in FP64.
+ * split over the paired indices into FP32 partials summed in double-float
+ * (TwoSum) and rounded once to FP32.
  * `scratch` (caller-owned device memory, contents ignored) must hold
  * lqc_contract_mixed_scratch_bytes(...) bytes (at least 256; that call returns 0
  * for shapes or a precision it rejects).  Errors: LQC_ERR_ARG,

@@ -759,17 +759,28 @@ int build_program(Dag& g) {
         for (size_t l = 0; l < r.levels.size(); ++l) {
           int kinds[LQC_NUM_KINDS];
           const int nk = level_launch_kinds(r.ldev[l], kinds);
-          int64_t fl = 0;
+          // each GEMM launch of the level carries the flops of its own tasks:
+          // plane form, CTA-pair fused form (launched first), one-CTA fused form
+          int64_t fl_planes = 0, fl_pair = 0, fl_single = 0;
           for (int32_t m : r.levels[l])
             if (P[m].kind == I_CONTRACT) {
               const ContractDesc& cd = x.cdesc[m];
-              fl += 8 * cd.lt * cd.M * cd.N * cd.K;
+              const MixedDesc& md = x.mdesc[m];
+              const int64_t f = 8 * cd.lt * cd.M * cd.N * cd.K;
+              (md.fused ? (md.pair ? fl_pair : fl_single) : fl_planes) += f;
             }
           r.lev_slot[l] = (int32_t)x.kev_kind.size();
+          bool pair_next = r.ldev[l].ngemm_pair > 0;
           for (int k = 0; k < nk; ++k) {
             x.kev_kind.push_back((int8_t)kinds[k]);
-            x.kev_flops.push_back(
-                kinds[k] == LQC_KIND_GEMM_PLANES || kinds[k] == LQC_KIND_GEMM_FUSED ? fl : 0);
+            int64_t f = 0;
+            if (kinds[k] == LQC_KIND_GEMM_PLANES) {
+              f = fl_planes;
+            } else if (kinds[k] == LQC_KIND_GEMM_FUSED) {
+              f = pair_next ? fl_pair : fl_single;
+              pair_next = false;
+            }
+            x.kev_flops.push_back(f);
           }
           x.kev_kind.push_back(-1);
           x.kev_flops.push_back(0);

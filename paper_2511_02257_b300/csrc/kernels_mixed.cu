@@ -22,14 +22,18 @@
 //     buffers and eight drain warps add the finished one into FP32 registers
 //     (one output row per thread), then stage 32x16 output blocks through
 //     shared memory for coalesced stores.  Fused form (TF32): TMA brings raw
-//     complex64 tiles (K-major, or [k][n] for right operands read in place
-//     through maps of up to 5 dimensions) and converter warps build the
-//     hi/lo operand tiles.  Contractions longer than kMaxChunk real k are
-//     split over k into FP32 partial tiles summed in FP64.
+//     complex64 tiles (K-major, [k][rows] for left operands contracted over
+//     their leading axis, or [k][n] for right operands read in place through
+//     maps of up to 5 dimensions) and converter warps build the hi/lo operand
+//     tiles.  Products with fewer rows than a tile run exchanged (C^T = B^T
+//     A^T) and the epilogue stores them transposed.  Products of more than
+//     128 rows can run on CTA pairs (cta_group::2, 256-row tiles, each CTA
+//     converting half of the B' tile).  Contractions longer than kMaxChunk
+//     real k are split over k into FP32 partial tiles summed in double-float.
 // Reorder / K2m: a PermDesc maps destination elements to source offsets;
 //     blocks of runs or of transposed tiles copy operands into [rows][K]
-//     order, and the correlators (contract-all, double-float per thread, FP64
-//     across threads and blocks) visit their partner in place.
+//     order, and the correlators (contract-all, double-float sums per thread
+//     and per block, FP64 across blocks) visit their partner in place.
 // Grouped launches run each kind over every member of a window level.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
@@ -1327,15 +1331,28 @@ k_gemm_tf32_tmem_a(const __grid_constant__ GemmParams gp) {
                  "r"(C::kTmemCols));
 }
 
-// K4r: out c64 [lt][M][N] = sum over splits of the FP32 partials, in FP64
+// K4r: out c64 [lt][M][N] = sum over splits of the FP32 partials
+// The k-split partials of one output element summed in double-float (Knuth's
+// TwoSum per partial, the rounding errors gathered apart) and rounded once to
+// FP32: the correctly rounded sum but for rare ties, with FP32 arithmetic
+// (B300 issues FP64 at a small fraction of its FP32 rate).
+__device__ __forceinline__ float sum_splits(const float* __restrict__ p, long long stride, int n) {
+  float h = 0.f, l = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float x = p[(long long)k * stride];
+    const float t = __fadd_rn(h, x);
+    const float bp = __fsub_rn(t, h);
+    l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+    h = t;
+  }
+  return __fadd_rn(h, l);
+}
+
 __global__ void k_reduce_splits(const float* __restrict__ part, float* __restrict__ out,
                                 long long per_split, int splits) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per_split;
-       i += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += (double)part[(long long)k * per_split + i];
-    out[i] = (float)s;
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = sum_splits(part + i, per_split, splits);
 }
 
 // ------------------------------------------------------------ K3 pack
@@ -1606,8 +1623,9 @@ __device__ __forceinline__ void ca_partial_block(const float2* __restrict__ A,
   __shared__ __align__(16) unsigned char smem[(kPermElems + 1) * 4];
   A += t * d.n;
   B += t * d.src_ts;
-  // per thread: double-float sums (exact FP32 products, TwoSum accumulation,
-  // ~44 significant bits) at FP32 throughput; across threads and blocks: FP64
+  // per thread and across the block: double-float sums (exact FP32 products,
+  // TwoSum accumulation, ~44 significant bits) at FP32 throughput; across
+  // blocks: FP64
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   if (d.mode == 0) {
     perm_visit(d, B, b, smem, [&](unsigned e) { return A[e]; },
@@ -1810,9 +1828,7 @@ k_reduce_grouped(const ReduceTask* __restrict__ tasks, const long long* __restri
   for (int e = threadIdx.x; e < kReduceElems; e += 256) {
     const long long i = base + e;
     if (i >= tk.per) break;
-    double acc = 0.0;
-    for (int k = 0; k < tk.splits; ++k) acc += (double)tk.part[(long long)k * tk.per + i];
-    tk.out[i] = (float)acc;
+    tk.out[i] = sum_splits(tk.part + i, tk.per, tk.splits);
   }
 }
 

@@ -425,3 +425,33 @@ def test_tf32_rounding_equals_the_hardware_conversion():
     bad = ctypes.c_int64(-1)
     assert L.lqc_test_tf32_rounding(1 << 26, 12345, ctypes.byref(bad)) == 0
     assert bad.value == 0
+
+
+def test_gemm_flops_counted_once_per_launch():
+    """With per-kind timing, each GEMM launch of a level carries the flops
+    of its own tasks: the counted GEMM flops equal the sum of 8 Lt M N K over
+    the exterior contractions, whether a level runs one fused launch or a
+    CTA-pair launch and a one-CTA launch."""
+    import math
+    wl = synth.make_workload("multi_meson", n_functions=30)
+    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd.schedule("tree", "lru", 0)
+    nd.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    nd.set_option(L.LQC_OPT_TIMING, 1)
+    expect = 0
+    for u in range(nd.num_nodes()):
+        left, right, _, _ = nd.node_operands(u)
+        if left < 0 or nd.node_info(u)["rank"] == 0:
+            continue
+        lt = nd.node_info(u)["lt"]
+        mk, kn, mn = (nd.node_info(x)["size"] // (8 * lt) for x in (left, right, u))
+        k = math.isqrt(mk * kn // mn)
+        expect += 8 * lt * (mk // k) * (kn // k) * k
+    stream = torch.cuda.current_stream().cuda_stream
+    counted = {}
+    for kernel in (0, 2):
+        nd.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+        nd.execute(stream)
+        nd.wait()
+        counted[kernel] = nd.exec_info()["flops_gemm"]
+    assert counted[0] == counted[2] == expect, (counted, expect)

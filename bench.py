@@ -58,7 +58,7 @@ sys.path.insert(0, HERE)
 # the hash of the kernel source it was taken on (None until captured: the
 # figure is reported only while the source is unchanged).
 GEMM_TRAFFIC = {
-    "bytes_per_flop": 62.80e9 / 5.099e12, "source_sha16": "a5ace22f78a7e64c",
+    "bytes_per_flop": 62.80e9 / 5.099e12, "source_sha16": "15b5f0ab5be7ee7f",
     "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 39 grouped fused-GEMM "
             "launches (CTA-pair and one-CTA) of one step of the batched workload with 8 parts "
             "(40.28 + 22.52 GB for 5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + "
@@ -330,9 +330,21 @@ def gen_leaves(wl):
         return list(ex.map(lambda li: synth.leaf_data(wl, li), range(len(wl.leaves))))
 
 
-def source_sha16(name):
+def source_sha16(name, start=None, end=None):
+    """First 16 hex digits of the SHA-256 of a kernel source, or of its text
+    from the first line starting with `start` to the line starting with `end`
+    (the code a captured kernel is built from, so that edits elsewhere in the
+    file keep its ncu figures)."""
     with open(os.path.join(HERE, "paper_2511_02257_b300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        text = f.read()
+    if start is not None:
+        text = text[text.index(start.encode()):text.index(end.encode())]
+    return hashlib.sha256(text).hexdigest()[:16]
+
+
+# the fused GEMM's code in kernels_mixed.cu: its helpers and kernels up to the
+# A-in-TMEM form (the split-K sums, reorders and correlators come after it)
+GEMM_SOURCE = ("kernels_mixed.cu", "#include", "// " + "-" * 60 + " K4t: A in TMEM")
 
 
 def link_bandwidth(nbytes=1 << 30, reps=3):
@@ -424,7 +436,7 @@ def gemm_roofline(L, info, precision, steps_timed):
     peak_s = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * ratio
     ach = 3 * fl / (ms * 1e-3) / 1e12 if ms > 0 else None
     traffic = None
-    if GEMM_TRAFFIC and GEMM_TRAFFIC.get("source_sha16") == source_sha16("kernels_mixed.cu") \
+    if GEMM_TRAFFIC and GEMM_TRAFFIC.get("source_sha16") == source_sha16(*GEMM_SOURCE) \
             and n:
         traffic = GEMM_TRAFFIC["bytes_per_flop"] * fl / n
     total = sum(kinds.values())

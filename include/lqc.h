@@ -152,6 +152,10 @@ typedef struct {
    * moved to the host (written back first when they had no host copy) and
    * loaded again before their next use; not part of lqc_stats            */
   int64_t extra_evictions, extra_h2d_bytes, extra_d2h_bytes;
+  /* programs built so far (op list, task tables and, with LQC_OPT_CUDA_GRAPH,
+   * the graph): a schedule, an option change or leaf data with a new scale
+   * exponent makes the next execute build one                             */
+  int64_t n_programs;
 } lqc_exec_info;
 
 /* Option keys for lqc_dag_set_option. */
@@ -246,7 +250,14 @@ int lqc_dag_add_leaf_tensor(lqc_dag* dag, int rank, const int64_t* extents,
 
 /* (Re)set the values of an existing leaf; same layout and ownership as
  * lqc_dag_add_leaf_tensor.  Allowed after scheduling; takes effect at the
- * next execute (it synchronises with an execution in flight). */
+ * next execute (it synchronises with an execution in flight).  The host
+ * pass (normalisation and conversion, or the FP64 copy) runs on up to 32
+ * threads.  Mixed precisions: new data keeps the leaf's power-of-two
+ * exponent while its largest |component| stays in (2^(e-32), 2^e]; then
+ * the program (and its CUDA graph) stays valid and only a staged device copy
+ * is refreshed, so a caller can stream new leaves every step.  Otherwise
+ * the exponent changes and the next execute builds a new program
+ * (lqc_exec_info.n_programs).  FP64 never needs a new program. */
 int lqc_dag_set_leaf_data(lqc_dag* dag, int64_t leaf_id, const double* data);
 
 /* Register a binary contraction (a non-leaf node, Sec. II-B).

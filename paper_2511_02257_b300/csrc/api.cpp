@@ -10,6 +10,40 @@
 
 #include "internal.hpp"
 
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+namespace {
+// Host passes over leaf data (normalisation, conversion, copies): the range
+// [0, n) in contiguous chunks on up to kMaxHostThreads threads (one chunk per
+// thread, at least 2^20 values each); f(a, b) or f(a, b, chunk index).
+constexpr int kMaxHostThreads = 32;
+template <typename F>
+void parallel_chunks(int64_t n, F f) {
+  const int64_t per_min = 1 << 20;
+  int t = (int)std::min<int64_t>(kMaxHostThreads, std::max<int64_t>(1, n / per_min));
+  t = std::min<int>(t, std::max(1u, std::thread::hardware_concurrency()));
+  auto call = [&](int64_t a, int64_t b, int i) {
+    if constexpr (std::is_invocable_v<F, int64_t, int64_t, int>) f(a, b, i);
+    else f(a, b);
+  };
+  if (t <= 1) {
+    call(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(t - 1);
+  const int64_t per = (n + t - 1) / t;
+  for (int i = 1; i < t; ++i) {
+    const int64_t a = std::min(n, i * per), b = std::min(n, a + per);
+    th.emplace_back(call, a, b, i);
+  }
+  call(0, std::min(n, per), 0);
+  for (auto& x : th) x.join();
+}
+}  // namespace
+
 using lqc::Dag;
 using lqc::Node;
 
@@ -451,26 +485,70 @@ int lqc_dag_set_leaf_data(lqc_dag* h, int64_t id, const double* data) {
   if (rc != LQC_OK) return fail(h, rc, err);
   Node& n = g.nodes[id];
   const int64_t cnt = n.lt * n.elems;  // complex values
+  const int64_t nv = 2 * cnt;          // real components
+  bool rescaled = false;
   if (g.prec == LQC_PREC_FP64) {
-    std::memcpy(n.host, data, (size_t)cnt * 16);
+    parallel_chunks(nv, [&](int64_t a, int64_t b) {
+      std::memcpy(static_cast<double*>(n.host) + a, data + a, (size_t)(b - a) * 8);
+    });
   } else {
     // complex64 storage with FP64 normalisation: scale by the power of two
     // that brings the largest |component| into [0.5, 1), then round once
-    double mx = 0.0;
-    for (int64_t i = 0; i < 2 * cnt; ++i) mx = std::max(mx, std::fabs(data[i]));
+    // (x * 2^-e in FP64 is exact, as ldexp).  New data of a leaf keeps its
+    // exponent while its largest component stays within (2^(e-32), 2^e]:
+    // then no consumer's exponent changes and the program (and its CUDA
+    // graph) stays valid.  With an exponent to keep, one pass converts and
+    // finds the largest component; a second pass runs only if it changed.
+    float* dst = static_cast<float*>(n.host);
+    std::vector<double> part(kMaxHostThreads, 0.0);
+    auto pass = [&](int e, bool convert) {
+      const double sc = std::ldexp(1.0, -e);
+      std::fill(part.begin(), part.end(), 0.0);
+      parallel_chunks(nv, [&](int64_t a, int64_t b, int t) {
+        // plain compares, which vectorise: a NaN component never wins (it is
+        // stored as NaN), an infinite one does (then the exponent is 0)
+        double m = 0.0;
+        if (convert) {
+          for (int64_t i = a; i < b; ++i) {
+            const double x = data[i], ax = std::fabs(x);
+            m = ax > m ? ax : m;
+            dst[i] = (float)(x * sc);
+          }
+        } else {
+          for (int64_t i = a; i < b; ++i) {
+            const double ax = std::fabs(data[i]);
+            m = ax > m ? ax : m;
+          }
+        }
+        part[t] = m;
+      });
+      double mx = 0.0;
+      for (double m : part) mx = m > mx ? m : mx;
+      return mx;
+    };
+    const double mx = n.has_data ? pass(n.scale_exp, true) : pass(0, false);
     int e = 0;
     if (mx > 0.0 && std::isfinite(mx)) std::frexp(mx, &e);
-    n.scale_exp = e;
-    float* dst = static_cast<float*>(n.host);
-    for (int64_t i = 0; i < 2 * cnt; ++i) dst[i] = (float)std::ldexp(data[i], -e);
-    // consumers registered before the data changed keep their exponents in sync
-    for (size_t u = (size_t)id + 1; u < g.nodes.size(); ++u) {
-      Node& c = g.nodes[u];
-      if (!c.is_leaf()) c.scale_exp = g.nodes[c.left].scale_exp + g.nodes[c.right].scale_exp;
+    const bool keep = n.has_data && (mx == 0.0 || (std::isfinite(mx) &&
+                                                   mx <= std::ldexp(1.0, n.scale_exp) &&
+                                                   mx > std::ldexp(1.0, n.scale_exp - 32)));
+    if (!keep) {
+      rescaled = !n.has_data || e != n.scale_exp;
+      n.scale_exp = e;
+      pass(e, true);
     }
+    // consumers registered before the data changed keep their exponents in sync
+    if (rescaled)
+      for (size_t u = (size_t)id + 1; u < g.nodes.size(); ++u) {
+        Node& c = g.nodes[u];
+        if (!c.is_leaf()) c.scale_exp = g.nodes[c.left].scale_exp + g.nodes[c.right].scale_exp;
+      }
   }
-  lqc::exec_invalidate_plan(g);  // staged leaf copies are stale
-  return LQC_OK;
+  n.has_data = true;
+  // a staged device copy takes the new values; a new exponent also changes
+  // the correlators' scales, which the program holds
+  if (rescaled) lqc::exec_invalidate_plan(g);
+  return lqc::exec_refresh_staged_leaf(g, id);
   LQC_GUARD_END(h)
 }
 

@@ -71,6 +71,7 @@ struct WinRec {
 }  // namespace
 
 struct ExecState {
+  int64_t n_programs = 0;  // programs built (op list, task tables, graph)
   int device = -1;
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // [1] h2d, [2] d2h
   cudaEvent_t start_ev = nullptr, done_ev = nullptr;
@@ -797,6 +798,7 @@ int build_program(Dag& g) {
     CK(pinned_alloc((void**)&x.host_arena, (size_t)hpl.top),
        "pinned write-back arena");
   x.prog_valid = true;
+  ++x.n_programs;
   x.tset = 0;
   g.info.n_contract = g.info.n_contract_all = 0;
   g.info.ms_contract = g.info.ms_contract_all = 0.0;
@@ -1187,6 +1189,7 @@ int exec_run(Dag& g, void* stream) {
   g.info.extra_evictions = x.extra_evict;
   g.info.extra_h2d_bytes = x.extra_h2d;
   g.info.extra_d2h_bytes = x.extra_d2h;
+  g.info.n_programs = x.n_programs;
   g.executed = true;
   return LQC_OK;
 }
@@ -1319,6 +1322,15 @@ int exec_stage_leaves(Dag& g, void* stream) {
   CK(cudaStreamSynchronize(s), "stage sync");
   x.staged_valid = true;
   free_program(x);
+  return LQC_OK;
+}
+
+int exec_refresh_staged_leaf(Dag& g, int64_t u) {
+  if (!g.ex) return LQC_OK;
+  ExecState& x = *g.ex;
+  if (!x.staged_valid || u < 0 || u >= (int64_t)x.staged.size() || !x.staged[u]) return LQC_OK;
+  CK(cudaMemcpy(x.staged[u], g.nodes[u].host, (size_t)g.size_bytes(u), cudaMemcpyHostToDevice),
+     "refresh staged leaf");
   return LQC_OK;
 }
 

@@ -27,6 +27,7 @@ struct Node {
   // the DAG's storage precision; nullptr until data is given
   void* host = nullptr;
   bool host_pinned = false;
+  bool has_data = false;        // leaves: data given at least once
   // mixed precisions: stored values are the tensor times 2^-scale_exp
   // (leaves: FP64 normalisation; contractions: sum of the operands')
   int scale_exp = 0;
@@ -111,6 +112,9 @@ int exec_kernel_times(Dag& g, int64_t* node, double* ms, int64_t cap, int64_t* n
 int exec_read(Dag& g, int64_t root, double* out);
 int exec_read_all(Dag& g, double* out, int64_t cap);
 int exec_stage_leaves(Dag& g, void* stream);
+// after new data of leaf u with unchanged scale: refresh its staged device
+// copy (if the leaves are staged); the program and its graph stay valid
+int exec_refresh_staged_leaf(Dag& g, int64_t u);
 int exec_unstage_leaves(Dag& g);
 void exec_destroy(Dag& g);
 void exec_invalidate_plan(Dag& g);   // plan changed: rebuild arena program on next run

@@ -63,7 +63,8 @@ class lqc_exec_info(ctypes.Structure):
          ("flops_contract", c_i64), ("flops_contract_all", c_i64), ("host_arena_bytes", c_i64),
          ("n_kind", c_i64 * LQC_NUM_KINDS), ("ms_kind", ctypes.c_double * LQC_NUM_KINDS),
          ("flops_gemm", c_i64), ("resident_peak_bytes", c_i64),
-         ("extra_evictions", c_i64), ("extra_h2d_bytes", c_i64), ("extra_d2h_bytes", c_i64)]
+         ("extra_evictions", c_i64), ("extra_h2d_bytes", c_i64), ("extra_d2h_bytes", c_i64),
+         ("n_programs", c_i64)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}

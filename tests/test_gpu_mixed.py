@@ -217,7 +217,12 @@ def test_grouped_windows_bit_identical_to_single_launches(precision):
                                   ((4, 4, 40, 40), (4, 4, 40, 40), (0, 1, 2, 3), (1, 0, 3, 2)),
                                   ((9, 10, 11), (11, 9, 10), (0, 1, 2), (1, 2, 0)),
                                   ((33, 70), (33, 70), (0, 1), (0, 1)),
-                                  ((3, 1, 50), (50, 1, 3), (0, 1, 2), (2, 1, 0))])
+                                  ((3, 1, 50), (50, 1, 3), (0, 1, 2), (2, 1, 0)),
+                                  # runs read by warps: 64, 32 (ragged), 128, 1536 = 6 x 256
+                                  ((64, 64, 64), (64, 64, 64), (0, 1, 2), (1, 0, 2)),
+                                  ((5, 7, 32), (7, 5, 32), (0, 1, 2), (1, 0, 2)),
+                                  ((9, 10, 128), (10, 9, 128), (0, 1, 2), (1, 0, 2)),
+                                  ((32, 48), (32, 48), (0, 1), (0, 1))])
 @pytest.mark.parametrize("lt", [1, 5])
 def test_contract_all_c64_vs_oracle(case, lt):
     """Correlator of two complex64 tensors (FP64 sums; a permuted partner is

@@ -518,7 +518,8 @@ def mixed_form(L, wl, leaves, args, precision, policy, budget, stream, steps, wa
                        "fused_max_n": tuned["best"]["fused_max_n"] if tuned else args.fused_max_n,
                        "split_policy": tuned["best"]["split_policy"] if tuned
                        else args.split_policy, "cuda_graph": bool(args.graph),
-                       "fused_kernel": args.fused_kernel},
+                       "fused_kernel": tuned["best"]["fused_kernel"] if tuned
+                       else args.fused_kernel},
            "peak_paper_bytes": planned["peak_paper"], "peak_exec_bytes": planned["peak_exec"],
            "n_evict": planned["n_evict"], "h2d_bytes_planned": planned["h2d_bytes"],
            "d2h_bytes_planned": planned["d2h_bytes"],
@@ -839,7 +840,8 @@ def main():
                                        else args.fused_max_n) if mixed else None,
                        "split_policy": (tuned["best"]["split_policy"] if tuned
                                         else args.split_policy) if mixed else None,
-                       "fused_kernel": args.fused_kernel if mixed else None,
+                       "fused_kernel": (tuned["best"]["fused_kernel"] if tuned
+                                        else args.fused_kernel) if mixed else None,
                        "autotune": tuned,
                        "parallelism": ("lt-shard" if sharded else "replicas") if ws > 1
                                       else "single",

@@ -204,6 +204,7 @@ typedef struct {
   int64_t window;        /* LQC_OPT_WINDOW */
   int64_t fused_max_n;   /* LQC_OPT_FUSED_MAX_N */
   int64_t split_policy;  /* LQC_OPT_SPLIT_POLICY */
+  int64_t fused_kernel;  /* LQC_OPT_FUSED_KERNEL (the GEMM tile: 128 rows, or 256-row CTA-pair tiles) */
   double ms;             /* device time per execute (CUDA events) */
 } lqc_tune_entry;
 
@@ -391,10 +392,13 @@ int lqc_dag_prepare(lqc_dag* dag, void* stream);
  * leaf data given (or staged): for every candidate of LQC_OPT_WINDOW in
  * {0, 64, 512, 4096} (windows only when the plan evicts nothing) x
  * LQC_OPT_FUSED_MAX_N in {0, 64, 2^30} (TF32X3 only) x LQC_OPT_SPLIT_POLICY
- * in {0, 1}, runs one execute that builds the program, then times `reps`
- * executes on `stream` with CUDA events; sets the three options to the
- * fastest candidate.  entries (nullable; capacity cap) receive every
- * candidate with its time, *n their count (at most 24).  Correlators of
+ * in {0, 1}, and with every width fused also LQC_OPT_FUSED_KERNEL in {0, 2}
+ * (128-row tiles, or 256-row CTA-pair tiles for products of more than 128
+ * rows; with LQC_OPT_FUSED_KERNEL 1 set, that kernel only), runs one execute
+ * that builds the program, then times `reps` executes on `stream` with CUDA
+ * events; sets the four options to the fastest candidate.  entries
+ * (nullable; capacity cap) receive every candidate with its time, *n their
+ * count (at most 32).  Correlators of
  * every candidate agree within the mixed tolerance; the chosen options stay
  * in effect for later executes.  Errors: LQC_ERR_STATE (not scheduled, leaf
  * without data), LQC_ERR_ARG (FP64 DAG, reps outside [1, 1000], cap too

@@ -990,18 +990,28 @@ int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64
                   int64_t* n) {
   std::vector<lqc_tune_entry> cand;
   const bool windows_ok = g.planned.n_evict == 0;
+  // the GEMM tile (one CTA or a CTA pair) is a candidate with every width
+  // fused; the A-in-TMEM kernel, when chosen, is kept as it is
+  const bool tmem_a = g.opt_fused_kernel == 1;
   for (int64_t w : {int64_t(0), int64_t(64), int64_t(512), int64_t(4096)}) {
     if (w && !windows_ok) continue;
     for (int64_t f : {int64_t(0), int64_t(64), int64_t(1) << 30}) {
       if (g.prec == LQC_PREC_BF16X3 && f) continue;  // no fused form for BF16
-      for (int64_t sp : {int64_t(0), int64_t(1)}) cand.push_back(lqc_tune_entry{w, f, sp, 0.0});
+      for (int64_t sp : {int64_t(0), int64_t(1)}) {
+        if (tmem_a || f != (int64_t(1) << 30)) {
+          cand.push_back(lqc_tune_entry{w, f, sp, g.opt_fused_kernel, 0.0});
+        } else {
+          for (int64_t k : {int64_t(0), int64_t(2)}) cand.push_back(lqc_tune_entry{w, f, sp, k, 0.0});
+        }
+      }
     }
   }
   if (cap < (int64_t)cand.size() && entries) {
     g.err = "tune entry capacity too small";
     return LQC_ERR_ARG;
   }
-  const int64_t save[3] = {g.opt_window, g.opt_fused_max_n, g.opt_split_policy};
+  const int64_t save[4] = {g.opt_window, g.opt_fused_max_n, g.opt_split_policy,
+                           g.opt_fused_kernel};
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0), "tune event");
@@ -1012,6 +1022,7 @@ int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64
     g.opt_window = cand[c].window;
     g.opt_fused_max_n = cand[c].fused_max_n;
     g.opt_split_policy = cand[c].split_policy;
+    g.opt_fused_kernel = cand[c].fused_kernel;
     exec_invalidate_plan(g);
     rc = exec_run(g, stream);  // builds the program (and the graph)
     if (rc != LQC_OK) break;
@@ -1034,12 +1045,14 @@ int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64
     g.opt_window = save[0];
     g.opt_fused_max_n = save[1];
     g.opt_split_policy = save[2];
+    g.opt_fused_kernel = save[3];
     exec_invalidate_plan(g);
     return rc;
   }
   g.opt_window = cand[best].window;
   g.opt_fused_max_n = cand[best].fused_max_n;
   g.opt_split_policy = cand[best].split_policy;
+  g.opt_fused_kernel = cand[best].fused_kernel;
   exec_invalidate_plan(g);
   *n = (int64_t)cand.size();
   if (entries) std::copy(cand.begin(), cand.end(), entries);

@@ -75,7 +75,7 @@ class lqc_exec_info(ctypes.Structure):
 
 class lqc_tune_entry(ctypes.Structure):
     _fields_ = [("window", c_i64), ("fused_max_n", c_i64), ("split_policy", c_i64),
-                ("ms", ctypes.c_double)]
+                ("fused_kernel", c_i64), ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -345,12 +345,12 @@ class Dag:
         self._check(_lib.lqc_dag_prepare(self.h, c_vp(stream)), "prepare")
 
     def autotune(self, stream: int = 0, reps: int = 3):
-        """Time every candidate of (window, fused-form limit, split policy)
-        on this DAG and keep the fastest; returns the candidates with their
-        ms per execute, fastest first."""
-        entries = (lqc_tune_entry * 32)()
+        """Time every candidate of (window, fused-form limit, split policy,
+        fused GEMM tile) on this DAG and keep the fastest; returns the
+        candidates with their ms per execute, fastest first."""
+        entries = (lqc_tune_entry * 64)()
         n = c_i64()
-        self._check(_lib.lqc_dag_autotune(self.h, c_vp(stream), int(reps), entries, 32,
+        self._check(_lib.lqc_dag_autotune(self.h, c_vp(stream), int(reps), entries, 64,
                                           ctypes.byref(n)), "autotune")
         return sorted((entries[i].as_dict() for i in range(n.value)), key=lambda e: e["ms"])
 

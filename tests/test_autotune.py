@@ -89,9 +89,11 @@ def test_autotune_picks_fastest_and_stays_correct():
     nd.set_option(L.LQC_OPT_CUDA_GRAPH, 1)
     nd.stage_leaves(stream)
     entries = nd.autotune(stream, reps=2)
-    assert len(entries) == 24
-    assert {(e["window"], e["fused_max_n"], e["split_policy"]) for e in entries} == \
-        {(w, f, s) for w in (0, 64, 512, 4096) for f in (0, 64, 1 << 30) for s in (0, 1)}
+    assert len(entries) == 32
+    assert {(e["window"], e["fused_max_n"], e["split_policy"], e["fused_kernel"])
+            for e in entries} == \
+        {(w, f, s, 0) for w in (0, 64, 512, 4096) for f in (0, 64) for s in (0, 1)} | \
+        {(w, 1 << 30, s, k) for w in (0, 64, 512, 4096) for s in (0, 1) for k in (0, 2)}
     assert all(e["ms"] > 0 for e in entries)
     best = entries[0]
     assert best["ms"] == min(e["ms"] for e in entries)

@@ -812,6 +812,12 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
             }
           }
         }
+        // the raw tile is in registers now: its slot goes back to the TMA
+        // producer before this warp's splits and stores, so that the next
+        // loads start a conversion earlier (the arrive orders the warp's
+        // loads before it)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rempty[r]);
         if (lane == 0) {
           if (!mbar_wait(&empty[st], ((uint32_t)(g / S) & 1u) ^ 1u) || *abort_flag) {
             *abort_flag = 1;
@@ -879,7 +885,6 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         if (lane == 0) {
           if (PAIR && rank != 0) mbar_arrive_leader(&full[st]);  // CTA 0 issues the MMAs
           else mbar_arrive(&full[st]);
-          mbar_arrive(&rempty[r]);
         }
       }
     }

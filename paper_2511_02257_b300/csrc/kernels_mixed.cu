@@ -325,8 +325,13 @@ struct GemmTask {  // 64-byte aligned through its tensor maps
   const float2* a_raw;
   long long a_ts, a_rs;
   int kc;
-  int a_mn;             // fused form: A's raw tile is [16 complex k][128 rows] (rows
-                        // unit-stride), transposed by the converters
+  int a_mn;             // fused form: A read in place with its rows unit-stride, transposed
+                        // by the converters: 1 = [k][rows] (3-d map, raw tile [16 k][128
+                        // rows]); 2 = [outer rows][k][inner rows] (4-d map, raw tile
+                        // [128 / a_ni outer][16 k][a_ni inner])
+  int a_ni;             // a_mn: inner rows per raw-tile block (128 for a_mn 1; 16, 32, 64 or
+                        // 128 for a_mn 2)
+  int a_nio;            // a_mn 2: the inner row extent (a multiple of 128 when a_ni = 128)
   int out_t;            // D' row r, real column c -> out[((c / 2) * M + r) * 2 + (c & 1)]
                         // of each slice: the transposed product of exchanged operands
 };
@@ -499,8 +504,11 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
           if (FUSED) {
             uint8_t* rp = raw + st * C::kRawBytes;
             mbar_expect_tx(&rf[st], C::kRawBytes);
-            if (tk->a_mn)  // [16 complex k rows][128 complex rows], unswizzled
+            if (tk->a_mn == 1)  // [16 complex k rows][128 complex rows], unswizzled
               tma_load_3d(rp, &tk->map[0], &rf[st], 2 * m0, k0 / 2, t);
+            else if (tk->a_mn == 2)  // [outer][16 k][inner] blocks holding rows m0 .. m0 + 127
+              tma_load_4d(rp, &tk->map[0], &rf[st], 2 * (m0 % tk->a_nio), k0 / 2,
+                          m0 / tk->a_nio, t);
             else
               tma_load_3d(rp, &tk->map[0], &rf[st], k0, m0, t);
             if (tk->b_mn == 2) {  // the same tile inside one block of every outer axis
@@ -757,18 +765,21 @@ k_gemm_split3(const __grid_constant__ GemmParams gp) {
         constexpr int kNBlk = NB / 16, kCShift = NB == 64 ? 7 : 6;
         float4 va[kUA], vb[kUB];
         // A unit c: K-major tiles: the 16-byte chunk c, written to the same
-        // place; [k][rows] tiles: row c % 128, complex k pair c / 128 (lanes
-        // on consecutive rows: contiguous loads, and the swizzled stores of a
-        // quarter warp fall on 8 distinct chunk positions)
+        // place; in-place [k][rows] / [outer][k][inner] tiles: row n = c % 128
+        // (outer block n / a_ni, inner row n % a_ni), complex k pair c / 128
+        // (lanes on consecutive rows: contiguous loads, and the swizzled stores
+        // of a quarter warp fall on 8 distinct chunk positions)
         const bool amn = AMN && tk->a_mn != 0;
         const float2* ra = reinterpret_cast<const float2*>(rp);
         if (amn) {  // warp-uniform (one task per tile): two copies of the loop
+          const int ni = tk->a_ni, nsh = __ffs(ni) - 1;
 #pragma unroll
           for (int j = 0; j < kUA; ++j) {
             const int c = ct + j * kCT;
             if (c < C::kRawA / 16) {
               const int n = c & (kBM - 1), kc2 = c / kBM;
-              const float2 v0 = ra[(2 * kc2) * kBM + n], v1 = ra[(2 * kc2 + 1) * kBM + n];
+              const int blk = ((n >> nsh) * 16 + 2 * kc2) * ni + (n & (ni - 1));
+              const float2 v0 = ra[blk], v1 = ra[blk + ni];
               va[j] = make_float4(v0.x, v0.y, v1.x, v1.y);
             }
           }
@@ -1927,6 +1938,25 @@ bool make_raw_map_mnx(CUtensorMap* m, const void* base, const Group& bn, const G
   return r == CUDA_SUCCESS;
 }
 
+// left operand stored [outer rows][k][inner rows] (inner unit-stride): dims
+// (2 ni floats, k, outer, lt), boxes of 128 rows = 128 / ni outer blocks of
+// ni inner rows (ni <= 128), or 128 inner rows of one outer block
+bool make_raw_map_a3(CUtensorMap* m, const void* base, int64_t ni, int64_t krows, int64_t no,
+                     int64_t lt, int64_t k_stride, int64_t outer_stride, int64_t slice_stride) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int64_t bi = std::min<int64_t>(ni, kBM);
+  cuuint64_t dims[4] = {(cuuint64_t)(2 * ni), (cuuint64_t)krows, (cuuint64_t)no, (cuuint64_t)lt};
+  cuuint64_t strides[3] = {(cuuint64_t)(k_stride * 8), (cuuint64_t)(outer_stride * 8),
+                           (cuuint64_t)(slice_stride * 8)};
+  cuuint32_t box[4] = {(cuuint32_t)(2 * bi), 16u, (cuuint32_t)(kBM / bi), 1u};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool make_raw_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t lt,
                   int64_t row_stride, int64_t slice_stride, int box_rows) {
   auto fn = encode_fn();
@@ -2120,6 +2150,20 @@ bool make_fused_desc(const ContractDesc& cd, MixedDesc* d, int split_policy) {
   d->a_mn = !d->tmem_a && !d->a_direct && !cd.a_kfast && cd.am.n == 1 &&
             cd.am.stride[0] == 1 && cd.ak.n == 1 && cd.ak.stride[0] % 2 == 0 &&
             cd.a_ts % 2 == 0;
+  d->a_ni = 0;
+  // ... or [outer rows][k][inner rows] (a baryon contracted over its middle
+  // leg): inner extent 16, 32, 64 or a multiple of 128, so that a 128-row
+  // tile is whole outer blocks or one piece of one
+  if (!d->a_mn && !d->tmem_a && !d->a_direct && !cd.a_kfast && cd.am.n == 2 &&
+      cd.am.stride[1] == 1 && cd.ak.n == 1 && cd.ak.stride[0] % 2 == 0 &&
+      cd.am.stride[0] % 2 == 0 && cd.a_ts % 2 == 0) {
+    const int64_t ni = cd.am.ext[1];
+    if (ni == 16 || ni == 32 || ni == 64 || ni % 128 == 0) {
+      d->a_mn = true;
+      d->a_ni = ni;
+      d->a_outer_stride = cd.am.stride[0];
+    }
+  }
   if (d->a_mn) {
     d->a_direct = true;
     d->a_rowstride = cd.ak.stride[0];
@@ -2180,10 +2224,21 @@ bool fill_gemm_task(const MixedDesc& d, const float* A, const float* B, void* sc
     const void* b = d.b_direct ? (const void*)B : (const void*)bs;
     const int64_t ats = d.a_direct ? cd.a_ts : cd.M * cd.K;
     const int64_t bts = d.b_direct ? cd.b_ts : cd.N * cd.K;
-    if (d.a_mn ? !make_raw_map_mn(&t->map[0], a, 2 * cd.M, cd.K, cd.lt, d.a_rowstride, ats, 2 * kBM)
-               : !make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM))
+    if (d.a_mn && d.a_ni) {  // [outer][k][inner]
+      if (!make_raw_map_a3(&t->map[0], a, d.a_ni, cd.K, cd.M / d.a_ni, cd.lt, d.a_rowstride,
+                           d.a_outer_stride, ats))
+        return false;
+      t->a_mn = 2;
+      t->a_ni = (int)std::min<int64_t>(d.a_ni, kBM);
+      t->a_nio = (int)d.a_ni;
+    } else if (d.a_mn) {
+      if (!make_raw_map_mn(&t->map[0], a, 2 * cd.M, cd.K, cd.lt, d.a_rowstride, ats, 2 * kBM))
+        return false;
+      t->a_mn = 1;
+      t->a_ni = kBM;
+    } else if (!make_raw_map(&t->map[0], a, d.kp, cd.M, cd.lt, d.a_rowstride, ats, kBM)) {
       return false;
-    t->a_mn = d.a_mn ? 1 : 0;
+    }
     // raw B boxes: kBN / 2 complex columns, or half that for a CTA of a pair
     const int bcols = d.pair ? kBN / 4 : kBN / 2;
     if (d.b_mn2) {

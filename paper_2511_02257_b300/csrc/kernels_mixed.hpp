@@ -50,8 +50,10 @@ struct MixedDesc {
   bool a_direct, b_direct;
   bool b_mn;                // B read in place as [k][n]; the GEMM's converters transpose it
   bool b_mn2;               // ... as [k][outer n][inner n] blocks (4-d map)
-  bool a_mn;                // A read in place as [k][rows] (rows unit-stride); transposed by
-                            // the converters
+  bool a_mn;                // A read in place as [k][rows] (rows unit-stride), or with a_ni
+                            // as [outer rows][k][inner rows]; transposed by the converters
+  int64_t a_ni;             // a_mn: 0 = one row group, else the inner row extent
+  int64_t a_outer_stride;   // a_ni: complex elements between outer row blocks
   bool swap;                // operands exchanged: the GEMM computes C^T = B^T A^T (its rows
                             // are C's columns) and stores it transposed; cd describes the
                             // exchanged roles

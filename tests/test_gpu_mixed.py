@@ -98,6 +98,13 @@ CASES = [
     # left operand [k][rows] read in place (a baryon over its first leg)
     ((24, 24, 24), (24, 24), (0,), (0,)),
     ((18, 130), (18, 40), (0,), (0,)),
+    # left operand [outer][k][inner] read in place (a baryon over its middle
+    # leg), inner extents 16, 32, 128 and 256; and exchanged into that role
+    ((9, 12, 16), (12, 10), (1,), (0,)),
+    ((5, 32, 32), (32, 24), (1,), (0,)),
+    ((3, 16, 128), (16, 40), (1,), (0,)),
+    ((2, 8, 256), (8, 20), (1,), (0,)),
+    ((13, 18), (5, 18, 32), (1,), (1,)),
 ]
 
 
@@ -460,3 +467,30 @@ def test_gemm_flops_counted_once_per_launch():
         nd.wait()
         counted[kernel] = nd.exec_info()["flops_gemm"]
     assert counted[0] == counted[2] == expect, (counted, expect)
+
+
+@pytest.mark.parametrize("kernel", [0, 2])
+@pytest.mark.parametrize("window", [0, 64])
+def test_left_operand_outer_k_inner_exact(kernel, window):
+    """A baryon-like left operand contracted over its middle axis, [4][64][64]
+    read in place as [outer][k][inner] blocks (256 rows: CTA pairs with kernel
+    2), times a matrix, then a correlator: equal to the oracle bit for bit on
+    small integers."""
+    lt = 2
+    rng = np.random.default_rng(31 + kernel + window)
+
+    def ints(*s):
+        return rng.integers(-3, 4, (lt,) + s) + 1j * rng.integers(-3, 4, (lt,) + s)
+    A, Bm, Dm = ints(4, 64, 64), ints(64, 40), ints(4, 64, 40)
+    ref = C.contract_pair(C.contract_pair(A, Bm, (1,), (0,)), Dm, (0, 1, 2), (0, 1, 2))
+    d = L.Dag(lt, "tf32x3")
+    a, b, dd = d.add_leaf((4, 64, 64), A), d.add_leaf((64, 40), Bm), d.add_leaf((4, 64, 40), Dm)
+    r = d.add_contraction(d.add_contraction(a, b, [1], [0]), dd, [0, 1, 2], [0, 1, 2])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+    d.set_option(L.LQC_OPT_WINDOW, window)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    got = d.read_correlator(r)
+    assert L.lqc_mixed_error(1) == 0
+    assert np.array_equal(got, ref), rel_err(got, ref)

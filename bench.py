@@ -58,10 +58,10 @@ sys.path.insert(0, HERE)
 # the hash of the kernel source it was taken on (None until captured: the
 # figure is reported only while the source is unchanged).
 GEMM_TRAFFIC = {
-    "bytes_per_flop": 62.20e9 / 5.099e12, "source_sha16": "139a2299b62b7a34",
+    "bytes_per_flop": 62.61e9 / 5.099e12, "source_sha16": "ebde4106fbdf049b",
     "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 39 grouped fused-GEMM "
             "launches (CTA-pair and one-CTA) of one step of the batched workload with 8 parts "
-            "(39.69 + 22.51 GB for 5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + "
+            "(40.09 + 22.52 GB for 5.099e12 algorithmic flops, 71.5 GB of algorithmic operand + "
             "output bytes), scaled by the flops of a launch of this run"}
 # DRAM bytes per launch of the dominant FP64 kernel (k_contract_fp64<4,4>),
 # same convention.

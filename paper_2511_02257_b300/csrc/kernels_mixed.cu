@@ -1752,7 +1752,19 @@ struct CATask {
   double2* part;
   PermDesc d;            // B in A's order; d.blocks partial sums per slice
   double scale;
-  long long block_start, t_start;
+  long long t_start;
+};
+
+// The blocks of a grouped correlator launch walk segments of consecutive
+// slices (about kCaChunkElems elements of the left operand each) in
+// chunk-major order, the tasks that share an operand adjacent: the
+// correlators of a level often share a tensor (a leaf), whose chunk is then
+// read from DRAM once and from L2 by the others, while each segment still
+// streams megabytes of contiguous data.  A block's partial sum does not
+// depend on the order.
+constexpr long long kCaChunkElems = 1ll << 19;
+struct CASeg {
+  int task, t0;  // slices t0, t0 + 1, ... (d.blocks blocks each)
 };
 
 struct PermTask {
@@ -1808,11 +1820,12 @@ k_permute_grouped(const PermTask* __restrict__ tasks, const long long* __restric
 
 __global__ void __launch_bounds__(256)
 k_contract_all_grouped(const CATask* __restrict__ tasks, const long long* __restrict__ starts,
-                       int n) {
-  const CATask& tk = tasks[find_task(starts, n, blockIdx.x)];
-  const long long local = blockIdx.x - tk.block_start;
-  ca_partial_block(tk.A, tk.B, tk.part, tk.d, local / tk.d.blocks,
-                   (unsigned)(local % tk.d.blocks));
+                       const CASeg* __restrict__ segs, int n) {
+  const int s = find_task(starts, n, blockIdx.x);
+  const CASeg sg = segs[s];
+  const CATask& tk = tasks[sg.task];
+  const unsigned local = (unsigned)(blockIdx.x - __ldg(starts + s)), nb = (unsigned)tk.d.blocks;
+  ca_partial_block(tk.A, tk.B, tk.part, tk.d, sg.t0 + local / nb, local % nb);
 }
 
 __global__ void k_contract_all_final_grouped(const CATask* __restrict__ tasks, int n,
@@ -2673,11 +2686,50 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
     c.d = ca_perm(*r.d);
     if (!perm_fits(c.d)) return false;
     c.scale = r.scale;
-    c.block_start = cb;
     c.t_start = ct;
-    cb += c.d.blocks * c.d.lt;
     ct += c.d.lt;
     ca.push_back(c);
+  }
+  // correlator segments, chunk-major; within a chunk the tasks ordered by the
+  // operand they share most in this level (then the other operand)
+  std::vector<long long> seg_start;
+  std::vector<CASeg> segs;
+  {
+    std::unordered_map<const void*, int> uses;
+    for (const CATask& c : ca) {
+      ++uses[c.A];
+      ++uses[c.B];
+    }
+    struct Key {
+      uintptr_t primary, secondary;
+      int task;
+    };
+    std::vector<Key> keys;
+    std::vector<int> per(ca.size());  // slices per chunk
+    int max_chunks = 0;
+    for (size_t i = 0; i < ca.size(); ++i) {
+      uintptr_t a = reinterpret_cast<uintptr_t>(ca[i].A), b = reinterpret_cast<uintptr_t>(ca[i].B);
+      const int ua = uses[ca[i].A], ub = uses[ca[i].B];
+      if (ub > ua || (ub == ua && b < a)) std::swap(a, b);
+      keys.push_back({a, b, (int)i});
+      per[i] = (int)std::min<long long>(ca[i].d.lt, std::max<long long>(
+                                                        1, kCaChunkElems / std::max(1ll, ca[i].d.n)));
+      max_chunks = std::max(max_chunks, (ca[i].d.lt + per[i] - 1) / per[i]);
+    }
+    std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+      if (x.primary != y.primary) return x.primary < y.primary;
+      if (x.secondary != y.secondary) return x.secondary < y.secondary;
+      return x.task < y.task;
+    });
+    for (int q = 0; q < max_chunks; ++q)
+      for (const Key& k : keys) {
+        const CATask& c = ca[k.task];
+        const int t0 = q * per[k.task];
+        if (t0 >= c.d.lt) continue;
+        seg_start.push_back(cb);
+        segs.push_back({k.task, t0});
+        cb += c.d.blocks * std::min(per[k.task], c.d.lt - t0);
+      }
   }
   auto starts = [&](const auto& v) {
     std::vector<long long> st;
@@ -2687,7 +2739,9 @@ bool append_level_tasks(const std::vector<GroupExt>& ext, const std::vector<Grou
   lvl->pack_starts = starts(pk);
   lvl->red_starts = starts(rd);
   lvl->perm_starts = starts(pm);
-  lvl->ca_starts = starts(ca);
+  lvl->ca_starts = reinterpret_cast<const long long*>(append(buf, seg_start, 64));
+  lvl->ca_segs = reinterpret_cast<const void*>(append(buf, segs, 64));
+  lvl->nca_seg = (int)segs.size();
   lvl->pack = reinterpret_cast<const void*>(append(buf, pk, 64));
   lvl->npack = (int)pk.size();
   lvl->pack_blocks = pb;
@@ -2725,6 +2779,7 @@ void rebase_level(LevelDev* lvl, const char* base) {
   lvl->gemm_fused = base + reinterpret_cast<uintptr_t>(lvl->gemm_fused);
   lvl->gemm_pair = base + reinterpret_cast<uintptr_t>(lvl->gemm_pair);
   lvl->ca = base + reinterpret_cast<uintptr_t>(lvl->ca);
+  lvl->ca_segs = base + reinterpret_cast<uintptr_t>(lvl->ca_segs);
   auto rb = [&](const long long*& p) {
     p = reinterpret_cast<const long long*>(base + reinterpret_cast<uintptr_t>(p));
   };
@@ -2810,7 +2865,8 @@ int launch_level(const LevelDev& L, cudaStream_t s, cudaEvent_t* marks, unsigned
   if (L.nca > 0) {
     mark();
     k_contract_all_grouped<<<(unsigned)L.ca_blocks, 256, 0, s>>>(
-        static_cast<const CATask*>(L.ca), L.ca_starts, L.nca);
+        static_cast<const CATask*>(L.ca), L.ca_starts, static_cast<const CASeg*>(L.ca_segs),
+        L.nca_seg);
     ++nk;
     mark();
     k_contract_all_final_grouped<<<(unsigned)((L.ca_threads + 127) / 128), 128, 0, s>>>(

@@ -141,8 +141,9 @@ struct LevelDev {
   int nperm;
   long long perm_blocks;
   const void* ca;
-  const long long* ca_starts;
-  int nca;
+  const long long* ca_starts;   // first block of each (task, slice) segment
+  const void* ca_segs;          // the segments, slice-major
+  int nca, nca_seg;
   long long ca_blocks, ca_threads;
   bool bf16;
 };

@@ -219,6 +219,36 @@ def test_grouped_windows_bit_identical_to_single_launches(precision):
     assert kernels[64] < kernels[7] < kernels[0]     # windows hold at most W contractions
 
 
+@pytest.mark.parametrize("name,kw", [
+    # parts of uneven (N, Lt): a level's correlators have different slice counts
+    ("batched", dict(n_dags=5, n_functions=12, nvecs=(32, 48, 64), lts=(16, 32, 64))),
+    # two-baryon functions: most correlators of a level share one of 12 leaves
+    ("baryon", dict(n_functions=60))])
+def test_grouped_correlators_sharing_operands(name, kw):
+    """A grouped level's correlators run slice by slice across its tasks, the
+    tasks that share an operand next to each other (its slice is then read
+    from L2 after the first).  Every block still sums the same elements in the
+    same order: bit-identical to one launch per contraction, and within 1e-6
+    of the oracle."""
+    wl = synth.make_workload(name, seed=3, **kw)
+    nd, _ = L.build_dag(wl, precision="tf32x3", leaf_data_fn=lambda li: synth.leaf_data(wl, li))
+    nd.schedule("tree", "lru", 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for w in (0, 512):
+        nd.set_option(L.LQC_OPT_WINDOW, w)
+        nd.execute(stream)
+        nd.wait()
+        out[w] = nd.read_all_correlators()
+    assert np.array_equal(out[512].view(np.float64), out[0].view(np.float64))
+    od, _ = D.build_from_workload(wl)
+    rng = np.random.default_rng(7)
+    roots = [int(r) for r in rng.choice(od.roots(), size=min(16, len(od.roots())), replace=False)]
+    _, ref = _oracle(wl, roots)
+    errs = [rel_err(nd.read_correlator(r), ref[r]) for r in roots]
+    assert max(errs) < TOL_TF32X3, errs
+
+
 @pytest.mark.parametrize("case", [((16, 16), (16, 16), (0, 1), (1, 0)),
                                   ((4, 4, 20, 20), (4, 4, 20, 20), (0, 1, 2, 3), (1, 0, 3, 2)),
                                   ((4, 4, 40, 40), (4, 4, 40, 40), (0, 1, 2, 3), (1, 0, 3, 2)),

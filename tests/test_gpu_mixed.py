@@ -524,3 +524,41 @@ def test_left_operand_outer_k_inner_exact(kernel, window):
     got = d.read_correlator(r)
     assert L.lqc_mixed_error(1) == 0
     assert np.array_equal(got, ref), rel_err(got, ref)
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+@pytest.mark.parametrize("kernel", [0, 2])
+@pytest.mark.parametrize("window", [0, 64])
+def test_left_operand_split_k_in_place_exact(n, kernel, window):
+    """Propagator products whose left operand is K-major over several axes:
+    P x P over (spin, distillation) has k = (spin, distillation) and rows =
+    (spin, distillation) of the left operand, P x P over (spin, spin,
+    distillation) has k = (merged spins, distillation) and one row axis (the
+    left operand is reordered first; rows of 32, 64 and 128, CTA pairs at
+    4n > 128 rows with kernel 2), then closed into correlators: equal to the
+    oracle bit for bit on small integers."""
+    lt = 2
+    rng = np.random.default_rng(n + 7 * kernel + window)
+
+    def ints(*s):
+        return rng.integers(-2, 3, (lt,) + s) + 1j * rng.integers(-2, 3, (lt,) + s)
+    P1, P2, Dx, Mm = ints(4, 4, n, n), ints(4, 4, n, n), ints(4, n, 4, n), ints(n, n)
+    x = C.contract_pair(P1, P2, (1, 3), (0, 2))
+    y = C.contract_pair(P1, P2, (0, 1, 3), (1, 0, 2))
+    ref1 = C.contract_pair(x, Dx, (0, 1, 2, 3), (0, 1, 2, 3))
+    ref2 = C.contract_pair(y, Mm, (0, 1), (0, 1))
+    d = L.Dag(lt, "tf32x3")
+    a, b = d.add_leaf((4, 4, n, n), P1), d.add_leaf((4, 4, n, n), P2)
+    dx, m = d.add_leaf((4, n, 4, n), Dx), d.add_leaf((n, n), Mm)
+    r1 = d.add_contraction(d.add_contraction(a, b, [1, 3], [0, 2]), dx, [0, 1, 2, 3],
+                           [0, 1, 2, 3])
+    r2 = d.add_contraction(d.add_contraction(a, b, [0, 1, 3], [1, 0, 2]), m, [0, 1], [0, 1])
+    d.schedule("tree")
+    d.set_option(L.LQC_OPT_FUSED_MAX_N, 1 << 30)
+    d.set_option(L.LQC_OPT_FUSED_KERNEL, kernel)
+    d.set_option(L.LQC_OPT_WINDOW, window)
+    d.execute(torch.cuda.current_stream().cuda_stream)
+    got1, got2 = d.read_correlator(r1), d.read_correlator(r2)
+    assert L.lqc_mixed_error(1) == 0
+    assert np.array_equal(got1, ref1), rel_err(got1, ref1)
+    assert np.array_equal(got2, ref2), rel_err(got2, ref2)

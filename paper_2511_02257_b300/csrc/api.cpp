@@ -10,6 +10,7 @@
 
 #include "internal.hpp"
 
+#include <system_error>
 #include <thread>
 #include <type_traits>
 #include <vector>
@@ -35,11 +36,20 @@ void parallel_chunks(int64_t n, F f) {
   std::vector<std::thread> th;
   th.reserve(t - 1);
   const int64_t per = (n + t - 1) / t;
-  for (int i = 1; i < t; ++i) {
-    const int64_t a = std::min(n, i * per), b = std::min(n, a + per);
-    th.emplace_back(call, a, b, i);
+  int started = 1;
+  try {
+    for (int i = 1; i < t; ++i, ++started) {
+      const int64_t a = std::min(n, i * per), b = std::min(n, a + per);
+      th.emplace_back(call, a, b, i);
+    }
+  } catch (const std::system_error&) {
+    // no more threads: the calling thread takes the chunks not started
   }
   call(0, std::min(n, per), 0);
+  for (int i = started; i < t; ++i) {
+    const int64_t a = std::min(n, i * per), b = std::min(n, a + per);
+    call(a, b, i);
+  }
   for (auto& x : th) x.join();
 }
 }  // namespace

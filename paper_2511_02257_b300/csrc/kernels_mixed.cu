@@ -1985,15 +1985,17 @@ bool make_raw_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, in
 }
 
 int num_sms() {  // SMs of the current device (one persistent CTA each)
-  static int cached[64] = {0};
+  static int cached[64] = {0};  // read and written atomically: host threads may race here
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-  if (!cached[dev]) {
+  int c = __atomic_load_n(&cached[dev], __ATOMIC_RELAXED);
+  if (!c) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = n > 0 ? n : 148;
+    c = n > 0 ? n : 148;
+    __atomic_store_n(&cached[dev], c, __ATOMIC_RELAXED);
   }
-  return cached[dev];
+  return c;
 }
 
 }  // namespace
@@ -2327,19 +2329,20 @@ int launch_gemm_pair_t(const GemmParams& gp, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  static int pairs[2] = {0, 0};  // resident pairs per kernel form (device 0 sized)
-  int& np = pairs[AMN ? 1 : 0];
-  if (!np) {
+  // resident pairs of this kernel form, found once (a function-local static:
+  // initialised by one thread; sized on the first device that launches it)
+  static const int np = [&]() {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-    cfg.gridDim = dim3(2 * (num_sms() / 2));
+    cudaLaunchConfig_t probe = cfg;
+    probe.gridDim = dim3(2 * (num_sms() / 2));
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &probe) != cudaSuccess || n < 1) {
       cudaGetLastError();
       n = num_sms() / 2;
     }
-    np = n;
-  }
+    return n;
+  }();
   cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(gp.total_tiles, np)));
   return cudaLaunchKernelEx(&cfg, kern, gp) == cudaSuccess ? 1 : -1;
 }

@@ -1015,7 +1015,10 @@ int exec_autotune(Dag& g, void* stream, int reps, lqc_tune_entry* entries, int64
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0), "tune event");
-  CK(cudaEventCreate(&e1), "tune event");
+  if (cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(g, e, "tune event");
+  }
   int rc = LQC_OK;
   size_t best = 0;
   for (size_t c = 0; c < cand.size() && rc == LQC_OK; ++c) {

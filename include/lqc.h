@@ -599,6 +599,16 @@ int lqc_test_tf32_rounding(int64_t n, uint32_t seed, int64_t* mismatches);
  * budgeted plan). */
 int lqc_test_tamper_plan(lqc_dag* dag, int what);
 
+/* Copy a leaf's host store as the library keeps it (the store the device
+ * copies come from) into `out`, and its exponent into *scale_exp.  FP64:
+ * the complex128 values as given, exponent 0.  Mixed precisions: complex64
+ * values x * 2^-scale_exp, rounded once to nearest from FP64 (the leaf
+ * normalisation of lqc_dag_set_leaf_data).  Bytes: Lt x elements x 16
+ * (FP64) or x 8; `cap_bytes` must hold them.  Errors: LQC_ERR_ARG (not a
+ * leaf, null pointer, capacity too small), LQC_ERR_STATE (no data given). */
+int lqc_test_read_leaf_store(lqc_dag* dag, int64_t leaf_id, void* out, int64_t cap_bytes,
+                             int* scale_exp);
+
 #ifdef __cplusplus
 }
 #endif

@@ -173,6 +173,23 @@ int lqc_test_tamper_plan(lqc_dag* h, int what) {
   LQC_GUARD_END(h)
 }
 
+int lqc_test_read_leaf_store(lqc_dag* h, int64_t id, void* out, int64_t cap_bytes,
+                             int* scale_exp) {
+  if (!h || !out || !scale_exp) return LQC_ERR_ARG;
+  LQC_GUARD_BEGIN
+  Dag& g = h->d;
+  if (id < 0 || id >= (int64_t)g.nodes.size() || !g.nodes[id].is_leaf())
+    return fail(h, LQC_ERR_ARG, "not a leaf");
+  const Node& n = g.nodes[id];
+  if (!n.has_data || !n.host) return fail(h, LQC_ERR_STATE, "leaf has no data");
+  const int64_t bytes = g.size_bytes(id);
+  if (cap_bytes < bytes) return fail(h, LQC_ERR_ARG, "capacity too small");
+  std::memcpy(out, n.host, (size_t)bytes);
+  *scale_exp = n.scale_exp;
+  return LQC_OK;
+  LQC_GUARD_END(h)
+}
+
 int lqc_dag_create(lqc_dag** out, int64_t lt, lqc_precision prec) {
   if (!out || lt < 1 || lt > kMaxLt) return LQC_ERR_ARG;
   if (prec != LQC_PREC_FP64 && prec != LQC_PREC_TF32X3 && prec != LQC_PREC_BF16X3)

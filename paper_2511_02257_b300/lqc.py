@@ -112,6 +112,7 @@ _sig("lqc_test_inject_failure", ctypes.c_int, [ctypes.c_int, c_i64])
 _sig("lqc_test_expire_wait", ctypes.c_int, [c_i64, c_vp])
 _sig("lqc_test_tamper_plan", ctypes.c_int, [c_vp, ctypes.c_int])
 _sig("lqc_test_tf32_rounding", ctypes.c_int, [c_i64, ctypes.c_uint32, P_i64])
+_sig("lqc_test_read_leaf_store", ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, P_int])
 _sig("lqc_dag_wait", ctypes.c_int, [c_vp, c_i64])
 _sig("lqc_dag_autotune", ctypes.c_int, [c_vp, c_vp, ctypes.c_int, ctypes.POINTER(lqc_tune_entry),
                                         c_i64, P_i64])
@@ -157,7 +158,7 @@ for _n in ("lqc_dag_create", "lqc_dag_destroy", "lqc_dag_set_batch", "lqc_dag_ad
            "lqc_measure_fp64_peak", "lqc_contract_mixed", "lqc_contract_mixed_scratch_bytes",
            "lqc_contract_all_c64", "lqc_mixed_error", "lqc_contract_all_c64_scratch_bytes",
            "lqc_dag_prepare", "lqc_test_inject_failure", "lqc_test_expire_wait",
-           "lqc_test_tamper_plan", "lqc_test_tf32_rounding"):
+           "lqc_test_tamper_plan", "lqc_test_tf32_rounding", "lqc_test_read_leaf_store"):
     globals()[_n] = getattr(_lib, _n)
 
 
@@ -244,6 +245,19 @@ class Dag:
         self._check(_lib.lqc_dag_set_leaf_data(self.h, int(leaf),
                                                arr.view(np.float64).ctypes.data_as(P_dbl)),
                     "set_leaf_data")
+
+    def leaf_store(self, leaf: int):
+        """(values, exponent) of a leaf's host store as the library keeps it:
+        complex128 values (FP64), or complex64 values x * 2^-exponent (mixed
+        precisions); shape (Lt, elements).  A test hook."""
+        info = self.node_info(leaf)
+        dt = np.complex128 if self.precision == "fp64" else np.complex64
+        out = np.zeros(info["size"] // np.dtype(dt).itemsize, dtype=dt)
+        e = ctypes.c_int()
+        self._check(_lib.lqc_test_read_leaf_store(self.h, int(leaf), out.ctypes.data_as(c_vp),
+                                                  out.nbytes, ctypes.byref(e)),
+                    "test_read_leaf_store")
+        return out.reshape(info["lt"], -1), e.value
 
     def add_contraction(self, left: int, right: int, la: Sequence[int], ra: Sequence[int]) -> int:
         a, pa = _intarr(la)

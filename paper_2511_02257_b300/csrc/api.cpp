@@ -22,7 +22,7 @@ namespace {
 constexpr int kMaxHostThreads = 32;
 template <typename F>
 void parallel_chunks(int64_t n, F f) {
-  const int64_t per_min = 1 << 20;
+  const int64_t per_min = 1 << 17;
   int t = (int)std::min<int64_t>(kMaxHostThreads, std::max<int64_t>(1, n / per_min));
   t = std::min<int>(t, std::max(1u, std::thread::hardware_concurrency()));
   auto call = [&](int64_t a, int64_t b, int i) {
